@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Benchmark: forward + adjoint gradient evaluations per second at 256^3.
+
+Workload: one chain per GPU, 256^3 mesh, L = 1000 Mpc/h, ALPT (r_s = 4) + CIC,
+Phi x delta web (16 regions, Table 3 bias), NB likelihood; FP32 fields with
+FP64 reductions.  A step is one full log-posterior + gradient evaluation
+(every stage of the forward model and of its adjoint).
+
+  value      device-resident inputs, CUDA events on the context stream,
+             max over ranks; grad evals/s for the whole job
+  e2e        the same through bridge_logpost_grad_host: pinned host nu and
+             counts copied in and the gradient copied out inside every step
+  roofline   dominant kernel class from live CUDA-event timing of its
+             launches; algorithmic bytes = each launch's distinct inputs read
+             once and outputs written once; peak = measured copy bandwidth
+  cpu_baseline  the FP64 oracle on the host cores (bounded sample)
+
+`--impl reference` times the FP64 CPU oracle instead (the paper has no code).
+Under torchrun (N > 1) every rank runs its own chain (replicas, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "forward+adjoint grad evals/s at 256^3 (FP32 batched vs FP64 plain); % HBM peak"
+UNIT = "grad evals/s"
+WORKLOAD_INDEX = 2               # 256^3, L = 1000, Phi x delta web
+MODEL_R = {16: 226, 4: 178}      # canonical algorithmic bytes per evaluation, in units of R = 4 N^3 bytes
+FALLBACK_HBM = 6800.0
+
+
+# ---------------------------------------------------------------------------
+# host-side helpers (also exercised by the CPU multi-process tests)
+# ---------------------------------------------------------------------------
+def rank_seeds(cfg, rank: int):
+    """Independent chains per rank: seeds offset by the rank."""
+    return cfg.seed_eval + 1000 * rank, cfg.seed_counts + 1000 * rank
+
+
+def max_over_ranks(value: float, dist=None) -> float:
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": FALLBACK_HBM}, "fallback"
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_2506_03969_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(kernel: str, alg_bytes_per_launch: float):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current sources.
+
+    The summary line reads: traffic <kernel> <csrc hash> <dram/algorithmic ratio>; the ratio
+    (measured on a smaller mesh) scales to the timed launch."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    if not os.path.exists(path):
+        return None
+    cur = csrc_hash()
+    for line in open(path):
+        m = re.match(r"\s*traffic\s+(\S+)\s+(\S+)\s+([0-9.eE+-]+)", line)
+        if m and m.group(1) == kernel and m.group(2) == cur:
+            return float(m.group(3)) * alg_bytes_per_launch
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing
+# ---------------------------------------------------------------------------
+def oracle_eval_seconds(n: int, seed: int) -> float:
+    import numpy as np
+    import torch
+    import synth
+    from oracle import model
+    cfg = synth.config(WORKLOAD_INDEX)
+    cfg.n = n
+    cfg.box = 1000.0 * n / 256.0                     # same cell size as the timed workload
+    bias = synth.default_bias(cfg)
+    nu = synth.white_noise(n, seed)
+    counts = synth.timing_counts(n, seed + 1, cfg.mean_tracers)
+    t0 = time.perf_counter()
+    model.logpost_and_grad(nu, counts, cfg, bias)
+    return time.perf_counter() - t0
+
+
+def oracle_sample(budget_s: float):
+    """Largest mesh whose single oracle gradient fits the budget; throughput scaled
+    to 256^3 evaluations by the voxel count (an upper bound for the CPU)."""
+    import torch
+    threads = torch.get_num_threads()
+    t64 = oracle_eval_seconds(64, 9000)
+    n, t = 64, t64
+    for cand in (128, 256):
+        est = t * 8.5
+        if est > budget_s:
+            break
+        t = oracle_eval_seconds(cand, 9000)
+        n = cand
+    scale = (n / 256.0) ** 3
+    return {"value": scale / t, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"one FP64 oracle gradient at {n}^3 (same cell size, 16 regions) took {t:.2f} s on "
+                      f"{threads} threads; scaled to 256^3 by voxel count (x{1/scale:g})",
+            "seconds": t, "mesh": n}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, each step a bounded sample."""
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    threads = torch.get_num_threads()
+    # mesh per step sized so that warm-up + steps fit in about two minutes
+    per_step = 120.0 / max(1, args.steps + args.warmup)
+    t32 = oracle_eval_seconds(32, 9100)
+    n = 32
+    for cand, factor in ((64, 10.0), (128, 75.0), (256, 650.0)):
+        if t32 * factor <= per_step:
+            n = cand
+    for _ in range(args.warmup):
+        oracle_eval_seconds(n, 9100)
+    times = [oracle_eval_seconds(n, 9100 + s) for s in range(args.steps)]
+    total = sum(times)
+    scale = (n / 256.0) ** 3
+    value = args.steps * scale / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps / scale,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"each step one FP64 oracle gradient at {n}^3 (same cell size); "
+                                       f"throughput scaled to 256^3 by voxel count (x{1/scale:g})"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(batch: int):
+    return {"workload": "256^3 mesh, L=1000 Mpc/h, ALPT r_s=4 + CIC, Phi x delta web (16 regions, Table 3 bias), "
+                        "NB likelihood; forward + hand-written adjoint per step",
+            "n": 256, "box_mpc_h": 1000.0, "chains_per_gpu": batch, "regions": 16,
+            "precision": "FP32 fields, FP64 reductions",
+            "l2": "working set ~3.7 GB per chain and ~15 GB moved per evaluation, far above the 129 MB L2"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    import paper_2506_03969_gb300 as pkg
+    from paper_2506_03969_gb300 import build as pbuild
+    import synth
+    if rank == 0:
+        pbuild.build()
+    if world > 1:
+        dist.barrier()
+
+    cfg = synth.config(WORKLOAD_INDEX)
+    bias = synth.default_bias(cfg)
+    seed_nu, seed_c = rank_seeds(cfg, rank)
+    nu_h = torch.tensor(synth.white_noise(cfg.n, seed_nu), dtype=torch.float32).contiguous()
+    c_h = torch.tensor(synth.timing_counts(cfg.n, seed_c, cfg.mean_tracers), dtype=torch.int32).contiguous()
+    ctx = pkg.Context(pkg.config_from(cfg, batch=1))
+    nu = nu_h.cuda()
+    counts = c_h.cuda()
+    grad = torch.empty_like(nu)
+    stream = ctx.stream
+
+    for _ in range(args.warmup):
+        ctx.bridge_logpost_grad(nu, counts, [bias], grad_out=grad, want_bias_grad=False)
+    launches_per_step = ctx.launches()
+
+    # --- timed region: device-resident inputs -------------------------------
+    sampler = ClockSampler(local) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        lp, _, _ = ctx.bridge_logpost_grad(nu, counts, [bias], grad_out=grad, want_bias_grad=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    elapsed = e0.elapsed_time(e1) / 1e3
+    elapsed = max_over_ranks(elapsed, dist if world > 1 else None)
+    value = args.steps * world / elapsed
+
+    # --- per-kernel-class CUDA-event timing (separate pass, same work) ------
+    ctx.bridge_profile_enable(True)
+    prof_steps = max(1, min(args.steps, 5))
+    for _ in range(prof_steps):
+        ctx.bridge_logpost_grad(nu, counts, [bias], grad_out=grad, want_bias_grad=False)
+    prof = ctx.bridge_profile_read()
+    ctx.bridge_profile_enable(False)
+    total_ms = sum(v[1] for v in prof.values())
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dname, (dl, dms, dbytes) = dom
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    achieved = dbytes / (dms / 1e3) / 1e9
+    alg_per_launch = dbytes / dl
+    traffic = recorded_traffic(dname, alg_per_launch)
+    R = 4.0 * cfg.n ** 3
+    model_bytes = MODEL_R[cfg.n_regions] * R
+    eval_gbs = model_bytes * value / world / 1e9
+
+    # --- end to end through the host-buffer entry point ---------------------
+    nu_p = nu_h.pin_memory()
+    c_p = c_h.pin_memory()
+    g_p = torch.empty_like(nu_p).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        ctx.bridge_logpost_grad_host(nu_p, c_p, [bias], g_p)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 50))
+    for _ in range(e2e_steps):
+        ctx.bridge_logpost_grad_host(nu_p, c_p, [bias], g_p)
+    e2e_t = max_over_ranks(time.perf_counter() - t0, dist if world > 1 else None)
+    e2e_value = e2e_steps * world / e2e_t
+
+    extras = {}
+    cpu = None
+    if rank == 0 and not args.no_extras:
+        extras = run_extras(pkg, synth, cfg, bias, nu, counts, args)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(budget_s=args.cpu_budget)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(1),
+            "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src + " copy bandwidth",
+                         "launches_per_step": dl / prof_steps, "alg_bytes_per_launch": alg_per_launch,
+                         "share_of_step": dms / total_ms},
+            "path_roofline": {"model_bytes_per_eval": model_bytes, "achieved_gbs": eval_gbs,
+                              "frac": eval_gbs / hbm, "model": f"{MODEL_R[cfg.n_regions]}R, R = 4 N^3 bytes"},
+            "kernels": {k: {"launches_per_step": v[0] / prof_steps, "ms_per_step": v[1] / prof_steps,
+                            "gbs": (v[2] / (v[1] / 1e3) / 1e9) if v[1] > 0 and v[2] > 0 else None}
+                        for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(nu_h.numel() * 4 + c_h.numel() * 4),
+                    "d2h_bytes_per_step": int(nu_h.numel() * 4 + 8)},
+            "gpu_launches": int(launches_per_step * args.steps),
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "logpost": float(lp[0]),
+            "extras": extras,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_extras(pkg, synth, cfg, bias, nu32, counts, args):
+    """Comparators reported beside the headline: FP64 plain path, batched chains, HMC dH."""
+    import numpy as np
+    import torch
+    out = {}
+
+    def timed(fn, steps):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / steps
+
+    # FP64 plain single chain at 256^3
+    c64 = pkg.Context(pkg.config_from(cfg, precision=pkg.BRIDGE_FP64, batch=1))
+    nu64 = nu32.double()
+    g64 = torch.empty_like(nu64)
+    t = timed(lambda: c64.bridge_logpost_grad(nu64, counts, [bias], grad_out=g64, want_bias_grad=False), 3)
+    lp64, _, _ = c64.bridge_logpost_grad(nu64, counts, [bias], grad_out=g64, want_bias_grad=False)
+    c32 = pkg.Context(pkg.config_from(cfg, batch=1))
+    lp32, g32, _ = c32.bridge_logpost_grad(nu32, counts, [bias], want_bias_grad=False)
+    out["fp64_plain_256"] = {"evals_per_s": 1.0 / t,
+                             "fp32_vs_fp64_grad_rel_l2": float(torch.linalg.vector_norm(g32.double() - g64) /
+                                                               torch.linalg.vector_norm(g64)),
+                             "fp32_vs_fp64_logpost_rel": abs(lp32[0] - lp64[0]) / abs(lp64[0])}
+    # HMC trajectory at 256^3: 10 leapfrog steps, eps = 0.05, FP32 vs FP64 dH
+    p0 = torch.tensor(synth.momentum(cfg.n, cfg.seed_momentum), dtype=torch.float64, device="cuda")
+    n64, p64 = nu64.clone(), p0.clone()
+    h0a, h1a = c64.bridge_leapfrog(n64, p64, counts, [bias], 10, 0.05)
+    n32, p32 = nu32.clone(), p0.float()
+    t0 = time.perf_counter()
+    h0b, h1b = c32.bridge_leapfrog(n32, p32, counts, [bias], 10, 0.05)
+    torch.cuda.synchronize()
+    tl = time.perf_counter() - t0
+    out["hmc_256_10_steps"] = {"dH_fp64": h1a[0] - h0a[0], "dH_fp32": h1b[0] - h0b[0],
+                               "nu_rel_l2_fp32_vs_fp64": float(torch.linalg.vector_norm(n32.double() - n64) /
+                                                               torch.linalg.vector_norm(n64)),
+                               "fp32_trajectory_s": tl}
+    del c64
+    # batched: 16 chains at 128^3 in one launch per pass
+    cb = synth.config(3)
+    biases = synth.perturbed_biases(synth.default_bias(cb), cb.batch, cb.seed_perturb)
+    ctxb = pkg.Context(pkg.config_from(cb))
+    nub = torch.tensor(synth.white_noise(cb.n, cb.seed_eval, cb.batch), dtype=torch.float32, device="cuda")
+    cnb = torch.tensor(synth.timing_counts(cb.n, cb.seed_counts, cb.mean_tracers, batch=cb.batch),
+                       dtype=torch.int32, device="cuda")
+    gb = torch.empty_like(nub)
+    t = timed(lambda: ctxb.bridge_logpost_grad(nub, cnb, biases, grad_out=gb, want_bias_grad=False), 5)
+    out["batched_16x128"] = {"chain_evals_per_s": cb.batch / t, "ms_per_batched_eval": 1e3 * t}
+    c1 = pkg.Context(pkg.config_from(cb, batch=1))
+    g1 = torch.empty_like(nub[0])
+    t1 = timed(lambda: c1.bridge_logpost_grad(nub[0].contiguous(), cnb[0].contiguous(), [biases[0]], grad_out=g1,
+                                              want_bias_grad=False), 5)
+    out["single_128"] = {"evals_per_s": 1.0 / t1}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=60.0, help="seconds for the oracle sample")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,214 @@
+/*
+ * bridge.h -- C ABI of the GB300 (sm_103a) library for the differentiable
+ * fuzzy-cosmic-web forward model and its adjoint (arXiv 2506.03969).
+ *
+ * The library evaluates, for B independent chains on one GPU,
+ *
+ *     log P(nu | n*) = log P(nu) + log L(n* | M(nu, b)) + log P(b)       (Eq. posterior)
+ *
+ * with M = M_b o M_Psi o M_delta (Sect. 2.1):
+ *   M_delta : white noise nu -> linear field delta0 (App. A)
+ *   M_Psi   : ALPT displacement, Psi = K o Psi_2LPT + (1-K) o Psi_SC (Sect. 2.3),
+ *             then cloud-in-cell mass assignment -> evolved delta
+ *   M_b     : Phi-web (tidal tensor) and, for 16 regions, delta-web (density
+ *             Hessian) eigenvalues -> sigmoid memberships (Eq. sigmoid,
+ *             Eq. soft_cweb_p; Sect. 2.7 hierarchy) -> per-voxel bias
+ *             parameters -> Eq. local_bias -> normalisation C
+ *   L       : negative binomial (gamma-Poisson, Sect. 2.6, Eq. log_likelihood)
+ *   priors  : -1/2 |nu|^2 (constant dropped) and log-normal (Eq. lognormal) on
+ *             alpha_r, beta_r for regions r in bias.prior_mask
+ * and its gradient with respect to nu (hand-written adjoint of every step)
+ * and to the alpha/beta bias tables, plus HMC leapfrog trajectories (Sect. 2.2).
+ *
+ * Conventions.
+ *   Fields are C-order [chain][x][y][z] with N^3 cells of side L/N.  FP32
+ *   configurations take float buffers, FP64 configurations double buffers.
+ *   Wavenumbers k_j = 2 pi m_j / L; operators with an odd power of k_j set
+ *   k_j = 0 on the Nyquist plane of axis j; 1/k^2 := 0 at k = 0.
+ *   Eigenvalues are ordered lambda1 >= lambda2 >= lambda3; memberships are
+ *   p^V = 1 - w1, p^S = w1 - w2, p^F = w2 - w3, p^K = w3 (regions V,S,F,K =
+ *   0..3); 16-region models use region 4*j + k for Phi class j, delta class k.
+ *
+ * Ownership.  The caller owns every buffer and the CUDA stream.  A context owns
+ * its device workspace (allocated once in bridge_create, sized by
+ * bridge_workspace_bytes) and releases it in bridge_destroy.  Calls on one
+ * context are stream-ordered on its stream and must not overlap from several
+ * host threads.
+ *
+ * Errors.  Every int-returning call returns a BRIDGE_* status; 0 is success.
+ * On error the outputs are unspecified and bridge_last_error() describes the
+ * cause.  There is no CPU fallback: without a usable GPU, bridge_create
+ * returns BRIDGE_ENODEVICE.
+ */
+#ifndef BRIDGE_H
+#define BRIDGE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    BRIDGE_OK = 0,
+    BRIDGE_EINVAL = 1,      /* bad shape, parameter, pointer or count value    */
+    BRIDGE_ENOMEM = 2,      /* device or pinned-host allocation failed         */
+    BRIDGE_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed     */
+    BRIDGE_ENONFINITE = 4,  /* log posterior or Hamiltonian is not finite      */
+    BRIDGE_ETIMEOUT = 5,    /* a bounded device-side wait gave up              */
+    BRIDGE_ENODEVICE = 6    /* no CUDA device of compute capability 10.3       */
+};
+
+enum { BRIDGE_FP32 = 0, BRIDGE_FP64 = 1 };
+
+#define BRIDGE_MAX_REGIONS 16
+
+/* Model and mesh configuration (one per context). */
+typedef struct {
+    int32_t n;               /* mesh side N: power of two, 16 <= N <= 512            */
+    int32_t batch;           /* independent chains B >= 1                            */
+    double box;              /* box side L [Mpc/h], > 0                              */
+    double pk_amp;           /* P(k) = pk_amp k^pk_ns / (1 + (k/pk_kc)^2)^pk_pow     */
+    double pk_ns, pk_kc, pk_pow;
+    double growth_d;         /* linear growth D (1 at z = 0)                         */
+    double d2_over_d2;       /* second-order growth D2 / D^2 (-3/7)                  */
+    double r_s;              /* ALPT blend radius [Mpc/h] (Sect. 2.3: 4)             */
+    double lambda_th_phi;    /* Phi-web eigenvalue threshold (Sect. 2.8)             */
+    double lambda_th_delta;  /* delta-web eigenvalue threshold                       */
+    double sharpness;        /* sigmoid steepness s (Eq. sigmoid)                    */
+    int32_t n_regions;       /* 4: Phi-web; 16: Phi x delta web (Sect. 2.7)          */
+    double rho_floor;        /* 1 + delta is floored at this value (> 0)             */
+    int32_t precision;       /* BRIDGE_FP32, or BRIDGE_FP64 (n <= 256)               */
+} bridge_config;
+
+/* Bias table of one chain; entries [0, n_regions) are used (Eq. local_bias,
+ * Sect. 2.6 beta, Eq. lognormal hyper-parameters). */
+typedef struct {
+    double a[BRIDGE_MAX_REGIONS];      /* amplitude per region (> 0)          */
+    double alpha[BRIDGE_MAX_REGIONS];  /* power-law exponent                  */
+    double rho[BRIDGE_MAX_REGIONS];    /* first cut-off scale (> 0)           */
+    double eps[BRIDGE_MAX_REGIONS];    /* first cut-off exponent              */
+    double rhop[BRIDGE_MAX_REGIONS];   /* second cut-off scale (>= 0; 0: off) */
+    double epsp[BRIDGE_MAX_REGIONS];   /* second cut-off exponent (> 0)       */
+    double beta[BRIDGE_MAX_REGIONS];   /* NB dispersion (> 0)                 */
+    uint32_t prior_mask;               /* bit r: log-normal prior on alpha_r and beta_r */
+    double mu_alpha, sigma_alpha;      /* log-normal hyper-parameters          */
+    double mu_beta, sigma_beta;
+} bridge_bias;
+
+typedef struct bridge_ctx bridge_ctx;
+
+/* Host-only check of a configuration (no device needed).  Returns BRIDGE_OK or
+ * BRIDGE_EINVAL. */
+int bridge_validate_config(const bridge_config* cfg);
+
+/* Device workspace a context with this configuration allocates, in bytes;
+ * 0 if the configuration is invalid.  Host-only. */
+size_t bridge_workspace_bytes(const bridge_config* cfg);
+
+/* Amplitude A such that sigma(R) = sigma for P(k) = A k^ns/(1+(k/kc)^2)^pw,
+ * sigma^2(R) = 1/(2 pi^2) int k^2 P(k) W(kR)^2 dk with the spherical top-hat
+ * window W (normalisation of the linear spectrum, Sect. 2.1/App. A).  Composite
+ * Simpson rule in ln k; host-only.  Returns a negative value on bad input. */
+double bridge_pk_amplitude(double sigma, double radius, double ns, double kc, double pw);
+
+/* Create a context on the current CUDA device for `cfg`, ordered on `stream`
+ * (a cudaStream_t; NULL = legacy default stream).  Allocates the workspace.
+ * *out is set only on success.  Errors: EINVAL, ENODEVICE, ENOMEM, ECUDA. */
+int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out);
+
+/* Release a context and its workspace (after synchronising its stream).  NULL is a no-op. */
+void bridge_destroy(bridge_ctx* ctx);
+
+/* Forward model (Sect. 2.1).
+ *   nu          device, [B][N][N][N] float or double (per precision), read only
+ *   counts      device, [B][N][N][N] int32 tracer counts n* in [0, 65535]
+ *               (EINVAL otherwise), read only
+ *   bias        host, bias[B]
+ *   ln_nbar_out device, [B][N^3] float/double: ln nbar_i; may be NULL
+ *   logpost_out host, [B] doubles: log posterior; may be NULL
+ * Every evaluating call synchronises the context stream before it returns (it
+ * reads back the FP64 scalars and the count range check). */
+int bridge_forward(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
+                   void* ln_nbar_out, double* logpost_out);
+
+/* Log posterior and gradient (the "single-gradient evaluation" of Sect. 3.1).
+ *   nu, counts, bias   as in bridge_forward
+ *   logpost_out        host [B] doubles, may be NULL
+ *   grad_nu_out        device [B][N^3] float/double: d log post / d nu; required
+ *   grad_bias_out      host [B][2*n_regions] doubles: d/d alpha_r (r < n_regions)
+ *                      then d/d beta_r; may be NULL
+ * Synchronises the context stream before returning. */
+int bridge_logpost_grad(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
+                        double* logpost_out, void* grad_nu_out, double* grad_bias_out);
+
+/* The same evaluation with HOST buffers: nu_host, counts_host and
+ * grad_nu_host are host arrays of the shapes above (pinned memory gives
+ * asynchronous copies).  The call copies the inputs to the device, evaluates,
+ * copies the gradient back and synchronises. */
+int bridge_logpost_grad_host(bridge_ctx* ctx, const void* nu_host, const int32_t* counts_host,
+                             const bridge_bias* bias, double* logpost_out, void* grad_nu_host,
+                             double* grad_bias_out);
+
+/* HMC leapfrog trajectory (Sect. 2.2), identity mass matrix, U = -log post:
+ *   p <- p + eps/2 grad; nu <- nu + eps p; p <- p + eps/2 grad  (n_steps times)
+ *   nu, p      device [B][N^3] float/double, updated in place
+ *   counts     device int32 as above; bias host [B]
+ *   h0_out/h1_out host [B] doubles: H = -log post + 1/2 |p|^2 before/after
+ *              (FP64 sums); may be NULL.
+ * Performs n_steps + 1 gradient evaluations.  n_steps >= 1, eps finite.
+ * Returns ENONFINITE if a Hamiltonian is not finite. */
+int bridge_leapfrog(bridge_ctx* ctx, void* nu, void* p, const int32_t* counts, const bridge_bias* bias,
+                    int32_t n_steps, double eps, double* h0_out, double* h1_out);
+
+/* Intermediate fields of the forward model, for inspection and testing.
+ * Writes the field selected by `which` for all chains to device `out`:
+ *   BRIDGE_FIELD_DELTA0   [B][N^3]     linear density delta0 (App. A)
+ *   BRIDGE_FIELD_PSI      [B][3][N^3]  ALPT displacement in cell units (Sect. 2.3)
+ *   BRIDGE_FIELD_DELTA    [B][N^3]     CIC density contrast
+ *   BRIDGE_FIELD_TIDAL    [B][6][N^3]  tidal tensor xx,xy,xz,yy,yz,zz (Sect. 2.8)
+ *   BRIDGE_FIELD_HESSIAN  [B][6][N^3]  density Hessian (App. B; 16 regions only)
+ *   BRIDGE_FIELD_LAMBDA   [B][3][N^3]  Phi-web eigenvalues, descending
+ *   BRIDGE_FIELD_LNNBAR   [B][N^3]     ln nbar (needs counts for N_tr)
+ * Element type follows the precision.  Runs the forward model. */
+enum {
+    BRIDGE_FIELD_DELTA0 = 0, BRIDGE_FIELD_PSI = 1, BRIDGE_FIELD_DELTA = 2, BRIDGE_FIELD_TIDAL = 3,
+    BRIDGE_FIELD_HESSIAN = 4, BRIDGE_FIELD_LAMBDA = 5, BRIDGE_FIELD_LNNBAR = 6
+};
+int bridge_debug_field(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
+                       int32_t which, void* out);
+
+/* Per-kernel-class timing of later calls on this context: with enable != 0
+ * every launch is bracketed by CUDA events recorded on the context stream (a
+ * few microseconds of overhead per launch); the table is cleared.  Host-side;
+ * errors: EINVAL for a NULL context. */
+int bridge_profile_enable(bridge_ctx* ctx, int enable);
+
+/* One row per kernel class since bridge_profile_enable: launches, summed
+ * event-timed duration and summed algorithmic bytes (each launch's distinct
+ * inputs read once and outputs written once). */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+    double bytes;
+} bridge_profile_row;
+
+/* Synchronises the stream and writes at most max_rows rows to `rows` (host);
+ * returns the number written, or a negative BRIDGE_* status. */
+int bridge_profile_read(bridge_ctx* ctx, bridge_profile_row* rows, int max_rows);
+
+/* Number of kernel launches the most recent call on this context issued. */
+int64_t bridge_last_launch_count(const bridge_ctx* ctx);
+
+/* Text of the last error on this context (never NULL; "" if none). */
+const char* bridge_last_error(const bridge_ctx* ctx);
+
+/* Static description of a status code. */
+const char* bridge_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BRIDGE_H */

@@ -13,6 +13,7 @@ Pins: closed forms for pure power laws n = 0 and n = -2 (tests).
 from __future__ import annotations
 
 import math
+import warnings
 
 import numpy as np
 from scipy import integrate
@@ -44,9 +45,11 @@ def sigma2(radius: float, amp: float, ns: float, kc: float, pw: float) -> float:
     total = 0.0
     # split the range so the oscillating tail is resolved
     edges = np.linspace(math.log(1e-8), math.log(1e3 / radius), 64)
-    for a, b in zip(edges[:-1], edges[1:]):
-        v, _ = integrate.quad(integrand, a, b, limit=200, epsabs=0.0, epsrel=1e-12)
-        total += v
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore", integrate.IntegrationWarning)
+        for a, b in zip(edges[:-1], edges[1:]):
+            v, _ = integrate.quad(integrand, a, b, limit=200, epsabs=0.0, epsrel=1e-12)
+            total += v
     return total / (2.0 * math.pi ** 2)
 
 

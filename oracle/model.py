@@ -329,7 +329,7 @@ def logpost_and_grad(nu_np, counts_np, cfg, bias):
     tables = bias_tables(bias, requires_grad=True)
     lp = log_posterior(nu, counts, cfg, bias, tables)
     g_nu, g_a, g_b = torch.autograd.grad(lp, (nu, tables["alpha"], tables["beta"]))
-    return float(lp), g_nu.numpy(), g_a.numpy(), g_b.numpy()
+    return float(lp.detach()), g_nu.numpy(), g_a.numpy(), g_b.numpy()
 
 
 def logpost_value(nu_np, counts_np, cfg, bias) -> float:

@@ -1,0 +1,853 @@
+// C ABI of the library: context, workspace plan, the pass programs of the
+// forward model and of its adjoint, and the leapfrog driver.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/bridge.h"
+#include "common.cuh"
+#include "passes.cuh"
+#include "pointwise.cuh"
+
+using namespace bridge;
+
+namespace {
+
+constexpr int kMaxSpec = 19;   // spectral scratch buffers (peak use: adjoint y merge 13 -> 6)
+constexpr int kMaxReal = 36;   // real-space buffers
+
+// Real buffer slots.
+enum {
+    RB_ALPT = 0,    // 7: delta0, phi_xx, phi_xy, phi_xz, phi_yy, phi_yz, phi_zz
+    RB_PSI = 7,     // 3: displacement (cell units)
+    RB_DELTA = 10,  // 1: CIC density contrast
+    RB_TH = 11,     // 12: tidal tensor (6) then density Hessian (6)
+    RB_SCR = 23     // 13: scratch
+};
+
+Term mk(int src, int dst, int px, int py, int pz, RCode rc, double cre, double cim = 0.0) {
+    Term t;
+    t.src = (int8_t)src; t.dst = (int8_t)dst; t.px = (int8_t)px; t.py = (int8_t)py; t.pz = (int8_t)pz;
+    t.rcode = rc; t.cre = cre; t.cim = cim;
+    return t;
+}
+
+}  // namespace
+
+struct bridge_ctx {
+    bridge_config cfg{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    int64_t launches = 0;
+    int n = 0, B = 0, nr = 4;
+    long long nvox = 0, nspec = 0;
+    size_t esz = 4;
+    // workspace
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    void* spec[kMaxSpec] = {};
+    void* real[kMaxReal] = {};
+    uint16_t* c16 = nullptr;
+    double* partial = nullptr;
+    ChainScalars* sc = nullptr;
+    BiasD* biasd = nullptr;
+    void* biast = nullptr;
+    int* errflag = nullptr;
+    void* grad_tmp = nullptr;   // gradient scratch for leapfrog
+    // host e2e buffers
+    void* h_nu = nullptr;
+    int32_t* h_counts = nullptr;
+    void* h_grad = nullptr;
+    // pinned host staging
+    ChainScalars* sc_host = nullptr;
+    BiasD* biasd_host = nullptr;
+    void* biast_host = nullptr;
+    int* errflag_host = nullptr;
+    KParams kp{};
+    WebParams wp{};
+    // per-launch CUDA-event profiling (bridge_profile_enable)
+    bool prof = false;
+    struct ProfRec { const char* name; double bytes; cudaEvent_t a, b; };
+    std::vector<ProfRec> prof_recs;
+    std::vector<cudaEvent_t> prof_pool;
+    size_t prof_used = 0;
+};
+
+namespace {
+
+int fail(bridge_ctx* c, int st, const std::string& msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+// CK: a CUDA runtime call; CKL: a kernel launch (counted).
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(ctx, BRIDGE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+#define CKL(name, bytes, call)                              \
+    do {                                                    \
+        cudaEvent_t pa_ = nullptr, pb_ = nullptr;           \
+        if (ctx->prof) {                                    \
+            pa_ = prof_event(ctx); pb_ = prof_event(ctx);   \
+            if (pa_) cudaEventRecord(pa_, ctx->stream);     \
+        }                                                   \
+        CK(call);                                           \
+        ++ctx->launches;                                    \
+        if (pb_) {                                          \
+            cudaEventRecord(pb_, ctx->stream);              \
+            ctx->prof_recs.push_back({name, double(bytes), pa_, pb_}); \
+        }                                                   \
+    } while (0)
+
+cudaEvent_t prof_event(bridge_ctx* ctx) {
+    if (ctx->prof_used == ctx->prof_pool.size()) {
+        if (ctx->prof_pool.size() >= 1u << 16) return nullptr;
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        ctx->prof_pool.push_back(e);
+    }
+    return ctx->prof_pool[ctx->prof_used++];
+}
+template <typename T> double rby(const bridge_ctx* c) { return double(c->nvox) * c->B * sizeof(T); }
+template <typename T> double sby(const bridge_ctx* c) { return double(c->nspec) * c->B * 2 * sizeof(T); }
+inline double c16b(const bridge_ctx* c) { return double(c->nvox) * c->B * 2; }
+inline int nth_of(const bridge_ctx* c) { return c->nr == 16 ? 12 : 6; }
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int validate(const bridge_config* c, std::string* why) {
+    auto bad = [&](const char* m) { if (why) *why = m; return BRIDGE_EINVAL; };
+    if (!c) return bad("config is NULL");
+    if (!is_pow2(c->n) || c->n < 16 || c->n > 512) return bad("n must be a power of two in [16, 512]");
+    if (c->batch < 1 || c->batch > 4096) return bad("batch must be in [1, 4096]");
+    if (!(c->box > 0) || !std::isfinite(c->box)) return bad("box must be positive and finite");
+    if (!(c->pk_amp >= 0) || !std::isfinite(c->pk_amp)) return bad("pk_amp must be >= 0 and finite");
+    if (!(c->pk_kc > 0) || !std::isfinite(c->pk_ns) || !std::isfinite(c->pk_pow)) return bad("bad P(k) parameters");
+    if (!std::isfinite(c->growth_d) || !std::isfinite(c->d2_over_d2)) return bad("bad growth factors");
+    if (!(c->r_s >= 0) || !std::isfinite(c->r_s)) return bad("r_s must be >= 0 and finite");
+    if (!std::isfinite(c->lambda_th_phi) || !std::isfinite(c->lambda_th_delta)) return bad("bad thresholds");
+    if (!(c->sharpness > 0) || !std::isfinite(c->sharpness)) return bad("sharpness must be positive");
+    if (c->n_regions != 4 && c->n_regions != 16) return bad("n_regions must be 4 or 16");
+    if (!(c->rho_floor > 0) || !(c->rho_floor < 1)) return bad("rho_floor must be in (0, 1)");
+    if (c->precision != BRIDGE_FP32 && c->precision != BRIDGE_FP64) return bad("precision must be FP32 or FP64");
+    if (c->precision == BRIDGE_FP64 && c->n > 256) return bad("the FP64 path supports n <= 256");
+    return BRIDGE_OK;
+}
+
+int validate_bias(const bridge_ctx* ctx, const bridge_bias* b, std::string* why) {
+    if (!b) { *why = "bias is NULL"; return BRIDGE_EINVAL; }
+    for (int ch = 0; ch < ctx->B; ++ch) {
+        const bridge_bias& x = b[ch];
+        for (int r = 0; r < ctx->nr; ++r) {
+            if (!(x.a[r] > 0) || !(x.rho[r] > 0) || !(x.beta[r] > 0) || !(x.rhop[r] >= 0) || !(x.epsp[r] > 0) ||
+                !std::isfinite(x.alpha[r]) || !std::isfinite(x.eps[r]) || !std::isfinite(x.a[r]) ||
+                !std::isfinite(x.rho[r]) || !std::isfinite(x.beta[r]) || !std::isfinite(x.rhop[r]) ||
+                !std::isfinite(x.epsp[r])) {
+                *why = "bias table entry out of range (a, rho, beta, eps' > 0; rho' >= 0; all finite)";
+                return BRIDGE_EINVAL;
+            }
+        }
+        if (x.prior_mask & ~((ctx->nr == 16) ? 0xFFFFu : 0xFu)) { *why = "prior_mask has bits beyond n_regions"; return BRIDGE_EINVAL; }
+        if (x.prior_mask) {
+            for (int r = 0; r < ctx->nr; ++r)
+                if (((x.prior_mask >> r) & 1u) && !(x.alpha[r] > 0)) { *why = "log-normal prior needs alpha > 0"; return BRIDGE_EINVAL; }
+            if (!(x.sigma_alpha > 0) || !(x.sigma_beta > 0)) { *why = "prior sigma must be > 0"; return BRIDGE_EINVAL; }
+        }
+    }
+    return BRIDGE_OK;
+}
+
+struct Plan {
+    size_t spec_bytes, real_bytes, c16_bytes, partial_bytes, sc_bytes, biasd_bytes, biast_bytes, total;
+    int nspec_buf, nreal_buf;
+};
+
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+Plan make_plan(const bridge_config* c) {
+    Plan p{};
+    const long long n = c->n, B = c->batch;
+    const size_t esz = c->precision == BRIDGE_FP64 ? 8 : 4;
+    const long long nvox = n * n * n, nspec = (n / 2 + 1) * n * n;
+    p.nspec_buf = kMaxSpec;
+    p.nreal_buf = kMaxReal;
+    p.spec_bytes = align_up(size_t(nspec) * 2 * esz * B);
+    p.real_bytes = align_up(size_t(nvox) * esz * B);
+    p.c16_bytes = align_up(size_t(nvox) * 2 * B);
+    p.partial_bytes = align_up(size_t(B) * pw_blocks(c->n) * 32 * sizeof(double));
+    p.sc_bytes = align_up(sizeof(ChainScalars) * B);
+    p.biasd_bytes = align_up(sizeof(BiasD) * B);
+    p.biast_bytes = align_up(sizeof(BiasT<double>) * B);
+    p.total = p.spec_bytes * p.nspec_buf + p.real_bytes * (p.nreal_buf + 1) + p.c16_bytes + p.partial_bytes +
+              p.sc_bytes + p.biasd_bytes + p.biast_bytes + 256;
+    return p;
+}
+
+template <typename T> T* RB(bridge_ctx* c, int i) { return reinterpret_cast<T*>(c->real[i]); }
+template <typename T> cplx_t<T>* SB(bridge_ctx* c, int i) { return reinterpret_cast<cplx_t<T>*>(c->spec[i]); }
+
+Fields16 fields(bridge_ctx* c, int first, int count) {
+    Fields16 f{};
+    for (int i = 0; i < count; ++i) f.p[i] = c->real[first + i];
+    return f;
+}
+
+// --- z pass helpers ---------------------------------------------------------
+template <typename T> int z_fwd(bridge_ctx* ctx, std::vector<const void*> in, std::vector<void*> out) {
+    ZProgram p{};
+    p.n_fields = (int)in.size();
+    for (int i = 0; i < p.n_fields; ++i) { p.in[i] = in[i]; p.out[i] = out[i]; }
+    p.in_cs = ctx->nvox;
+    p.out_cs = ctx->nspec;
+    CKL("z_fwd", p.n_fields * (rby<T>(ctx) + sby<T>(ctx)), launch_z_fwd<T>(ctx->n, ctx->B, p, ctx->stream));
+    return BRIDGE_OK;
+}
+template <typename T> int z_inv(bridge_ctx* ctx, std::vector<const void*> in, std::vector<void*> out) {
+    ZProgram p{};
+    p.n_fields = (int)in.size();
+    for (int i = 0; i < p.n_fields; ++i) { p.in[i] = in[i]; p.out[i] = out[i]; }
+    p.in_cs = ctx->nspec;
+    p.out_cs = ctx->nvox;
+    CKL("z_inv", p.n_fields * (rby<T>(ctx) + sby<T>(ctx)), launch_z_inv<T>(ctx->n, ctx->B, p, ctx->stream));
+    return BRIDGE_OK;
+}
+
+PassProgram program(std::vector<const void*> in, std::vector<void*> out, long long cs) {
+    PassProgram p{};
+    p.n_in = (int)in.size();
+    p.n_out = (int)out.size();
+    for (int i = 0; i < p.n_in; ++i) p.in[i] = in[i];
+    for (int i = 0; i < p.n_out; ++i) p.out[i] = out[i];
+    p.in_cs = p.out_cs = cs;
+    return p;
+}
+void add_merge(PassProgram& p, Term t) { p.merge[p.n_merge++] = t; }
+void add_expand(PassProgram& p, Term t) { p.expand[p.n_expand++] = t; }
+
+template <typename T> std::vector<const void*> cspec(bridge_ctx* c, int first, int count) {
+    std::vector<const void*> v;
+    for (int i = 0; i < count; ++i) v.push_back(c->spec[first + i]);
+    return v;
+}
+template <typename T> std::vector<void*> mspec(bridge_ctx* c, int first, int count) {
+    std::vector<void*> v;
+    for (int i = 0; i < count; ++i) v.push_back(c->spec[first + i]);
+    return v;
+}
+std::vector<const void*> creal(bridge_ctx* c, int first, int count) {
+    std::vector<const void*> v;
+    for (int i = 0; i < count; ++i) v.push_back(c->real[first + i]);
+    return v;
+}
+std::vector<void*> mreal(bridge_ctx* c, int first, int count) {
+    std::vector<void*> v;
+    for (int i = 0; i < count; ++i) v.push_back(c->real[first + i]);
+    return v;
+}
+
+// identity y pass (forward or inverse) on `count` fields, in place
+template <typename T> int y_identity(bridge_ctx* ctx, int first, int count, bool fwd) {
+    PassProgram p = program(cspec<T>(ctx, first, count), mspec<T>(ctx, first, count), ctx->nspec);
+    for (int i = 0; i < count; ++i) {
+        if (fwd) add_merge(p, mk(i, i, 0, 0, 0, R_ONE, 1.0));
+        else add_expand(p, mk(i, i, 0, 0, 0, R_ONE, 1.0));
+    }
+    if (fwd) CKL("y_fwd", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_fwd<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+    else CKL("y_inv", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_inv<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+    return BRIDGE_OK;
+}
+
+#define RUN(x) do { int st_ = (x); if (st_ != BRIDGE_OK) return st_; } while (0)
+
+// ---------------------------------------------------------------------------
+// Forward model.  Leaves in the workspace: real ALPT fields, psi, delta, T/H,
+// lnf (SCR+0), beta_i (SCR+1), scalars (ntr, sumf, lnC, loglik, G, logpost).
+// nu: device [B][N^3].
+// ---------------------------------------------------------------------------
+template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelihood) {
+    const double invn3 = 1.0 / double(ctx->nvox);
+    const bool hier = ctx->nr == 16;
+    // M_delta (App. A) and the linear potential Hessian: nu -> delta0, phi_ij
+    RUN(z_fwd<T>(ctx, {nu}, {ctx->spec[0]}));
+    RUN(y_identity<T>(ctx, 0, 1, true));
+    {
+        PassProgram p = program(cspec<T>(ctx, 0, 1), mspec<T>(ctx, 1, 4), ctx->nspec);
+        add_merge(p, mk(0, 0, 0, 0, 0, R_SQRTP, invn3));
+        add_expand(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));    // W0 -> delta0
+        add_expand(p, mk(0, 1, 2, 0, 0, R_INVK2, 1.0));  // V2 = kx^2/k^2
+        add_expand(p, mk(0, 2, 1, 0, 0, R_INVK2, 1.0));  // V1 = kx/k^2
+        add_expand(p, mk(0, 3, 0, 0, 0, R_INVK2, 1.0));  // V0 = 1/k^2
+        CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+    }
+    {
+        PassProgram p = program(cspec<T>(ctx, 1, 4), mspec<T>(ctx, 5, 7), ctx->nspec);
+        add_expand(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));    // delta0
+        add_expand(p, mk(1, 1, 0, 0, 0, R_ONE, 1.0));    // phi_xx
+        add_expand(p, mk(2, 2, 0, 1, 0, R_ONE, 1.0));    // phi_xy
+        add_expand(p, mk(2, 3, 0, 0, 1, R_ONE, 1.0));    // phi_xz
+        add_expand(p, mk(3, 4, 0, 2, 0, R_ONE, 1.0));    // phi_yy
+        add_expand(p, mk(3, 5, 0, 1, 1, R_ONE, 1.0));    // phi_yz
+        add_expand(p, mk(3, 6, 0, 0, 2, R_ONE, 1.0));    // phi_zz
+        CKL("y_inv", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_inv<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+    }
+    RUN(z_inv<T>(ctx, cspec<T>(ctx, 5, 7), mreal(ctx, RB_ALPT, 7)));
+    // ALPT sources (Sect. 2.3) -> blend -> displacement
+    {
+        const double D = ctx->cfg.growth_d, D2 = ctx->cfg.d2_over_d2 * D * D;
+        CKL("alpt_src", 9 * rby<T>(ctx), launch_alpt_src<T>(ctx->n, ctx->B, fields(ctx, RB_ALPT, 7), RB<T>(ctx, RB_SCR), RB<T>(ctx, RB_SCR + 1), D, D2,
+                              ctx->stream));
+    }
+    RUN(z_fwd<T>(ctx, creal(ctx, RB_SCR, 2), mspec<T>(ctx, 0, 2)));
+    RUN(y_identity<T>(ctx, 0, 2, true));
+    {
+        PassProgram p = program(cspec<T>(ctx, 0, 2), mspec<T>(ctx, 2, 2), ctx->nspec);
+        add_merge(p, mk(0, 0, 0, 0, 0, R_KBLEND, invn3));
+        add_merge(p, mk(1, 0, 0, 0, 0, R_1MKBLEND, invn3));
+        const double c = -1.0 / ctx->kp.dx;               // Psi_j = -i k_j theta / (k^2 dx)
+        add_expand(p, mk(0, 0, 1, 0, 0, R_INVK2, 0.0, c));
+        add_expand(p, mk(0, 1, 0, 0, 0, R_INVK2, 0.0, c));
+        CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+    }
+    {
+        PassProgram p = program(cspec<T>(ctx, 2, 2), mspec<T>(ctx, 4, 3), ctx->nspec);
+        add_expand(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));
+        add_expand(p, mk(1, 1, 0, 1, 0, R_ONE, 1.0));
+        add_expand(p, mk(1, 2, 0, 0, 1, R_ONE, 1.0));
+        CKL("y_inv", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_inv<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+    }
+    RUN(z_inv<T>(ctx, cspec<T>(ctx, 4, 3), mreal(ctx, RB_PSI, 3)));
+    // CIC
+    CKL("fill", rby<T>(ctx), launch_fill<T>(ctx->nvox * ctx->B, RB<T>(ctx, RB_DELTA), T(-1), ctx->stream));
+    CKL("cic_scatter", 4 * rby<T>(ctx), launch_cic_scatter<T>(ctx->n, ctx->B, fields(ctx, RB_PSI, 3), RB<T>(ctx, RB_DELTA), ctx->stream));
+    // tidal tensor and density Hessian (Sect. 2.8, App. B)
+    RUN(z_fwd<T>(ctx, creal(ctx, RB_DELTA, 1), mspec<T>(ctx, 0, 1)));
+    RUN(y_identity<T>(ctx, 0, 1, true));
+    {
+        PassProgram p = program(cspec<T>(ctx, 0, 1), mspec<T>(ctx, 1, hier ? 6 : 3), ctx->nspec);
+        add_merge(p, mk(0, 0, 0, 0, 0, R_ONE, invn3));
+        add_expand(p, mk(0, 0, 2, 0, 0, R_INVK2, 1.0));
+        add_expand(p, mk(0, 1, 1, 0, 0, R_INVK2, 1.0));
+        add_expand(p, mk(0, 2, 0, 0, 0, R_INVK2, 1.0));
+        if (hier) {
+            add_expand(p, mk(0, 3, 2, 0, 0, R_ONE, -1.0));
+            add_expand(p, mk(0, 4, 1, 0, 0, R_ONE, -1.0));
+            add_expand(p, mk(0, 5, 0, 0, 0, R_ONE, -1.0));
+        }
+        CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+    }
+    {
+        const int nt = hier ? 2 : 1;
+        PassProgram p = program(cspec<T>(ctx, 1, 3 * nt), mspec<T>(ctx, 7, 6 * nt), ctx->nspec);
+        for (int h = 0; h < nt; ++h) {
+            const int s = 3 * h, d = 6 * h;
+            add_expand(p, mk(s + 0, d + 0, 0, 0, 0, R_ONE, 1.0));
+            add_expand(p, mk(s + 1, d + 1, 0, 1, 0, R_ONE, 1.0));
+            add_expand(p, mk(s + 1, d + 2, 0, 0, 1, R_ONE, 1.0));
+            add_expand(p, mk(s + 2, d + 3, 0, 2, 0, R_ONE, 1.0));
+            add_expand(p, mk(s + 2, d + 4, 0, 1, 1, R_ONE, 1.0));
+            add_expand(p, mk(s + 2, d + 5, 0, 0, 2, R_ONE, 1.0));
+        }
+        CKL("y_inv", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_inv<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+        RUN(z_inv<T>(ctx, cspec<T>(ctx, 7, 6 * nt), mreal(ctx, RB_TH, 6 * nt)));
+    }
+    // fused web / bias (pass A), normalisation, NB likelihood (pass B)
+    CKL("web_bias", (nth_of(ctx) + 3) * rby<T>(ctx), launch_pass_a<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 12), RB<T>(ctx, RB_DELTA), RB<T>(ctx, RB_SCR),
+                        RB<T>(ctx, RB_SCR + 1), reinterpret_cast<const BiasT<T>*>(ctx->biast), ctx->wp, ctx->partial,
+                        ctx->stream));
+    CKL("reduce", 0.0, launch_reduce(RED_SUMF, ctx->n, ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+    if (likelihood) {
+        CKL("nb_lik", 3 * rby<T>(ctx) + c16b(ctx), launch_pass_b<T>(ctx->n, ctx->B, RB<T>(ctx, RB_SCR), RB<T>(ctx, RB_SCR + 1), ctx->c16, nu, ctx->sc,
+                            ctx->partial, ctx->stream));
+        CKL("reduce", 0.0, launch_reduce(RED_LIK, ctx->n, ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+    }
+    return BRIDGE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint: every forward step transposed, ending with g_nu = d log post/d nu.
+// ---------------------------------------------------------------------------
+template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad) {
+    const double invn3 = 1.0 / double(ctx->nvox);
+    const bool hier = ctx->nr == 16;
+    const int nth = hier ? 12 : 6;
+    // web + bias + NB adjoint: g_delta (direct), g_T, g_H
+    CKL("web_bias_adj", 2 * (nth_of(ctx) + 1) * rby<T>(ctx) + c16b(ctx), launch_web_adjoint<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 12), RB<T>(ctx, RB_DELTA), ctx->c16,
+                             reinterpret_cast<const BiasT<T>*>(ctx->biast), ctx->wp, ctx->sc,
+                             fields(ctx, RB_SCR, 1 + nth), ctx->partial, ctx->stream));
+    CKL("reduce", 0.0, launch_reduce(RED_BIASGRAD, ctx->n, ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+    // spectral adjoint of the tensors (transpose of the forward x node / y expansion)
+    RUN(z_fwd<T>(ctx, creal(ctx, RB_SCR, 1 + nth), mspec<T>(ctx, 0, 1 + nth)));
+    {
+        const int nslot = hier ? 6 : 4;
+        PassProgram p = program(cspec<T>(ctx, 0, 1 + nth), mspec<T>(ctx, 13, nslot), ctx->nspec);
+        for (int h = 0; h < (hier ? 2 : 1); ++h) {
+            const int s = 1 + 6 * h, d = 3 * h;
+            add_merge(p, mk(s + 0, d + 0, 0, 0, 0, R_ONE, 1.0));
+            add_merge(p, mk(s + 1, d + 1, 0, 1, 0, R_ONE, 1.0));
+            add_merge(p, mk(s + 2, d + 1, 0, 0, 1, R_ONE, 1.0));
+            add_merge(p, mk(s + 3, d + 2, 0, 2, 0, R_ONE, 1.0));
+            add_merge(p, mk(s + 4, d + 2, 0, 1, 1, R_ONE, 1.0));
+            add_merge(p, mk(s + 5, d + 2, 0, 0, 2, R_ONE, 1.0));
+        }
+        if (hier) add_merge(p, mk(0, 5, 0, 0, 0, R_ONE, -1.0));   // direct g_delta joins W0' (coef -1 undone below)
+        else add_merge(p, mk(0, 3, 0, 0, 0, R_ONE, 1.0));         // own slot
+        CKL("y_fwd", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_fwd<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+    }
+    {
+        const int nslot = hier ? 6 : 4;
+        PassProgram p = program(cspec<T>(ctx, 13, nslot), mspec<T>(ctx, 0, 1), ctx->nspec);
+        add_merge(p, mk(0, 0, 2, 0, 0, R_INVK2, invn3));
+        add_merge(p, mk(1, 0, 1, 0, 0, R_INVK2, invn3));
+        add_merge(p, mk(2, 0, 0, 0, 0, R_INVK2, invn3));
+        if (hier) {
+            add_merge(p, mk(3, 0, 2, 0, 0, R_ONE, -invn3));
+            add_merge(p, mk(4, 0, 1, 0, 0, R_ONE, -invn3));
+            add_merge(p, mk(5, 0, 0, 0, 0, R_ONE, -invn3));
+        } else {
+            add_merge(p, mk(3, 0, 0, 0, 0, R_ONE, invn3));
+        }
+        add_expand(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));
+        CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+    }
+    RUN(y_identity<T>(ctx, 0, 1, false));
+    RUN(z_inv<T>(ctx, cspec<T>(ctx, 0, 1), mreal(ctx, RB_SCR, 1)));         // g_delta (total)
+    // CIC adjoint
+    CKL("cic_gather", 7 * rby<T>(ctx), launch_cic_gather<T>(ctx->n, ctx->B, RB<T>(ctx, RB_SCR), fields(ctx, RB_PSI, 3), fields(ctx, RB_SCR + 1, 3),
+                            ctx->stream));
+    // displacement adjoint
+    RUN(z_fwd<T>(ctx, creal(ctx, RB_SCR + 1, 3), mspec<T>(ctx, 0, 3)));
+    {
+        PassProgram p = program(cspec<T>(ctx, 0, 3), mspec<T>(ctx, 3, 2), ctx->nspec);
+        add_merge(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));
+        add_merge(p, mk(1, 1, 0, 1, 0, R_ONE, 1.0));
+        add_merge(p, mk(2, 1, 0, 0, 1, R_ONE, 1.0));
+        CKL("y_fwd", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_fwd<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+    }
+    {
+        PassProgram p = program(cspec<T>(ctx, 3, 2), mspec<T>(ctx, 5, 2), ctx->nspec);
+        const double c = invn3 / ctx->kp.dx;              // conj(-i/dx) = +i/dx
+        add_merge(p, mk(0, 0, 1, 0, 0, R_INVK2, 0.0, c));
+        add_merge(p, mk(1, 0, 0, 0, 0, R_INVK2, 0.0, c));
+        add_expand(p, mk(0, 0, 0, 0, 0, R_KBLEND, 1.0));
+        add_expand(p, mk(0, 1, 0, 0, 0, R_1MKBLEND, 1.0));
+        CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+    }
+    RUN(y_identity<T>(ctx, 5, 2, false));
+    RUN(z_inv<T>(ctx, cspec<T>(ctx, 5, 2), mreal(ctx, RB_SCR, 2)));          // g_a, g_b
+    {
+        const double D = ctx->cfg.growth_d, D2 = ctx->cfg.d2_over_d2 * D * D;
+        CKL("alpt_adj", 16 * rby<T>(ctx), launch_alpt_adjoint<T>(ctx->n, ctx->B, RB<T>(ctx, RB_SCR), RB<T>(ctx, RB_SCR + 1), fields(ctx, RB_ALPT, 7),
+                                  fields(ctx, RB_SCR + 2, 7), D, D2, ctx->stream));
+    }
+    RUN(z_fwd<T>(ctx, creal(ctx, RB_SCR + 2, 7), mspec<T>(ctx, 0, 7)));
+    {
+        PassProgram p = program(cspec<T>(ctx, 0, 7), mspec<T>(ctx, 7, 4), ctx->nspec);
+        add_merge(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));   // W0' <- g_delta0
+        add_merge(p, mk(1, 1, 0, 0, 0, R_ONE, 1.0));   // V2' <- g_phi_xx
+        add_merge(p, mk(2, 2, 0, 1, 0, R_ONE, 1.0));   // V1' <- ky g_phi_xy + kz g_phi_xz
+        add_merge(p, mk(3, 2, 0, 0, 1, R_ONE, 1.0));
+        add_merge(p, mk(4, 3, 0, 2, 0, R_ONE, 1.0));   // V0' <- ky^2 g_yy + ky kz g_yz + kz^2 g_zz
+        add_merge(p, mk(5, 3, 0, 1, 1, R_ONE, 1.0));
+        add_merge(p, mk(6, 3, 0, 0, 2, R_ONE, 1.0));
+        CKL("y_fwd", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_fwd<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+    }
+    {
+        PassProgram p = program(cspec<T>(ctx, 7, 4), mspec<T>(ctx, 0, 1), ctx->nspec);
+        add_merge(p, mk(0, 0, 0, 0, 0, R_ONE, invn3));
+        add_merge(p, mk(1, 0, 2, 0, 0, R_INVK2, invn3));
+        add_merge(p, mk(2, 0, 1, 0, 0, R_INVK2, invn3));
+        add_merge(p, mk(3, 0, 0, 0, 0, R_INVK2, invn3));
+        add_expand(p, mk(0, 0, 0, 0, 0, R_SQRTP, 1.0));
+        CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+    }
+    RUN(y_identity<T>(ctx, 0, 1, false));
+    RUN(z_inv<T>(ctx, cspec<T>(ctx, 0, 1), mreal(ctx, RB_SCR, 1)));
+    // white-noise prior: g_nu = (likelihood part) - nu
+    CKL("prior_grad", 3 * rby<T>(ctx), launch_sub<T>(ctx->nvox * ctx->B, RB<T>(ctx, RB_SCR), nu, grad, ctx->stream));
+    return BRIDGE_OK;
+}
+
+// Upload the bias tables of all chains and validate them.
+template <typename T> int upload_bias(bridge_ctx* ctx, const bridge_bias* bias) {
+    std::string why;
+    if (validate_bias(ctx, bias, &why) != BRIDGE_OK) return fail(ctx, BRIDGE_EINVAL, why);
+    BiasT<T>* bt = reinterpret_cast<BiasT<T>*>(ctx->biast_host);
+    for (int c = 0; c < ctx->B; ++c) {
+        BiasD& d = ctx->biasd_host[c];
+        std::memset(&d, 0, sizeof(d));
+        BiasT<T>& t = bt[c];
+        std::memset(&t, 0, sizeof(t));
+        for (int r = 0; r < 16; ++r) {
+            const bool on = r < ctx->nr;
+            d.a[r] = on ? bias[c].a[r] : 1.0; d.alpha[r] = on ? bias[c].alpha[r] : 0.0;
+            d.rho[r] = on ? bias[c].rho[r] : 1.0; d.eps[r] = on ? bias[c].eps[r] : 1.0;
+            d.rhop[r] = on ? bias[c].rhop[r] : 0.0; d.epsp[r] = on ? bias[c].epsp[r] : 1.0;
+            d.beta[r] = on ? bias[c].beta[r] : 1.0;
+            t.a[r] = T(d.a[r]); t.alpha[r] = T(d.alpha[r]); t.rho[r] = T(d.rho[r]); t.eps[r] = T(d.eps[r]);
+            t.rhop[r] = T(d.rhop[r]); t.epsp[r] = T(d.epsp[r]); t.beta[r] = T(d.beta[r]);
+        }
+        d.prior_mask = bias[c].prior_mask;
+        d.mu_alpha = bias[c].mu_alpha; d.sigma_alpha = bias[c].sigma_alpha;
+        d.mu_beta = bias[c].mu_beta; d.sigma_beta = bias[c].sigma_beta;
+    }
+    CK(cudaMemcpyAsync(ctx->biasd, ctx->biasd_host, sizeof(BiasD) * ctx->B, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->biast, ctx->biast_host, sizeof(BiasT<T>) * ctx->B, cudaMemcpyHostToDevice, ctx->stream));
+    return BRIDGE_OK;
+}
+
+template <typename T> int prep_counts(bridge_ctx* ctx, const int32_t* counts) {
+    if (!counts) return fail(ctx, BRIDGE_EINVAL, "counts is NULL");
+    CK(cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->stream));
+    CKL("counts_prep", 3 * c16b(ctx), launch_counts_prep<T>(ctx->n, ctx->B, counts, ctx->c16, ctx->partial, ctx->errflag, ctx->stream));
+    CKL("reduce", 0.0, launch_reduce(RED_NTR, ctx->n, ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+    return BRIDGE_OK;
+}
+
+// Synchronise, fetch scalars and the count-range flag.
+int finish(bridge_ctx* ctx) {
+    cudaError_t e = cudaMemcpyAsync(ctx->sc_host, ctx->sc, sizeof(ChainScalars) * ctx->B, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->errflag_host, ctx->errflag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, BRIDGE_ECUDA, std::string("synchronise: ") + cudaGetErrorString(e));
+    if (*ctx->errflag_host) return fail(ctx, BRIDGE_EINVAL, "counts outside [0, 65535]");
+    return BRIDGE_OK;
+}
+
+template <typename T> int do_forward(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
+                                     void* ln_nbar_out, double* logpost_out) {
+    if (!nu) return fail(ctx, BRIDGE_EINVAL, "nu is NULL");
+    RUN(upload_bias<T>(ctx, bias));
+    RUN(prep_counts<T>(ctx, counts));
+    RUN(run_forward<T>(ctx, reinterpret_cast<const T*>(nu), true));
+    if (ln_nbar_out)
+        CKL("lnnbar", 2 * rby<T>(ctx), launch_lnnbar<T>(ctx->nvox, ctx->B, RB<T>(ctx, RB_SCR), ctx->sc, reinterpret_cast<T*>(ln_nbar_out), ctx->stream));
+    RUN(finish(ctx));
+    for (int c = 0; c < ctx->B; ++c) {
+        if (!std::isfinite(ctx->sc_host[c].logpost)) return fail(ctx, BRIDGE_ENONFINITE, "log posterior is not finite");
+        if (logpost_out) logpost_out[c] = ctx->sc_host[c].logpost;
+    }
+    return BRIDGE_OK;
+}
+
+template <typename T> int do_grad(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
+                                  double* logpost_out, void* grad, double* gbias_out) {
+    if (!nu || !grad) return fail(ctx, BRIDGE_EINVAL, "nu and grad_nu_out are required");
+    RUN(upload_bias<T>(ctx, bias));
+    RUN(prep_counts<T>(ctx, counts));
+    RUN(run_forward<T>(ctx, reinterpret_cast<const T*>(nu), true));
+    RUN(run_adjoint<T>(ctx, reinterpret_cast<const T*>(nu), reinterpret_cast<T*>(grad)));
+    RUN(finish(ctx));
+    for (int c = 0; c < ctx->B; ++c) {
+        if (!std::isfinite(ctx->sc_host[c].logpost)) return fail(ctx, BRIDGE_ENONFINITE, "log posterior is not finite");
+        if (logpost_out) logpost_out[c] = ctx->sc_host[c].logpost;
+        if (gbias_out)
+            for (int k = 0; k < 2 * ctx->nr; ++k) gbias_out[c * 2 * ctx->nr + k] = ctx->sc_host[c].gbias[k];
+    }
+    return BRIDGE_OK;
+}
+
+template <typename T> int do_leapfrog(bridge_ctx* ctx, void* nu_v, void* p_v, const int32_t* counts,
+                                      const bridge_bias* bias, int n_steps, double eps, double* h0, double* h1) {
+    if (!nu_v || !p_v) return fail(ctx, BRIDGE_EINVAL, "nu and p are required");
+    if (n_steps < 1 || !std::isfinite(eps)) return fail(ctx, BRIDGE_EINVAL, "n_steps >= 1 and finite eps required");
+    T* nu = reinterpret_cast<T*>(nu_v);
+    T* p = reinterpret_cast<T*>(p_v);
+    T* g = reinterpret_cast<T*>(ctx->grad_tmp);
+    RUN(upload_bias<T>(ctx, bias));
+    RUN(prep_counts<T>(ctx, counts));
+    std::vector<double> u0(ctx->B), k0(ctx->B);
+    // initial potential and kinetic energy
+    RUN(run_forward<T>(ctx, nu, true));
+    RUN(run_adjoint<T>(ctx, nu, g));
+    CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, 0.0, 0.0, ctx->partial, ctx->stream));
+    CKL("reduce", 0.0, launch_reduce(RED_P2, ctx->n, ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+    RUN(finish(ctx));
+    for (int c = 0; c < ctx->B; ++c) { u0[c] = -ctx->sc_host[c].logpost; k0[c] = 0.5 * ctx->sc_host[c].sump2; }
+    // first half kick + drift, then (gradient, full kick + drift) ..., final half kick
+    CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, 0.5 * eps, eps, ctx->partial, ctx->stream));
+    for (int s = 0; s < n_steps; ++s) {
+        RUN(run_forward<T>(ctx, nu, true));
+        RUN(run_adjoint<T>(ctx, nu, g));
+        const bool last = s == n_steps - 1;
+        CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, last ? 0.5 * eps : eps, last ? 0.0 : eps, ctx->partial,
+                                ctx->stream));
+    }
+    CKL("reduce", 0.0, launch_reduce(RED_P2, ctx->n, ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+    RUN(finish(ctx));
+    for (int c = 0; c < ctx->B; ++c) {
+        const double H0 = u0[c] + k0[c];
+        const double H1 = -ctx->sc_host[c].logpost + 0.5 * ctx->sc_host[c].sump2;
+        if (!std::isfinite(H0) || !std::isfinite(H1)) return fail(ctx, BRIDGE_ENONFINITE, "Hamiltonian is not finite");
+        if (h0) h0[c] = H0;
+        if (h1) h1[c] = H1;
+    }
+    return BRIDGE_OK;
+}
+
+template <typename T> int do_debug(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
+                                   int which, void* out) {
+    if (!nu || !out) return fail(ctx, BRIDGE_EINVAL, "nu and out are required");
+    RUN(upload_bias<T>(ctx, bias));
+    RUN(prep_counts<T>(ctx, counts));
+    RUN(run_forward<T>(ctx, reinterpret_cast<const T*>(nu), true));
+    const size_t fb = size_t(ctx->nvox) * ctx->B * sizeof(T), one = size_t(ctx->nvox) * sizeof(T);
+    auto copy_fields = [&](int first, int count) -> int {
+        // out layout [B][count][N^3]; workspace layout [field][B][N^3]
+        for (int c = 0; c < ctx->B; ++c)
+            for (int f = 0; f < count; ++f)
+                CK(cudaMemcpyAsync(reinterpret_cast<char*>(out) + (size_t(c) * count + f) * one,
+                                   reinterpret_cast<const char*>(ctx->real[first + f]) + size_t(c) * one, one,
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+        return BRIDGE_OK;
+    };
+    (void)fb;
+    switch (which) {
+        case BRIDGE_FIELD_DELTA0: RUN(copy_fields(RB_ALPT, 1)); break;
+        case BRIDGE_FIELD_PSI: RUN(copy_fields(RB_PSI, 3)); break;
+        case BRIDGE_FIELD_DELTA: RUN(copy_fields(RB_DELTA, 1)); break;
+        case BRIDGE_FIELD_TIDAL: RUN(copy_fields(RB_TH, 6)); break;
+        case BRIDGE_FIELD_HESSIAN:
+            if (ctx->nr != 16) return fail(ctx, BRIDGE_EINVAL, "the density Hessian exists only for 16 regions");
+            RUN(copy_fields(RB_TH + 6, 6));
+            break;
+        case BRIDGE_FIELD_LAMBDA:
+            CKL("eigs", 9 * rby<T>(ctx), launch_eigs<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 6), fields(ctx, RB_SCR + 2, 3), ctx->stream));
+            RUN(copy_fields(RB_SCR + 2, 3));
+            break;
+        case BRIDGE_FIELD_LNNBAR:
+            CKL("lnnbar", 2 * rby<T>(ctx), launch_lnnbar<T>(ctx->nvox, ctx->B, RB<T>(ctx, RB_SCR), ctx->sc, RB<T>(ctx, RB_SCR + 2), ctx->stream));
+            RUN(copy_fields(RB_SCR + 2, 1));
+            break;
+        default: return fail(ctx, BRIDGE_EINVAL, "unknown field selector");
+    }
+    return finish(ctx);
+}
+
+// Simpson in ln k of k^3 P(k) W(kR)^2 / (2 pi^2).
+double tophat(double x) {
+    if (std::fabs(x) < 1e-3) return 1.0 - x * x / 10.0 + x * x * x * x / 280.0;
+    return 3.0 * (std::sin(x) - x * std::cos(x)) / (x * x * x);
+}
+double sigma2_unit(double R, double ns, double kc, double pw) {
+    const int M = 1 << 16;
+    const double a = std::log(1e-8), b = std::log(1e3 / R), h = (b - a) / M;
+    double s = 0.0;
+    for (int i = 0; i <= M; ++i) {
+        const double k = std::exp(a + i * h);
+        const double pk = std::pow(k, ns) / std::pow(1.0 + (k / kc) * (k / kc), pw);
+        const double w = tophat(k * R);
+        const double f = k * k * k * pk * w * w;
+        s += f * ((i == 0 || i == M) ? 1.0 : (i % 2 ? 4.0 : 2.0));
+    }
+    return s * h / 3.0 / (2.0 * kPi * kPi);
+}
+
+}  // namespace
+
+#define DISPATCH(ctx, fn, ...) \
+    ((ctx)->cfg.precision == BRIDGE_FP64 ? fn<double>(ctx, __VA_ARGS__) : fn<float>(ctx, __VA_ARGS__))
+
+extern "C" {
+
+int bridge_validate_config(const bridge_config* cfg) { return validate(cfg, nullptr); }
+
+size_t bridge_workspace_bytes(const bridge_config* cfg) {
+    if (validate(cfg, nullptr) != BRIDGE_OK) return 0;
+    return make_plan(cfg).total;
+}
+
+double bridge_pk_amplitude(double sigma, double radius, double ns, double kc, double pw) {
+    if (!(sigma > 0) || !(radius > 0) || !(kc > 0) || !std::isfinite(ns) || !std::isfinite(pw)) return -1.0;
+    const double s2 = sigma2_unit(radius, ns, kc, pw);
+    if (!(s2 > 0) || !std::isfinite(s2)) return -1.0;
+    return sigma * sigma / s2;
+}
+
+int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
+    if (!out) return BRIDGE_EINVAL;
+    std::string why;
+    if (validate(cfg, &why) != BRIDGE_OK) return BRIDGE_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return BRIDGE_ENODEVICE;
+    bridge_ctx* ctx = new bridge_ctx();
+    ctx->cfg = *cfg;
+    ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+    cudaGetDevice(&ctx->device);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess || prop.major != 10 || prop.minor != 3) {
+        delete ctx;
+        return BRIDGE_ENODEVICE;
+    }
+    ctx->n = cfg->n;
+    ctx->B = cfg->batch;
+    ctx->nr = cfg->n_regions;
+    ctx->nvox = (long long)cfg->n * cfg->n * cfg->n;
+    ctx->nspec = (long long)(cfg->n / 2 + 1) * cfg->n * cfg->n;
+    ctx->esz = cfg->precision == BRIDGE_FP64 ? 8 : 4;
+    ctx->kp.kf = 2.0 * kPi / cfg->box;
+    ctx->kp.dx = cfg->box / cfg->n;
+    ctx->kp.pk_amp = cfg->pk_amp; ctx->kp.pk_ns = cfg->pk_ns; ctx->kp.pk_kc = cfg->pk_kc; ctx->kp.pk_pow = cfg->pk_pow;
+    ctx->kp.r_s = cfg->r_s;
+    ctx->wp.sharpness = cfg->sharpness;
+    ctx->wp.th_phi = cfg->lambda_th_phi;
+    ctx->wp.th_delta = cfg->lambda_th_delta;
+    ctx->wp.rho_floor = cfg->rho_floor;
+    ctx->wp.tau = cfg->precision == BRIDGE_FP64 ? 1e-10 : 1e-4;
+    ctx->wp.n_regions = cfg->n_regions;
+    if (upload_twiddles() != cudaSuccess) { delete ctx; return BRIDGE_ECUDA; }
+    const Plan pl = make_plan(cfg);
+    if (cudaMalloc(&ctx->ws, pl.total) != cudaSuccess) { cudaGetLastError(); delete ctx; return BRIDGE_ENOMEM; }
+    ctx->ws_bytes = pl.total;
+    char* w = reinterpret_cast<char*>(align_up(reinterpret_cast<size_t>(ctx->ws)));
+    for (int i = 0; i < pl.nspec_buf; ++i) { ctx->spec[i] = w; w += pl.spec_bytes; }
+    for (int i = 0; i < pl.nreal_buf; ++i) { ctx->real[i] = w; w += pl.real_bytes; }
+    ctx->grad_tmp = w; w += pl.real_bytes;
+    ctx->c16 = reinterpret_cast<uint16_t*>(w); w += pl.c16_bytes;
+    ctx->partial = reinterpret_cast<double*>(w); w += pl.partial_bytes;
+    ctx->sc = reinterpret_cast<ChainScalars*>(w); w += pl.sc_bytes;
+    ctx->biasd = reinterpret_cast<BiasD*>(w); w += pl.biasd_bytes;
+    ctx->biast = w; w += pl.biast_bytes;
+    if (cudaMalloc(&ctx->errflag, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&ctx->sc_host, sizeof(ChainScalars) * ctx->B) != cudaSuccess ||
+        cudaMallocHost(&ctx->biasd_host, sizeof(BiasD) * ctx->B) != cudaSuccess ||
+        cudaMallocHost(&ctx->biast_host, sizeof(BiasT<double>) * ctx->B) != cudaSuccess ||
+        cudaMallocHost(&ctx->errflag_host, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        bridge_destroy(ctx);
+        return BRIDGE_ENOMEM;
+    }
+    if (cudaMemsetAsync(ctx->ws, 0, pl.total, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        bridge_destroy(ctx);
+        return BRIDGE_ECUDA;
+    }
+    *out = ctx;
+    return BRIDGE_OK;
+}
+
+void bridge_destroy(bridge_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->stream || ctx->ws) cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->errflag) cudaFree(ctx->errflag);
+    if (ctx->h_nu) cudaFree(ctx->h_nu);
+    if (ctx->h_counts) cudaFree(ctx->h_counts);
+    if (ctx->h_grad) cudaFree(ctx->h_grad);
+    if (ctx->sc_host) cudaFreeHost(ctx->sc_host);
+    if (ctx->biasd_host) cudaFreeHost(ctx->biasd_host);
+    if (ctx->biast_host) cudaFreeHost(ctx->biast_host);
+    if (ctx->errflag_host) cudaFreeHost(ctx->errflag_host);
+    for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+    delete ctx;
+}
+
+int bridge_forward(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
+                   void* ln_nbar_out, double* logpost_out) {
+    if (!ctx) return BRIDGE_EINVAL;
+    ctx->launches = 0;
+    ctx->err.clear();
+    return DISPATCH(ctx, do_forward, nu, counts, bias, ln_nbar_out, logpost_out);
+}
+
+int bridge_logpost_grad(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
+                        double* logpost_out, void* grad_nu_out, double* grad_bias_out) {
+    if (!ctx) return BRIDGE_EINVAL;
+    ctx->launches = 0;
+    ctx->err.clear();
+    return DISPATCH(ctx, do_grad, nu, counts, bias, logpost_out, grad_nu_out, grad_bias_out);
+}
+
+int bridge_logpost_grad_host(bridge_ctx* ctx, const void* nu_host, const int32_t* counts_host, const bridge_bias* bias,
+                             double* logpost_out, void* grad_nu_host, double* grad_bias_out) {
+    if (!ctx) return BRIDGE_EINVAL;
+    ctx->launches = 0;
+    ctx->err.clear();
+    if (!nu_host || !counts_host || !grad_nu_host) return fail(ctx, BRIDGE_EINVAL, "host buffers are required");
+    const size_t fb = size_t(ctx->nvox) * ctx->B * ctx->esz, cb = size_t(ctx->nvox) * ctx->B * sizeof(int32_t);
+    if (!ctx->h_nu) {
+        if (cudaMalloc(&ctx->h_nu, fb) != cudaSuccess || cudaMalloc(&ctx->h_counts, cb) != cudaSuccess ||
+            cudaMalloc(&ctx->h_grad, fb) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, BRIDGE_ENOMEM, "device staging for host buffers");
+        }
+    }
+    CK(cudaMemcpyAsync(ctx->h_nu, nu_host, fb, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_counts, counts_host, cb, cudaMemcpyHostToDevice, ctx->stream));
+    int st = DISPATCH(ctx, do_grad, ctx->h_nu, ctx->h_counts, bias, logpost_out, ctx->h_grad, grad_bias_out);
+    if (st != BRIDGE_OK) return st;
+    CK(cudaMemcpyAsync(grad_nu_host, ctx->h_grad, fb, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return BRIDGE_OK;
+}
+
+int bridge_leapfrog(bridge_ctx* ctx, void* nu, void* p, const int32_t* counts, const bridge_bias* bias, int32_t n_steps,
+                    double eps, double* h0_out, double* h1_out) {
+    if (!ctx) return BRIDGE_EINVAL;
+    ctx->launches = 0;
+    ctx->err.clear();
+    return DISPATCH(ctx, do_leapfrog, nu, p, counts, bias, n_steps, eps, h0_out, h1_out);
+}
+
+int bridge_debug_field(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias, int32_t which,
+                       void* out) {
+    if (!ctx) return BRIDGE_EINVAL;
+    ctx->launches = 0;
+    ctx->err.clear();
+    return DISPATCH(ctx, do_debug, nu, counts, bias, which, out);
+}
+
+int64_t bridge_last_launch_count(const bridge_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int bridge_profile_enable(bridge_ctx* ctx, int enable) {
+    if (!ctx) return BRIDGE_EINVAL;
+    ctx->prof = enable != 0;
+    ctx->prof_recs.clear();
+    ctx->prof_used = 0;
+    return BRIDGE_OK;
+}
+
+int bridge_profile_read(bridge_ctx* ctx, bridge_profile_row* rows, int max_rows) {
+    if (!ctx || (!rows && max_rows > 0)) return -BRIDGE_EINVAL;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return -BRIDGE_ECUDA;
+    std::vector<bridge_profile_row> agg;
+    for (const auto& r : ctx->prof_recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return -BRIDGE_ECUDA;
+        size_t i = 0;
+        while (i < agg.size() && std::strcmp(agg[i].name, r.name) != 0) ++i;
+        if (i == agg.size()) {
+            bridge_profile_row z{};
+            std::snprintf(z.name, sizeof(z.name), "%s", r.name);
+            agg.push_back(z);
+        }
+        agg[i].launches += 1;
+        agg[i].total_ms += ms;
+        agg[i].bytes += r.bytes;
+    }
+    const int n = (int)agg.size() < max_rows ? (int)agg.size() : max_rows;
+    for (int i = 0; i < n; ++i) rows[i] = agg[i];
+    return n;
+}
+
+const char* bridge_last_error(const bridge_ctx* ctx) { return ctx ? ctx->err.c_str() : "context is NULL"; }
+
+const char* bridge_status_string(int s) {
+    switch (s) {
+        case BRIDGE_OK: return "ok";
+        case BRIDGE_EINVAL: return "invalid argument";
+        case BRIDGE_ENOMEM: return "out of memory";
+        case BRIDGE_ECUDA: return "CUDA error";
+        case BRIDGE_ENONFINITE: return "non-finite result";
+        case BRIDGE_ETIMEOUT: return "device wait timed out";
+        case BRIDGE_ENODEVICE: return "no suitable CUDA device";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

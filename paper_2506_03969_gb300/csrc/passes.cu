@@ -1,0 +1,620 @@
+// FFT pass kernels: the 3D real<->complex DFT of the forward model is split into
+// three passes over HBM, with the k-space operators of the method fused in.
+//
+//   z pass : real [x][y][z] <-> half spectrum in [kz][y][x] order.  Two real
+//            z lines are packed as one complex line (a + i b), transformed with
+//            an N-point complex DFT and separated by Hermitian symmetry.
+//   y pass : complex DFT along y on [kz][ky][x]; monomial multipliers ky^p kz^q
+//            can expand one input into several outputs (inverse direction) or
+//            merge several inputs into one output (forward direction).
+//   x node : forward DFT along x (all of k is then known), merge the inputs into
+//            one scalar spectrum Q with k-space operators, expand Q into the
+//            outputs with further operators, inverse DFT along x.
+//
+// Each 1D DFT uses the four-step split N = N1 * N2: N1-point register DFTs
+// (step A), twiddles, a shared-memory transpose, N2-point register DFTs
+// (step B).  All global accesses of a warp are contiguous runs of >= 64 bytes.
+#include <cmath>
+#include <cstdio>
+#include <type_traits>
+
+#include "common.cuh"
+#include "passes.cuh"
+
+namespace bridge {
+
+// Twiddle tables: entry N + j holds exp(-2 pi i j / N) for N = 2..512.
+constexpr int kTwTable = 1024;
+__device__ float2 g_tw_f[kTwTable];
+__device__ double2 g_tw_d[kTwTable];
+template <typename T> __device__ __forceinline__ cplx_t<T> tw_load(int N, int j);
+template <> __device__ __forceinline__ float2 tw_load<float>(int N, int j) { return __ldg(&g_tw_f[N + j]); }
+template <> __device__ __forceinline__ double2 tw_load<double>(int N, int j) { return __ldg(&g_tw_d[N + j]); }
+
+cudaError_t upload_twiddles() {
+    static float2 hf[kTwTable];
+    static double2 hd[kTwTable];
+    for (int n = 2; n <= 512; n *= 2) {
+        for (int j = 0; j < n; ++j) {
+            const double a = -2.0 * kPi * double(j) / double(n);
+            hd[n + j] = make_double2(std::cos(a), std::sin(a));
+            hf[n + j] = make_float2(float(std::cos(a)), float(std::sin(a)));
+        }
+    }
+    cudaError_t e = cudaMemcpyToSymbol(g_tw_f, hf, sizeof(hf));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(g_tw_d, hd, sizeof(hd));
+}
+
+// ---------------------------------------------------------------------------
+// Multipliers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float m_pow(float x, float y) { return powf(x, y); }
+__device__ __forceinline__ double m_pow(double x, double y) { return pow(x, y); }
+__device__ __forceinline__ float m_exp(float x) { return expf(x); }
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
+
+// k_axis^p for signed index m; odd powers vanish on the Nyquist index.
+template <typename T> __device__ __forceinline__ T kpow(int m, int p, int n, T kf) {
+    if (p == 0) return T(1);
+    if ((p & 1) && (m == n / 2 || m == -(n / 2))) return T(0);
+    const T k = kf * T(m);
+    return p == 1 ? k : (p == 2 ? k * k : k * k * k);
+}
+
+template <typename T> __device__ __forceinline__ T radial(int code, T k2, const KParams& kp) {
+    switch (code) {
+        case R_INVK2: return k2 > T(0) ? T(1) / k2 : T(0);
+        case R_SQRTP: {
+            // sqrt(P(k)/dx^3), P = A k^ns / (1 + (k/kc)^2)^pow, P(0) = 0   (App. A)
+            if (k2 <= T(0)) return T(0);
+            const T a = T(m_sqrt(kp.pk_amp / (kp.dx * kp.dx * kp.dx)));
+            const T kc2 = T(kp.pk_kc * kp.pk_kc);
+            return a * m_pow(k2, T(0.25 * kp.pk_ns)) * m_pow(T(1) + k2 / kc2, T(-0.5 * kp.pk_pow));
+        }
+        case R_KBLEND: return m_exp(T(-0.5 * kp.r_s * kp.r_s) * k2);             // K(k), Sect. 2.3
+        case R_1MKBLEND: return -m_expm1(T(-0.5 * kp.r_s * kp.r_s) * k2);        // 1 - K(k)
+        default: return T(1);
+    }
+}
+
+template <typename T, bool RADIAL>
+__device__ __forceinline__ cplx_t<T> term_mult(const Term& tm, int mx, int my, int mz, int n, const KParams& kp) {
+    const T kf = T(kp.kf);
+    T r = kpow<T>(mx, tm.px, n, kf) * kpow<T>(my, tm.py, n, kf) * kpow<T>(mz, tm.pz, n, kf);
+    if (RADIAL && tm.rcode != R_ONE) {
+        const T k2 = kf * kf * T(mx * mx + my * my + mz * mz);
+        r *= radial<T>(tm.rcode, k2, kp);
+    }
+    return cmake<cplx_t<T>>(T(tm.cre) * r, T(tm.cim) * r);
+}
+
+// ---------------------------------------------------------------------------
+// Column tiles for the y pass (XM = false, lines strided by N) and the x node
+// (XM = true, lines contiguous).  Spectra are [kz][ky or y][x] with N*N
+// elements per kz plane and N/2+1 planes.
+// ---------------------------------------------------------------------------
+template <typename T, int N, bool XM> struct Tile {
+    using V = cplx_t<T>;
+    static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, J = N1 / N2;
+    static constexpr int GY0 = (int)(128 / sizeof(V)) > 256 / N2 ? (int)(128 / sizeof(V)) : 256 / N2;
+    static constexpr int GX0 = (sizeof(V) == 8 ? 256 : 128) / N2;
+    static constexpr int G0 = XM ? GX0 : GY0;
+    static constexpr int G = G0 < N ? G0 : N;
+    static constexpr int NT = G * N2;
+    static constexpr int SM_ELEMS = XM ? G * N1 * (N2 + 1) : N * G;
+    static constexpr int TILES_PER_PLANE = N / G;
+    static constexpr int TILES = (N / 2 + 1) * TILES_PER_PLANE;
+
+    __device__ static void tile_pos(int tile, int& kz, int& c0) {
+        kz = tile / TILES_PER_PLANE;
+        c0 = (tile % TILES_PER_PLANE) * G;
+    }
+    __device__ static size_t tile_base(int kz, int c0) {
+        return size_t(kz) * N * N + (XM ? size_t(c0) * N : size_t(c0));
+    }
+    __device__ static int goff(int n, int g) { return XM ? g * N + n : n * N + g; }
+    __device__ static int a_g(int t) { return XM ? t / N2 : t % G; }
+    __device__ static int a_n2(int t) { return XM ? t % N2 : t / G; }
+    __device__ static int b_g(int t) { return XM ? t / N2 : t % G; }
+    __device__ static int b_k1(int t, int j) { return (XM ? t % N2 : t / G) + j * N2; }
+    __device__ static int sidx(int g, int k1, int n2) {
+        return XM ? g * (N1 * (N2 + 1)) + k1 * (N2 + 1) + n2 : (k1 * N2 + n2) * G + g;
+    }
+    // signed frequencies of element (n, g) of a tile at (kz, c0)
+    __device__ static void freqs(int n, int g, int kz, int c0, int& mx, int& my, int& mz) {
+        mz = kz;
+        if (XM) { mx = signed_freq(n, N); my = signed_freq(c0 + g, N); }
+        else { mx = 0; my = signed_freq(n, N); }
+    }
+
+    // forward step A from global (A layout) into shared memory (twiddled)
+    __device__ static void fwdA(const V* __restrict__ src, V* sm, int t) {
+        const int g = a_g(t), n2 = a_n2(t);
+        V v[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) v[n1] = src[goff(N2 * n1 + n2, g)];
+        dft_dif<N1, 1, -1>(v);
+#pragma unroll
+        for (int i = 0; i < N1; ++i) {
+            const int k1 = bitrev(i, N1);
+            sm[sidx(g, k1, n2)] = cmul(v[i], tw_load<T>(N, n2 * k1));
+        }
+    }
+    // forward step B: X[j][i] = DFT value at k = k1_j + N1 * bitrev(i)
+    __device__ static void fwdB(const V* sm, int t, V (&X)[J][N2]) {
+        const int g = b_g(t);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int k1 = b_k1(t, j);
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) X[j][n2] = sm[sidx(g, k1, n2)];
+            dft_dif<N2, 1, -1>(X[j]);
+        }
+    }
+    // inverse step B' from natural-order registers Y[j][k2] (k = k1_j + N1 k2)
+    __device__ static void invB(V (&Y)[J][N2], V* sm, int t) {
+        const int g = b_g(t);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int k1 = b_k1(t, j);
+            dft_dif<N2, 1, +1>(Y[j]);
+#pragma unroll
+            for (int i = 0; i < N2; ++i) {
+                const int n2 = bitrev(i, N2);
+                sm[sidx(g, k1, n2)] = cmulc(Y[j][i], tw_load<T>(N, n2 * k1));
+            }
+        }
+    }
+    // inverse step A' to global (A layout)
+    __device__ static void invA(const V* sm, V* __restrict__ dst, int t) {
+        const int g = a_g(t), n2 = a_n2(t);
+        V v[N1];
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) v[k1] = sm[sidx(g, k1, n2)];
+        dft_dif<N1, 1, +1>(v);
+#pragma unroll
+        for (int i = 0; i < N1; ++i) dst[goff(n2 + N2 * bitrev(i, N1), g)] = v[i];
+    }
+};
+
+// Forward (merge) column pass: out[o] = sum_{terms -> o} mult * DFT(in[src])
+template <typename T, int N, bool XM>
+__global__ void __launch_bounds__(Tile<T, N, XM>::NT) k_col_fwd(const PassProgram P, const KParams kp) {
+    using TL = Tile<T, N, XM>;
+    using V = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* sm = reinterpret_cast<V*>(smraw);
+    const int t = threadIdx.x, chain = blockIdx.y;
+    int kz, c0;
+    TL::tile_pos(blockIdx.x, kz, c0);
+    const size_t base = TL::tile_base(kz, c0);
+    const int g = TL::b_g(t);
+    for (int o = 0; o < P.n_out; ++o) {
+        V acc[TL::J][TL::N2];
+#pragma unroll
+        for (int j = 0; j < TL::J; ++j)
+#pragma unroll
+            for (int i = 0; i < TL::N2; ++i) acc[j][i] = cmake<V>(T(0), T(0));
+        for (int m = 0; m < P.n_merge; ++m) {
+            const Term tm = P.merge[m];
+            if (tm.dst != o) continue;
+            const V* src = reinterpret_cast<const V*>(P.in[tm.src]) + chain * P.in_cs + base;
+            __syncthreads();
+            TL::fwdA(src, sm, t);
+            __syncthreads();
+            V X[TL::J][TL::N2];
+            TL::fwdB(sm, t, X);
+#pragma unroll
+            for (int j = 0; j < TL::J; ++j) {
+                const int k1 = TL::b_k1(t, j);
+#pragma unroll
+                for (int i = 0; i < TL::N2; ++i) {
+                    int mx, my, mz;
+                    TL::freqs(k1 + TL::N1 * bitrev(i, TL::N2), g, kz, c0, mx, my, mz);
+                    acc[j][i] = cadd(acc[j][i], cmul(term_mult<T, XM>(tm, mx, my, mz, N, kp), X[j][i]));
+                }
+            }
+        }
+        V* dst = reinterpret_cast<V*>(P.out[o]) + chain * P.out_cs + base;
+#pragma unroll
+        for (int j = 0; j < TL::J; ++j) {
+            const int k1 = TL::b_k1(t, j);
+#pragma unroll
+            for (int i = 0; i < TL::N2; ++i) dst[TL::goff(k1 + TL::N1 * bitrev(i, TL::N2), g)] = acc[j][i];
+        }
+    }
+}
+
+// Inverse (expand) column pass: out[dst] = IDFT(mult * in[src]) for each term.
+template <typename T, int N, bool XM>
+__global__ void __launch_bounds__(Tile<T, N, XM>::NT) k_col_inv(const PassProgram P, const KParams kp) {
+    using TL = Tile<T, N, XM>;
+    using V = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* sm = reinterpret_cast<V*>(smraw);
+    const int t = threadIdx.x, chain = blockIdx.y;
+    int kz, c0;
+    TL::tile_pos(blockIdx.x, kz, c0);
+    const size_t base = TL::tile_base(kz, c0);
+    const int g = TL::b_g(t);
+    for (int s = 0; s < P.n_in; ++s) {
+        bool used = false;
+        for (int m = 0; m < P.n_expand; ++m) used |= (P.expand[m].src == s);
+        if (!used) continue;
+        const V* src = reinterpret_cast<const V*>(P.in[s]) + chain * P.in_cs + base;
+        V X[TL::J][TL::N2];
+#pragma unroll
+        for (int j = 0; j < TL::J; ++j) {
+            const int k1 = TL::b_k1(t, j);
+#pragma unroll
+            for (int k2 = 0; k2 < TL::N2; ++k2) X[j][k2] = src[TL::goff(k1 + TL::N1 * k2, g)];
+        }
+        for (int m = 0; m < P.n_expand; ++m) {
+            const Term tm = P.expand[m];
+            if (tm.src != s) continue;
+            V Y[TL::J][TL::N2];
+#pragma unroll
+            for (int j = 0; j < TL::J; ++j) {
+                const int k1 = TL::b_k1(t, j);
+#pragma unroll
+                for (int k2 = 0; k2 < TL::N2; ++k2) {
+                    int mx, my, mz;
+                    TL::freqs(k1 + TL::N1 * k2, g, kz, c0, mx, my, mz);
+                    Y[j][k2] = cmul(term_mult<T, XM>(tm, mx, my, mz, N, kp), X[j][k2]);
+                }
+            }
+            __syncthreads();
+            TL::invB(Y, sm, t);
+            __syncthreads();
+            V* dst = reinterpret_cast<V*>(P.out[tm.dst]) + chain * P.out_cs + base;
+            TL::invA(sm, dst, t);
+        }
+    }
+}
+
+// x node: Q = sum_merge mult * DFTx(in[src]);  out[dst] = IDFTx(mult * Q).
+// The transcendental radial factors (sqrt P, K, 1 - K) of the tile are
+// tabulated once in shared memory (at most two codes per program) so the
+// unrolled register DFT code only reads them.
+template <typename T, int N>
+__device__ __forceinline__ cplx_t<T> xnode_mult(const Term& tm, int mx, int my, int mz, const KParams& kp,
+                                                 const T* tab, const int8_t* slot_of, int e) {
+    const T kf = T(kp.kf);
+    T r = kpow<T>(mx, tm.px, N, kf) * kpow<T>(my, tm.py, N, kf) * kpow<T>(mz, tm.pz, N, kf);
+    if (tm.rcode == R_INVK2) {
+        const int m2 = mx * mx + my * my + mz * mz;
+        r = m2 > 0 ? r / (kf * kf * T(m2)) : T(0);
+    } else if (tm.rcode != R_ONE) {
+        r *= tab[slot_of[tm.rcode] * (Tile<T, N, true>::G * N) + e];
+    }
+    return cmake<cplx_t<T>>(T(tm.cre) * r, T(tm.cim) * r);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(Tile<T, N, true>::NT) k_x_node(const PassProgram P, const KParams kp) {
+    using TL = Tile<T, N, true>;
+    using V = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* sm = reinterpret_cast<V*>(smraw);
+    T* tab = reinterpret_cast<T*>(sm + TL::SM_ELEMS);      // [2][G*N]
+    __shared__ int8_t slot_of[8];
+    const int t = threadIdx.x, chain = blockIdx.y;
+    int kz, c0;
+    TL::tile_pos(blockIdx.x, kz, c0);
+    const size_t base = TL::tile_base(kz, c0);
+    const int g = TL::b_g(t);
+    // radial tables
+    {
+        int codes[2] = {-1, -1}, nc = 0;
+        for (int m = 0; m < P.n_merge + P.n_expand; ++m) {
+            const int c = m < P.n_merge ? P.merge[m].rcode : P.expand[m - P.n_merge].rcode;
+            if (c == R_ONE || c == R_INVK2) continue;
+            if (c != codes[0] && c != codes[1] && nc < 2) codes[nc++] = c;
+        }
+        if (t < 8) slot_of[t] = (t == codes[0]) ? 0 : ((t == codes[1]) ? 1 : 0);
+        const T kf = T(kp.kf);
+        for (int s = 0; s < nc; ++s)
+            for (int e = t; e < TL::G * N; e += TL::NT) {
+                const int mx = signed_freq(e % N, N), my = signed_freq(c0 + e / N, N);
+                const T k2 = kf * kf * T(mx * mx + my * my + kz * kz);
+                tab[s * (TL::G * N) + e] = radial<T>(codes[s], k2, kp);
+            }
+        __syncthreads();
+    }
+    V Q[TL::J][TL::N2];   // bit-reversed k2 order
+#pragma unroll
+    for (int j = 0; j < TL::J; ++j)
+#pragma unroll
+        for (int i = 0; i < TL::N2; ++i) Q[j][i] = cmake<V>(T(0), T(0));
+    for (int m = 0; m < P.n_merge; ++m) {
+        const Term tm = P.merge[m];
+        const V* src = reinterpret_cast<const V*>(P.in[tm.src]) + chain * P.in_cs + base;
+        __syncthreads();
+        TL::fwdA(src, sm, t);
+        __syncthreads();
+        V X[TL::J][TL::N2];
+        TL::fwdB(sm, t, X);
+#pragma unroll
+        for (int j = 0; j < TL::J; ++j) {
+            const int k1 = TL::b_k1(t, j);
+#pragma unroll
+            for (int i = 0; i < TL::N2; ++i) {
+                const int n = k1 + TL::N1 * bitrev(i, TL::N2);
+                int mx, my, mz;
+                TL::freqs(n, g, kz, c0, mx, my, mz);
+                Q[j][i] = cadd(Q[j][i], cmul(xnode_mult<T, N>(tm, mx, my, mz, kp, tab, slot_of, g * N + n), X[j][i]));
+            }
+        }
+    }
+    for (int m = 0; m < P.n_expand; ++m) {
+        const Term tm = P.expand[m];
+        V Y[TL::J][TL::N2];   // natural k2 order
+#pragma unroll
+        for (int j = 0; j < TL::J; ++j) {
+            const int k1 = TL::b_k1(t, j);
+#pragma unroll
+            for (int k2 = 0; k2 < TL::N2; ++k2) {
+                const int n = k1 + TL::N1 * k2;
+                int mx, my, mz;
+                TL::freqs(n, g, kz, c0, mx, my, mz);
+                Y[j][k2] = cmul(xnode_mult<T, N>(tm, mx, my, mz, kp, tab, slot_of, g * N + n), Q[j][bitrev(k2, TL::N2)]);
+            }
+        }
+        __syncthreads();
+        TL::invB(Y, sm, t);
+        __syncthreads();
+        V* dst = reinterpret_cast<V*>(P.out[tm.dst]) + chain * P.out_cs + base;
+        TL::invA(sm, dst, t);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// z pass.  Tile: 16 consecutive x by GY consecutive y; complex line c packs the
+// real lines at x0 + 2(c % 8) and x0 + 2(c % 8) + 1 of row y0 + c / 8.
+// ---------------------------------------------------------------------------
+template <typename T, int N> struct ZTile {
+    using V = cplx_t<T>;
+    static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, J = N1 / N2;
+    static constexpr int GY0 = 256 / (8 * N2);
+    static constexpr int GY = GY0 < N ? GY0 : N;
+    static constexpr int GC = 8 * GY;                 // complex lines per tile
+    static constexpr int NT = GC * N2;
+    static constexpr int SM_A = GC * N1 * (N2 + 1);   // transpose buffer
+    static constexpr int ZS = N + 1;                  // natural-order row stride
+    static constexpr int SM_Z = GC * ZS;
+    static constexpr int SM_ELEMS = SM_A > SM_Z ? SM_A : SM_Z;
+    static constexpr int TILES = (N / 16) * (N / GY);
+    __device__ static int sidx(int c, int k1, int n2) { return c * (N1 * (N2 + 1)) + k1 * (N2 + 1) + n2; }
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(ZTile<T, N>::NT) k_z_fwd(const ZProgram P) {
+    using ZT = ZTile<T, N>;
+    using V = cplx_t<T>;
+    using V4 = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* sm = reinterpret_cast<V*>(smraw);
+    const int t = threadIdx.x;
+    const int f = blockIdx.y, chain = blockIdx.z;
+    const int x0 = (blockIdx.x % (N / 16)) * 16, y0 = (blockIdx.x / (N / 16)) * ZT::GY;
+    const T* __restrict__ rin = reinterpret_cast<const T*>(P.in[f]) + chain * P.in_cs;
+    // step A: pack two real lines, N1-point DFTs
+    {
+        const int n2 = t % ZT::N2, c = t / ZT::N2;
+        const int y = y0 + c / 8, xa = x0 + 2 * (c % 8);
+        const T* la = rin + (size_t(xa) * N + y) * N;
+        const T* lb = la + size_t(N) * N;
+        V v[ZT::N1];
+#pragma unroll
+        for (int n1 = 0; n1 < ZT::N1; ++n1) v[n1] = cmake<V>(la[ZT::N2 * n1 + n2], lb[ZT::N2 * n1 + n2]);
+        dft_dif<ZT::N1, 1, -1>(v);
+#pragma unroll
+        for (int i = 0; i < ZT::N1; ++i) {
+            const int k1 = bitrev(i, ZT::N1);
+            sm[ZT::sidx(c, k1, n2)] = cmul(v[i], tw_load<T>(N, n2 * k1));
+        }
+    }
+    __syncthreads();
+    // step B, then natural-order line spectra Z[c][k]
+    {
+        const int c = t / ZT::N2;
+        V X[ZT::J][ZT::N2];
+#pragma unroll
+        for (int j = 0; j < ZT::J; ++j) {
+            const int k1 = t % ZT::N2 + j * ZT::N2;
+#pragma unroll
+            for (int n2 = 0; n2 < ZT::N2; ++n2) X[j][n2] = sm[ZT::sidx(c, k1, n2)];
+            dft_dif<ZT::N2, 1, -1>(X[j]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < ZT::J; ++j) {
+            const int k1 = t % ZT::N2 + j * ZT::N2;
+#pragma unroll
+            for (int i = 0; i < ZT::N2; ++i) sm[c * ZT::ZS + k1 + ZT::N1 * bitrev(i, ZT::N2)] = X[j][i];
+        }
+    }
+    __syncthreads();
+    // separate the two real lines and store [kz][y][x] as (A, B) pairs
+    V* __restrict__ sout = reinterpret_cast<V*>(P.out[f]) + chain * P.out_cs;
+    constexpr int ROWS = ZT::NT / 8;
+    const int pair = t % 8;
+    for (int idx = t / 8; idx < (N / 2 + 1) * ZT::GY; idx += ROWS) {
+        const int kz = idx / ZT::GY, yl = idx % ZT::GY;
+        const int c = yl * 8 + pair;
+        const V z1 = sm[c * ZT::ZS + kz];
+        const V z2 = sm[c * ZT::ZS + ((N - kz) & (N - 1))];
+        const T h = T(0.5);
+        V4 ab;
+        ab.x = h * (z1.x + z2.x);
+        ab.y = h * (z1.y - z2.y);
+        ab.z = h * (z1.y + z2.y);
+        ab.w = h * (z2.x - z1.x);
+        *reinterpret_cast<V4*>(sout + (size_t(kz) * N + (y0 + yl)) * N + x0 + 2 * pair) = ab;
+    }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(ZTile<T, N>::NT) k_z_inv(const ZProgram P) {
+    using ZT = ZTile<T, N>;
+    using V = cplx_t<T>;
+    using V4 = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* sm = reinterpret_cast<V*>(smraw);
+    const int t = threadIdx.x;
+    const int f = blockIdx.y, chain = blockIdx.z;
+    const int x0 = (blockIdx.x % (N / 16)) * 16, y0 = (blockIdx.x / (N / 16)) * ZT::GY;
+    const V* __restrict__ sin_ = reinterpret_cast<const V*>(P.in[f]) + chain * P.in_cs;
+    // load (A, B) pairs, build Z = A + iB on the full circle
+    constexpr int ROWS = ZT::NT / 8;
+    const int pair = t % 8;
+    for (int idx = t / 8; idx < (N / 2 + 1) * ZT::GY; idx += ROWS) {
+        const int kz = idx / ZT::GY, yl = idx % ZT::GY;
+        const int c = yl * 8 + pair;
+        const V4 ab = *reinterpret_cast<const V4*>(sin_ + (size_t(kz) * N + (y0 + yl)) * N + x0 + 2 * pair);
+        if (kz == 0 || kz == N / 2) {
+            sm[c * ZT::ZS + kz] = cmake<V>(ab.x, ab.z);   // real parts only
+        } else {
+            sm[c * ZT::ZS + kz] = cmake<V>(ab.x - ab.w, ab.y + ab.z);
+            sm[c * ZT::ZS + (N - kz)] = cmake<V>(ab.x + ab.w, ab.z - ab.y);
+        }
+    }
+    __syncthreads();
+    {
+        const int c = t / ZT::N2;
+        V Y[ZT::J][ZT::N2];
+#pragma unroll
+        for (int j = 0; j < ZT::J; ++j) {
+            const int k1 = t % ZT::N2 + j * ZT::N2;
+#pragma unroll
+            for (int k2 = 0; k2 < ZT::N2; ++k2) Y[j][k2] = sm[c * ZT::ZS + k1 + ZT::N1 * k2];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < ZT::J; ++j) {
+            const int k1 = t % ZT::N2 + j * ZT::N2;
+            dft_dif<ZT::N2, 1, +1>(Y[j]);
+#pragma unroll
+            for (int i = 0; i < ZT::N2; ++i) {
+                const int n2 = bitrev(i, ZT::N2);
+                sm[ZT::sidx(c, k1, n2)] = cmulc(Y[j][i], tw_load<T>(N, n2 * k1));
+            }
+        }
+    }
+    __syncthreads();
+    {
+        const int n2 = t % ZT::N2, c = t / ZT::N2;
+        const int y = y0 + c / 8, xa = x0 + 2 * (c % 8);
+        T* __restrict__ rout = reinterpret_cast<T*>(P.out[f]) + chain * P.out_cs;
+        T* la = rout + (size_t(xa) * N + y) * N;
+        T* lb = la + size_t(N) * N;
+        V v[ZT::N1];
+#pragma unroll
+        for (int k1 = 0; k1 < ZT::N1; ++k1) v[k1] = sm[ZT::sidx(c, k1, n2)];
+        dft_dif<ZT::N1, 1, +1>(v);
+#pragma unroll
+        for (int i = 0; i < ZT::N1; ++i) {
+            const int pos = n2 + ZT::N2 * bitrev(i, ZT::N1);
+            la[pos] = v[i].x;
+            lb[pos] = v[i].y;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename K> static cudaError_t set_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    return cudaSuccess;
+}
+
+// Mesh sizes compiled in (FP64 stops at 256: the FP64 path is the comparator).
+#ifndef BRIDGE_ONLY_N
+#define BRIDGE_N_SWITCH(n, T, CALL)                                   \
+    switch (n) {                                                      \
+        case 16: { constexpr int NN = 16; CALL; }                     \
+        case 32: { constexpr int NN = 32; CALL; }                     \
+        case 64: { constexpr int NN = 64; CALL; }                     \
+        case 128: { constexpr int NN = 128; CALL; }                   \
+        case 256: { constexpr int NN = 256; CALL; }                   \
+        case 512: {                                                   \
+            if constexpr (sizeof(T) == 4) { constexpr int NN = 512; CALL; } \
+            else return cudaErrorInvalidValue;                        \
+        }                                                             \
+        default: return cudaErrorInvalidValue;                        \
+    }
+#else
+#define BRIDGE_N_SWITCH(n, T, CALL)                                   \
+    switch (n) {                                                      \
+        case BRIDGE_ONLY_N: { constexpr int NN = BRIDGE_ONLY_N; CALL; } \
+        default: return cudaErrorInvalidValue;                        \
+    }
+#endif
+
+template <typename T, int N> static cudaError_t z_fwd_n(int batch, const ZProgram& p, cudaStream_t s) {
+    using ZT = ZTile<T, N>;
+    const size_t sm = size_t(ZT::SM_ELEMS) * sizeof(cplx_t<T>);
+    cudaError_t e = set_smem(k_z_fwd<T, N>, sm);
+    if (e != cudaSuccess) return e;
+    k_z_fwd<T, N><<<dim3(ZT::TILES, p.n_fields, batch), ZT::NT, sm, s>>>(p);
+    return cudaGetLastError();
+}
+template <typename T, int N> static cudaError_t z_inv_n(int batch, const ZProgram& p, cudaStream_t s) {
+    using ZT = ZTile<T, N>;
+    const size_t sm = size_t(ZT::SM_ELEMS) * sizeof(cplx_t<T>);
+    cudaError_t e = set_smem(k_z_inv<T, N>, sm);
+    if (e != cudaSuccess) return e;
+    k_z_inv<T, N><<<dim3(ZT::TILES, p.n_fields, batch), ZT::NT, sm, s>>>(p);
+    return cudaGetLastError();
+}
+template <typename T, int N, bool XM, bool FWD>
+static cudaError_t col_n(int batch, const PassProgram& p, const KParams& kp, cudaStream_t s) {
+    using TL = Tile<T, N, XM>;
+    const size_t sm = size_t(TL::SM_ELEMS) * sizeof(cplx_t<T>);
+    auto kern = FWD ? k_col_fwd<T, N, XM> : k_col_inv<T, N, XM>;
+    cudaError_t e = set_smem(kern, sm);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3(TL::TILES, batch), TL::NT, sm, s>>>(p, kp);
+    return cudaGetLastError();
+}
+template <typename T, int N> static cudaError_t xnode_n(int batch, const PassProgram& p, const KParams& kp, cudaStream_t s) {
+    using TL = Tile<T, N, true>;
+    const size_t sm = size_t(TL::SM_ELEMS) * sizeof(cplx_t<T>) + 2 * size_t(TL::G) * N * sizeof(T);
+    cudaError_t e = set_smem(k_x_node<T, N>, sm);
+    if (e != cudaSuccess) return e;
+    k_x_node<T, N><<<dim3(TL::TILES, batch), TL::NT, sm, s>>>(p, kp);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t launch_z_fwd(int n, int batch, const ZProgram& p, cudaStream_t s) {
+    BRIDGE_N_SWITCH(n, T, return (z_fwd_n<T, NN>(batch, p, s)));
+}
+template <typename T> cudaError_t launch_z_inv(int n, int batch, const ZProgram& p, cudaStream_t s) {
+    BRIDGE_N_SWITCH(n, T, return (z_inv_n<T, NN>(batch, p, s)));
+}
+template <typename T> cudaError_t launch_y_fwd(int n, int batch, const PassProgram& p, const KParams& kp, cudaStream_t s) {
+    BRIDGE_N_SWITCH(n, T, return (col_n<T, NN, false, true>(batch, p, kp, s)));
+}
+template <typename T> cudaError_t launch_y_inv(int n, int batch, const PassProgram& p, const KParams& kp, cudaStream_t s) {
+    BRIDGE_N_SWITCH(n, T, return (col_n<T, NN, false, false>(batch, p, kp, s)));
+}
+template <typename T> cudaError_t launch_x_node(int n, int batch, const PassProgram& p, const KParams& kp, cudaStream_t s) {
+    BRIDGE_N_SWITCH(n, T, return (xnode_n<T, NN>(batch, p, kp, s)));
+}
+
+#define BRIDGE_INST(T)                                                                                       \
+    template cudaError_t launch_z_fwd<T>(int, int, const ZProgram&, cudaStream_t);                           \
+    template cudaError_t launch_z_inv<T>(int, int, const ZProgram&, cudaStream_t);                           \
+    template cudaError_t launch_y_fwd<T>(int, int, const PassProgram&, const KParams&, cudaStream_t);        \
+    template cudaError_t launch_y_inv<T>(int, int, const PassProgram&, const KParams&, cudaStream_t);        \
+    template cudaError_t launch_x_node<T>(int, int, const PassProgram&, const KParams&, cudaStream_t);
+BRIDGE_INST(float)
+BRIDGE_INST(double)
+
+}  // namespace bridge

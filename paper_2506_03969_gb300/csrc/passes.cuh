@@ -1,0 +1,62 @@
+// Host-visible launch interface of the FFT pass kernels (passes.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bridge {
+
+// Multiplier radial factors R(|k|) used by pass terms.
+enum RCode : int8_t { R_ONE = 0, R_INVK2 = 1, R_SQRTP = 2, R_KBLEND = 3, R_1MKBLEND = 4 };
+
+// One linear term of a pass program:
+//   out[dst] (+)= (cre + i cim) * kx^px * ky^py * kz^pz * R(|k|) * in[src]
+// Odd powers vanish on the Nyquist index of their axis.
+struct Term {
+    int8_t src, dst, px, py, pz, rcode;
+    double cre, cim;
+};
+
+constexpr int kMaxTerms = 16;
+constexpr int kMaxFields = 16;
+
+// A pass program: fields, chain strides (elements) and terms.  For the x node
+// `merge` terms map inputs into the scalar spectrum Q (dst ignored) and
+// `expand` terms map Q into outputs (src ignored).
+struct PassProgram {
+    int n_in, n_out, n_merge, n_expand;
+    const void* in[kMaxFields];
+    void* out[kMaxFields];
+    long long in_cs, out_cs;
+    Term merge[kMaxTerms];
+    Term expand[kMaxTerms];
+};
+
+// Physical constants for multipliers.
+struct KParams {
+    double kf;        // 2 pi / L
+    double dx;        // L / N
+    double pk_amp, pk_ns, pk_kc, pk_pow;
+    double r_s;
+};
+
+// Real-space z pass.  Fields: in[f] / out[f] for f < n_fields; chain strides in elements.
+struct ZProgram {
+    int n_fields;
+    const void* in[kMaxFields];
+    void* out[kMaxFields];
+    long long in_cs, out_cs;
+};
+
+template <typename T> cudaError_t launch_z_fwd(int n, int batch, const ZProgram& p, cudaStream_t s);
+template <typename T> cudaError_t launch_z_inv(int n, int batch, const ZProgram& p, cudaStream_t s);
+// y pass: forward (merge) or inverse (expand) with ky/kz monomial terms
+template <typename T> cudaError_t launch_y_fwd(int n, int batch, const PassProgram& p, const KParams& kp, cudaStream_t s);
+template <typename T> cudaError_t launch_y_inv(int n, int batch, const PassProgram& p, const KParams& kp, cudaStream_t s);
+// x node: forward x DFT of the inputs, merge into Q, expand, inverse x DFT of the outputs
+template <typename T> cudaError_t launch_x_node(int n, int batch, const PassProgram& p, const KParams& kp, cudaStream_t s);
+
+// Upload the twiddle tables (host FP64 cos/sin, rounded per precision).
+cudaError_t upload_twiddles();
+
+}  // namespace bridge

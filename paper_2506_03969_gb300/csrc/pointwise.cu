@@ -1,0 +1,577 @@
+// Real-space kernels: ALPT sources and adjoint (Sect. 2.3), CIC mass assignment
+// and its gather adjoint, the fused eigenvalue / fuzzy-web / bias pass and its
+// adjoint (Sect. 2.5-2.8, App. B), the NB likelihood (Sect. 2.6), deterministic
+// FP64 reductions and the leapfrog updates (Sect. 2.2).
+#include <cmath>
+
+#include "common.cuh"
+#include "pointwise.cuh"
+
+namespace bridge {
+
+// Thread-block partial sums: each thread accumulates its voxels, then a fixed
+// warp-shuffle + shared-memory tree; thread 0 writes partial[chain][block][k].
+template <int K>
+__device__ __forceinline__ void write_partials(const double (&acc)[K], double* partial) {
+    __shared__ double sh[kPwThreads / 32];
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) {
+        double r = block_sum<kPwThreads>(acc[k], sh);
+        if (threadIdx.x == 0)
+            partial[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * K + k] = r;
+    }
+}
+
+#define PW_LOOP(i, nvox) for (long long i = (long long)blockIdx.x * kPwThreads + threadIdx.x; i < (nvox); \
+                              i += (long long)gridDim.x * kPwThreads)
+
+// ---------------------------------------------------------------------------
+// counts: int32 -> uint16 with range check; N_tr partial sums
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPwThreads) k_counts_prep(long long nvox, const int32_t* __restrict__ counts,
+                                                           uint16_t* __restrict__ c16, double* partial, int* err) {
+    const size_t off = (size_t)blockIdx.y * nvox;
+    double acc[1] = {0.0};
+    long long s = 0;
+    PW_LOOP(i, nvox) {
+        int v = counts[off + i];
+        if (v < 0 || v > 65535) { atomicOr(err, 1); v = 0; }
+        c16[off + i] = (uint16_t)v;
+        s += v;
+    }
+    acc[0] = (double)s;
+    write_partials<1>(acc, partial);
+}
+
+// ---------------------------------------------------------------------------
+// ALPT sources (Sect. 2.3): a = -D delta0 + D2 S2 (2LPT divergence),
+// b = theta_SC = 3[(1 - 2/3 D delta0)^(1/2) - 1] (D delta0 < 3/2), -3 otherwise.
+// in7 = delta0, phi_xx, phi_xy, phi_xz, phi_yy, phi_yz, phi_zz.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kPwThreads) k_alpt_src(long long nvox, Fields16 in7, T* a_out, T* b_out, T D, T D2) {
+    const size_t off = (size_t)blockIdx.y * nvox;
+    const T* d0 = (const T*)in7.p[0] + off;
+    const T* pxx = (const T*)in7.p[1] + off; const T* pxy = (const T*)in7.p[2] + off;
+    const T* pxz = (const T*)in7.p[3] + off; const T* pyy = (const T*)in7.p[4] + off;
+    const T* pyz = (const T*)in7.p[5] + off; const T* pzz = (const T*)in7.p[6] + off;
+    PW_LOOP(i, nvox) {
+        const T xx = pxx[i], xy = pxy[i], xz = pxz[i], yy = pyy[i], yz = pyz[i], zz = pzz[i];
+        const T s2 = xx * yy + xx * zz + yy * zz - xy * xy - xz * xz - yz * yz;
+        const T x = D * d0[i];
+        a_out[off + i] = -x + D2 * s2;
+        T arg = T(1) - T(2.0 / 3.0) * x;
+        arg = arg > T(1e-12) ? arg : T(1e-12);
+        b_out[off + i] = x < T(1.5) ? T(3) * (v_sqrt(arg) - T(1)) : T(-3);
+    }
+}
+
+// ALPT adjoint: given g_a, g_b, returns g_delta0 (direct) and g_phi (stored comps).
+template <typename T>
+__global__ void __launch_bounds__(kPwThreads) k_alpt_adj(long long nvox, const T* ga, const T* gb, Fields16 in7,
+                                                        Fields16 out7, T D, T D2) {
+    const size_t off = (size_t)blockIdx.y * nvox;
+    PW_LOOP(i, nvox) {
+        const size_t j = off + i;
+        const T d0 = ((const T*)in7.p[0])[j];
+        const T xx = ((const T*)in7.p[1])[j], xy = ((const T*)in7.p[2])[j], xz = ((const T*)in7.p[3])[j];
+        const T yy = ((const T*)in7.p[4])[j], yz = ((const T*)in7.p[5])[j], zz = ((const T*)in7.p[6])[j];
+        const T g_a = ga[j], g_b = gb[j];
+        const T x = D * d0;
+        const T arg = T(1) - T(2.0 / 3.0) * x;
+        // d theta_SC / d delta0 = -D / sqrt(1 - 2/3 D delta0) on the uncollapsed, unclamped branch
+        const T dsc = (x < T(1.5) && arg > T(1e-12)) ? -D / v_sqrt(arg) : T(0);
+        const T gs2 = D2 * g_a;
+        ((T*)out7.p[0])[j] = -D * g_a + dsc * g_b;
+        ((T*)out7.p[1])[j] = gs2 * (yy + zz);
+        ((T*)out7.p[2])[j] = gs2 * (T(-2) * xy);
+        ((T*)out7.p[3])[j] = gs2 * (T(-2) * xz);
+        ((T*)out7.p[4])[j] = gs2 * (xx + zz);
+        ((T*)out7.p[5])[j] = gs2 * (T(-2) * yz);
+        ((T*)out7.p[6])[j] = gs2 * (xx + yy);
+    }
+}
+
+template <typename T> __global__ void k_fill(long long count, T* p, T v) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+// ---------------------------------------------------------------------------
+// CIC (mass assignment): the particle of cell q sits at q + psi (cell units);
+// trilinear weights to the 8 surrounding cells, periodic.  delta must hold -1
+// on entry (one particle per cell: delta = rho - 1).
+// ---------------------------------------------------------------------------
+template <typename T> struct CicCorner {
+    int i0[3];
+    T f[3];
+};
+template <typename T> __device__ __forceinline__ void cic_corner(long long q, int N, T px, T py, T pz, CicCorner<T>& c) {
+    const int lg = __ffs(N) - 1;
+    const int qz = (int)(q & (N - 1)), qy = (int)((q >> lg) & (N - 1)), qx = (int)(q >> (2 * lg));
+    const T fx = floor(px), fy = floor(py), fz = floor(pz);
+    c.f[0] = px - fx; c.f[1] = py - fy; c.f[2] = pz - fz;
+    c.i0[0] = qx + (int)fx; c.i0[1] = qy + (int)fy; c.i0[2] = qz + (int)fz;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPwThreads) k_cic_scatter(int N, long long nvox, Fields16 psi3, T* delta) {
+    const size_t off = (size_t)blockIdx.y * nvox;
+    const T* p0 = (const T*)psi3.p[0] + off; const T* p1 = (const T*)psi3.p[1] + off; const T* p2 = (const T*)psi3.p[2] + off;
+    T* d = delta + off;
+    const int msk = N - 1;
+    PW_LOOP(q, nvox) {
+        CicCorner<T> c;
+        cic_corner<T>(q, N, p0[q], p1[q], p2[q], c);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const T wx = a ? c.f[0] : T(1) - c.f[0];
+            const size_t ix = (size_t)((c.i0[0] + a) & msk) * N;
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const T wy = b ? c.f[1] : T(1) - c.f[1];
+                const size_t iy = (ix + (size_t)((c.i0[1] + b) & msk)) * N;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const T wz = e ? c.f[2] : T(1) - c.f[2];
+                    atomicAdd(d + iy + ((c.i0[2] + e) & msk), wx * wy * wz);
+                }
+            }
+        }
+    }
+}
+
+// Gather adjoint: g_psi_j = sum_corners g_delta[c] dw_c/dpsi_j (cell units).
+template <typename T>
+__global__ void __launch_bounds__(kPwThreads) k_cic_gather(int N, long long nvox, const T* gdelta, Fields16 psi3, Fields16 out3) {
+    const size_t off = (size_t)blockIdx.y * nvox;
+    const T* g = gdelta + off;
+    const int msk = N - 1;
+    PW_LOOP(q, nvox) {
+        CicCorner<T> c;
+        cic_corner<T>(q, N, ((const T*)psi3.p[0])[off + q], ((const T*)psi3.p[1])[off + q], ((const T*)psi3.p[2])[off + q], c);
+        T gx = 0, gy = 0, gz = 0;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const T wx = a ? c.f[0] : T(1) - c.f[0], dwx = a ? T(1) : T(-1);
+            const size_t ix = (size_t)((c.i0[0] + a) & msk) * N;
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const T wy = b ? c.f[1] : T(1) - c.f[1], dwy = b ? T(1) : T(-1);
+                const size_t iy = (ix + (size_t)((c.i0[1] + b) & msk)) * N;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const T wz = e ? c.f[2] : T(1) - c.f[2], dwz = e ? T(1) : T(-1);
+                    const T gv = g[iy + ((c.i0[2] + e) & msk)];
+                    gx += gv * dwx * wy * wz;
+                    gy += gv * wx * dwy * wz;
+                    gz += gv * wx * wy * dwz;
+                }
+            }
+        }
+        ((T*)out3.p[0])[off + q] = gx;
+        ((T*)out3.p[1])[off + q] = gy;
+        ((T*)out3.p[2])[off + q] = gz;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused web + bias, forward (pass A): eigenvalues of T (and H), memberships,
+// per-voxel parameters, ln f and beta_i; partial sums of f.
+// ---------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ void load6(const Fields16& f, int base, size_t j, T out[6]) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) out[q] = ((const T*)f.p[base + q])[j];
+}
+
+template <typename T, int NR> struct WebState {
+    Eig3<T> ephi, edel;
+    T wphi[3], pphi[4], wdel[3], pdel[4];
+    T wts[NR];
+    VoxParams<T> q;
+    LnF<T> lf;
+};
+
+template <typename T, int NR>
+__device__ __forceinline__ void web_forward(const Fields16& th, size_t j, T delta, const BiasT<T>& B,
+                                            const WebParams& wp, WebState<T, NR>& S) {
+    T a6[6];
+    load6<T>(th, 0, j, a6);
+    eig3<T>(a6, S.ephi);
+    T lam[3] = {S.ephi.m + S.ephi.mu[0], S.ephi.m + S.ephi.mu[1], S.ephi.m + S.ephi.mu[2]};
+    memberships<T>(lam, T(wp.sharpness), T(wp.th_phi), S.wphi, S.pphi);
+    if constexpr (NR == 16) {
+        load6<T>(th, 6, j, a6);
+        eig3<T>(a6, S.edel);
+        T ld[3] = {S.edel.m + S.edel.mu[0], S.edel.m + S.edel.mu[1], S.edel.m + S.edel.mu[2]};
+        memberships<T>(ld, T(wp.sharpness), T(wp.th_delta), S.wdel, S.pdel);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) S.wts[4 * a + b] = S.pphi[a] * S.pdel[b];
+    } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) S.wts[a] = S.pphi[a];
+    }
+    interp_params<T, NR>(B, S.wts, S.q);
+    log_f<T>(delta, T(wp.rho_floor), S.q, S.lf);
+}
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(kPwThreads) k_pass_a(long long nvox, Fields16 th, const T* delta, T* lnf_out,
+                                                      T* beta_out, const BiasT<T>* bias, WebParams wp, double* partial) {
+    __shared__ BiasT<T> B;
+    const int chain = blockIdx.y;
+    if (threadIdx.x == 0) B = bias[chain];
+    __syncthreads();
+    const size_t off = (size_t)chain * nvox;
+    T accf = T(0);
+    double acc[1];
+    double accd = 0.0;
+    int cnt = 0;
+    PW_LOOP(i, nvox) {
+        const size_t j = off + i;
+        WebState<T, NR> S;
+        web_forward<T, NR>(th, j, delta[j], B, wp, S);
+        lnf_out[j] = S.lf.lnf;
+        beta_out[j] = S.q.beta;
+        accf += v_exp(S.lf.lnf);
+        if (++cnt == 16) { accd += (double)accf; accf = T(0); cnt = 0; }
+    }
+    acc[0] = accd + (double)accf;
+    write_partials<1>(acc, partial);
+}
+
+// NB likelihood (pass B): ln nbar = ln f + ln C; partial sums of log P,
+// d log P/d ln nbar and nu^2.
+template <typename T>
+__global__ void __launch_bounds__(kPwThreads) k_pass_b(long long nvox, const T* lnf, const T* beta_i,
+                                                      const uint16_t* c16, const T* nu, const ChainScalars* sc,
+                                                      double* partial) {
+    const int chain = blockIdx.y;
+    const size_t off = (size_t)chain * nvox;
+    const T lnC = T(sc[chain].lnC);
+    T a0 = 0, a1 = 0, a2 = 0;
+    double acc[3] = {0.0, 0.0, 0.0};
+    int cnt = 0;
+    PW_LOOP(i, nvox) {
+        const size_t j = off + i;
+        NB<T> r;
+        nb_eval<T>((int)c16[j], lnf[j] + lnC, beta_i[j], true, r);
+        const T v = nu[j];
+        a0 += r.logp; a1 += r.g_lnnbar; a2 += v * v;
+        if (++cnt == 16) { acc[0] += a0; acc[1] += a1; acc[2] += a2; a0 = a1 = a2 = T(0); cnt = 0; }
+    }
+    acc[0] += a0; acc[1] += a1; acc[2] += a2;
+    write_partials<3>(acc, partial);
+}
+
+// ---------------------------------------------------------------------------
+// Web + bias + NB adjoint: g_delta (direct), g_T (6), g_H (6) and the
+// partial sums of d/d alpha_r and d/d beta_r.
+// ---------------------------------------------------------------------------
+template <typename T, int NR>
+__global__ void __launch_bounds__(kPwThreads) k_web_adj(long long nvox, Fields16 th, const T* delta,
+                                                       const uint16_t* c16, const BiasT<T>* bias, WebParams wp,
+                                                       const ChainScalars* sc, Fields16 out, double* partial) {
+    __shared__ BiasT<T> B;
+    const int chain = blockIdx.y;
+    if (threadIdx.x == 0) B = bias[chain];
+    __syncthreads();
+    const size_t off = (size_t)chain * nvox;
+    const T lnC = T(sc[chain].lnC);
+    const T gscale = T(sc[chain].G / sc[chain].ntr);   // f_i/sum f * G = nbar_i * G / N_tr
+    const T s = T(wp.sharpness), tau = T(wp.tau);
+    T ga[NR], gb[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) ga[r] = gb[r] = T(0);
+    PW_LOOP(i, nvox) {
+        const size_t j = off + i;
+        const T dl = delta[j];
+        WebState<T, NR> S;
+        web_forward<T, NR>(th, j, dl, B, wp, S);
+        const T lnnbar = S.lf.lnf + lnC;
+        NB<T> nb;
+        nb_eval<T>((int)c16[j], lnnbar, S.q.beta, true, nb);
+        const T nbar = v_exp(lnnbar);
+        const T glnf = nb.g_lnnbar - nbar * gscale;      // normalisation adjoint
+        const T gbeta = nb.g_beta;
+        // d ln f / d(parameters)
+        const T g_a = glnf / S.q.a;
+        const T g_al = glnf * S.lf.lnu;
+        const T g_rho = glnf * S.q.eps * S.lf.t1 / S.q.rho;
+        const T g_eps = -glnf * S.lf.t1 * (S.lf.lnu - S.lf.lnrho);
+        T g_rhop = T(0), g_epsp = T(0);
+        if (S.q.rhop > T(0)) {
+            g_rhop = -glnf * S.q.epsp * S.lf.t2 / S.q.rhop;
+            g_epsp = -glnf * S.lf.t2 * (S.lf.lnrhop - S.lf.lnu);
+        }
+        // direct density derivative (zero below the floor)
+        const T u = v_exp(S.lf.lnu);
+        const T gdel = S.lf.floored ? T(0) : glnf * (S.q.alpha - S.q.eps * S.lf.t1 + S.q.epsp * S.lf.t2) / u;
+        // region weights
+        T gw[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            gw[r] = g_a * B.a[r] + g_al * B.alpha[r] + g_rho * B.rho[r] + g_eps * B.eps[r] + g_rhop * B.rhop[r] +
+                    g_epsp * B.epsp[r] + gbeta * B.beta[r];
+            ga[r] += g_al * S.wts[r];
+            gb[r] += gbeta * S.wts[r];
+        }
+        T gpphi[4], gpdel[4];
+        if constexpr (NR == 16) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                gpphi[a] = T(0);
+                gpdel[a] = T(0);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    gpphi[a] += gw[4 * a + b] * S.pdel[b];
+                    gpdel[b] += gw[4 * a + b] * S.pphi[a];
+                }
+        } else {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) gpphi[a] = gw[a];
+        }
+        // memberships -> eigenvalues -> tensor (stored components)
+        T gt[6];
+        {
+            const T g1 = (gpphi[1] - gpphi[0]) * s * S.wphi[0] * (T(1) - S.wphi[0]);
+            const T g2 = (gpphi[2] - gpphi[1]) * s * S.wphi[1] * (T(1) - S.wphi[1]);
+            const T g3 = (gpphi[3] - gpphi[2]) * s * S.wphi[2] * (T(1) - S.wphi[2]);
+            eig_adjoint<T>(S.ephi, g1, g2, g3, tau, gt);
+        }
+        ((T*)out.p[0])[j] = gdel;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) ((T*)out.p[1 + q])[j] = gt[q];
+        if constexpr (NR == 16) {
+            const T g1 = (gpdel[1] - gpdel[0]) * s * S.wdel[0] * (T(1) - S.wdel[0]);
+            const T g2 = (gpdel[2] - gpdel[1]) * s * S.wdel[1] * (T(1) - S.wdel[1]);
+            const T g3 = (gpdel[3] - gpdel[2]) * s * S.wdel[2] * (T(1) - S.wdel[2]);
+            eig_adjoint<T>(S.edel, g1, g2, g3, tau, gt);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) ((T*)out.p[7 + q])[j] = gt[q];
+        }
+    }
+    double acc[2 * NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        acc[r] = (double)ga[r];
+        acc[NR + r] = (double)gb[r];
+    }
+    write_partials<2 * NR>(acc, partial);
+}
+
+template <typename T> __global__ void k_sub(long long count, const T* r, const T* nu, T* out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+        out[i] = r[i] - nu[i];
+}
+
+// Leapfrog (Sect. 2.2): p += ck g; nu += cd p; partial sums of p^2 after the update.
+template <typename T>
+__global__ void __launch_bounds__(kPwThreads) k_kick_drift(long long nvox, T* p, T* nu, const T* g, T ck, T cd,
+                                                          double* partial) {
+    const size_t off = (size_t)blockIdx.y * nvox;
+    T a = 0;
+    double acc[1] = {0.0};
+    int cnt = 0;
+    PW_LOOP(i, nvox) {
+        const size_t j = off + i;
+        T pv = p[j] + ck * g[j];
+        p[j] = pv;
+        if (cd != T(0)) nu[j] += cd * pv;
+        a += pv * pv;
+        if (++cnt == 16) { acc[0] += a; a = T(0); cnt = 0; }
+    }
+    acc[0] += a;
+    write_partials<1>(acc, partial);
+}
+
+template <typename T>
+__global__ void k_lnnbar(long long nvox, const T* lnf, const ChainScalars* sc, T* out) {
+    const size_t off = (size_t)blockIdx.y * nvox;
+    const T lnC = T(sc[blockIdx.y].lnC);
+    PW_LOOP(i, nvox) out[off + i] = lnf[off + i] + lnC;
+}
+
+template <typename T>
+__global__ void k_eigs(long long nvox, Fields16 t6, Fields16 out3) {
+    const size_t off = (size_t)blockIdx.y * nvox;
+    PW_LOOP(i, nvox) {
+        T a6[6];
+        load6<T>(t6, 0, off + i, a6);
+        Eig3<T> e;
+        eig3<T>(a6, e);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) ((T*)out3.p[q])[off + i] = e.m + e.mu[q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions (one block per chain; fixed order)
+// ---------------------------------------------------------------------------
+__device__ double lognormal_logpdf(double b, double mu, double sigma) {
+    const double lb = log(b);
+    return -lb - log(sigma * 2.5066282746310002) - (lb - mu) * (lb - mu) / (2.0 * sigma * sigma);
+}
+__device__ double lognormal_dlogpdf(double b, double mu, double sigma) {
+    const double lb = log(b);
+    return -1.0 / b - (lb - mu) / (sigma * sigma * b);
+}
+
+__global__ void __launch_bounds__(kPwThreads) k_reduce(int what, int nblk, int K, const double* partial,
+                                                      ChainScalars* sc, const BiasD* bias, int n_regions) {
+    __shared__ double sh[kPwThreads / 32];
+    const int chain = blockIdx.x;
+    ChainScalars& S = sc[chain];
+    for (int k = 0; k < K; ++k) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblk; b += kPwThreads) v += partial[((size_t)chain * nblk + b) * K + k];
+        const double tot = block_sum<kPwThreads>(v, sh);
+        if (threadIdx.x == 0) {
+            if (what == RED_NTR) S.ntr = tot;
+            else if (what == RED_SUMF) { S.sumf = tot; S.lnC = log(S.ntr) - log(tot); }
+            else if (what == RED_LIK) { if (k == 0) S.loglik = tot; else if (k == 1) S.G = tot; else S.sumnu2 = tot; }
+            else if (what == RED_BIASGRAD) S.gbias[k] = tot;
+            else if (what == RED_P2) S.sump2 = tot;
+        }
+    }
+    if (threadIdx.x == 0) {
+        const BiasD& Bd = bias[chain];
+        if (what == RED_LIK) {
+            double lp = 0.0;
+            for (int r = 0; r < n_regions; ++r)
+                if ((Bd.prior_mask >> r) & 1u)
+                    lp += lognormal_logpdf(Bd.alpha[r], Bd.mu_alpha, Bd.sigma_alpha) +
+                          lognormal_logpdf(Bd.beta[r], Bd.mu_beta, Bd.sigma_beta);
+            S.logprior = lp;
+            S.logpost = -0.5 * S.sumnu2 + S.loglik + lp;
+        } else if (what == RED_BIASGRAD) {
+            for (int r = 0; r < n_regions; ++r)
+                if ((Bd.prior_mask >> r) & 1u) {
+                    S.gbias[r] += lognormal_dlogpdf(Bd.alpha[r], Bd.mu_alpha, Bd.sigma_alpha);
+                    S.gbias[n_regions + r] += lognormal_dlogpdf(Bd.beta[r], Bd.mu_beta, Bd.sigma_beta);
+                }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline long long nvox_of(int n) { return (long long)n * n * n; }
+
+template <typename T>
+cudaError_t launch_counts_prep(int n, int batch, const int32_t* counts, uint16_t* c16, double* partial, int* err,
+                               cudaStream_t s) {
+    k_counts_prep<<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), counts, c16, partial, err);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_alpt_src(int n, int batch, const Fields16& in7, T* a_out, T* b_out, double growth, double d2,
+                            cudaStream_t s) {
+    k_alpt_src<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), in7, a_out, b_out, T(growth), T(d2));
+    return cudaGetLastError();
+}
+template <typename T> cudaError_t launch_fill(long long count, T* p, T v, cudaStream_t s) {
+    long long b = (count + 1023) / 1024;
+    k_fill<T><<<(unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b)), 256, 0, s>>>(count, p, v);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_cic_scatter(int n, int batch, const Fields16& psi3, T* delta, cudaStream_t s) {
+    k_cic_scatter<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(n, nvox_of(n), psi3, delta);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_pass_a(int n, int batch, const Fields16& th, const T* delta, T* lnf, T* beta_i,
+                          const BiasT<T>* bias, const WebParams& wp, double* partial, cudaStream_t s) {
+    if (wp.n_regions == 16)
+        k_pass_a<T, 16><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), th, delta, lnf, beta_i, bias, wp, partial);
+    else
+        k_pass_a<T, 4><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), th, delta, lnf, beta_i, bias, wp, partial);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_pass_b(int n, int batch, const T* lnf, const T* beta_i, const uint16_t* c16, const T* nu,
+                          const ChainScalars* sc, double* partial, cudaStream_t s) {
+    k_pass_b<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), lnf, beta_i, c16, nu, sc, partial);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_web_adjoint(int n, int batch, const Fields16& th, const T* delta, const uint16_t* c16,
+                               const BiasT<T>* bias, const WebParams& wp, const ChainScalars* sc,
+                               const Fields16& out, double* partial, cudaStream_t s) {
+    if (wp.n_regions == 16)
+        k_web_adj<T, 16><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), th, delta, c16, bias, wp, sc, out, partial);
+    else
+        k_web_adj<T, 4><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), th, delta, c16, bias, wp, sc, out, partial);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_cic_gather(int n, int batch, const T* gdelta, const Fields16& psi3, const Fields16& out3,
+                              cudaStream_t s) {
+    k_cic_gather<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(n, nvox_of(n), gdelta, psi3, out3);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_alpt_adjoint(int n, int batch, const T* ga, const T* gb, const Fields16& in7,
+                                const Fields16& out7, double growth, double d2, cudaStream_t s) {
+    k_alpt_adj<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), ga, gb, in7, out7, T(growth), T(d2));
+    return cudaGetLastError();
+}
+template <typename T> cudaError_t launch_sub(long long count, const T* r, const T* nu, T* out, cudaStream_t s) {
+    long long b = (count + 1023) / 1024;
+    k_sub<T><<<(unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b)), 256, 0, s>>>(count, r, nu, out);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_kick_drift(int n, int batch, T* p, T* nu, const T* g, double ck, double cd, double* partial,
+                              cudaStream_t s) {
+    k_kick_drift<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), p, nu, g, T(ck), T(cd), partial);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_lnnbar(long long nvox, int batch, const T* lnf, const ChainScalars* sc, T* out, cudaStream_t s) {
+    k_lnnbar<T><<<dim3(256, batch), kPwThreads, 0, s>>>(nvox, lnf, sc, out);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_eigs(int n, int batch, const Fields16& t6, const Fields16& out3, cudaStream_t s) {
+    k_eigs<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), t6, out3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(int what, int n, int batch, const double* partial, ChainScalars* sc, const BiasD* bias,
+                          int n_regions, cudaStream_t s) {
+    int K = what == RED_LIK ? 3 : (what == RED_BIASGRAD ? 2 * n_regions : 1);
+    k_reduce<<<batch, kPwThreads, 0, s>>>(what, pw_blocks(n), K, partial, sc, bias, n_regions);
+    return cudaGetLastError();
+}
+
+#define PW_INST(T)                                                                                                   \
+    template cudaError_t launch_counts_prep<T>(int, int, const int32_t*, uint16_t*, double*, int*, cudaStream_t);   \
+    template cudaError_t launch_alpt_src<T>(int, int, const Fields16&, T*, T*, double, double, cudaStream_t);        \
+    template cudaError_t launch_fill<T>(long long, T*, T, cudaStream_t);                                            \
+    template cudaError_t launch_cic_scatter<T>(int, int, const Fields16&, T*, cudaStream_t);                        \
+    template cudaError_t launch_pass_a<T>(int, int, const Fields16&, const T*, T*, T*, const BiasT<T>*,             \
+                                          const WebParams&, double*, cudaStream_t);                                 \
+    template cudaError_t launch_pass_b<T>(int, int, const T*, const T*, const uint16_t*, const T*,                  \
+                                          const ChainScalars*, double*, cudaStream_t);                              \
+    template cudaError_t launch_web_adjoint<T>(int, int, const Fields16&, const T*, const uint16_t*,                \
+                                               const BiasT<T>*, const WebParams&, const ChainScalars*,              \
+                                               const Fields16&, double*, cudaStream_t);                             \
+    template cudaError_t launch_cic_gather<T>(int, int, const T*, const Fields16&, const Fields16&, cudaStream_t);  \
+    template cudaError_t launch_alpt_adjoint<T>(int, int, const T*, const T*, const Fields16&, const Fields16&,     \
+                                                double, double, cudaStream_t);                                      \
+    template cudaError_t launch_sub<T>(long long, const T*, const T*, T*, cudaStream_t);                            \
+    template cudaError_t launch_kick_drift<T>(int, int, T*, T*, const T*, double, double, double*, cudaStream_t);   \
+    template cudaError_t launch_lnnbar<T>(long long, int, const T*, const ChainScalars*, T*, cudaStream_t);         \
+    template cudaError_t launch_eigs<T>(int, int, const Fields16&, const Fields16&, cudaStream_t);
+PW_INST(float)
+PW_INST(double)
+
+}  // namespace bridge

@@ -1,0 +1,86 @@
+// Host-visible launch interface of the real-space kernels (pointwise.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "voxel.cuh"
+
+namespace bridge {
+
+constexpr int kPwThreads = 256;
+// Blocks per chain of the real-space kernels (fixed per N so that the FP64
+// partial sums are reduced in a fixed order: the results are deterministic).
+inline int pw_blocks(int n) {
+    long long v = (long long)n * n * n / (kPwThreads * 4);
+    return int(v < 1 ? 1 : (v > 1024 ? 1024 : v));
+}
+
+// Per-chain FP64 scalars kept on the device.
+struct ChainScalars {
+    double ntr;       // N_tr = sum n*
+    double sumf;      // sum_i f_i
+    double lnC;       // ln N_tr - ln sum f
+    double loglik;    // sum_i log P_i
+    double G;         // sum_i d log P_i / d ln nbar_i
+    double sumnu2;    // sum nu^2
+    double logprior;  // log-normal prior of the bias tables
+    double logpost;
+    double sump2;     // sum p^2 (leapfrog)
+    double gbias[32]; // d/d alpha_r then d/d beta_r
+};
+
+struct BiasD {        // double copy of a chain's table and prior (device)
+    double a[16], alpha[16], rho[16], eps[16], rhop[16], epsp[16], beta[16];
+    uint32_t prior_mask;
+    double mu_alpha, sigma_alpha, mu_beta, sigma_beta;
+};
+
+struct WebParams {
+    double sharpness, th_phi, th_delta, rho_floor, tau;
+    int n_regions;
+};
+
+struct Fields16 { void* p[16]; };
+
+template <typename T>
+cudaError_t launch_counts_prep(int n, int batch, const int32_t* counts, uint16_t* c16, double* partial, int* err,
+                               cudaStream_t s);
+template <typename T>
+cudaError_t launch_alpt_src(int n, int batch, const Fields16& in7, T* a_out, T* b_out, double growth, double d2,
+                            cudaStream_t s);
+template <typename T> cudaError_t launch_fill(long long count, T* p, T v, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cic_scatter(int n, int batch, const Fields16& psi3, T* delta, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pass_a(int n, int batch, const Fields16& th, const T* delta, T* lnf, T* beta_i,
+                          const BiasT<T>* bias, const WebParams& wp, double* partial, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pass_b(int n, int batch, const T* lnf, const T* beta_i, const uint16_t* c16, const T* nu,
+                          const ChainScalars* sc, double* partial, cudaStream_t s);
+template <typename T>
+cudaError_t launch_web_adjoint(int n, int batch, const Fields16& th, const T* delta, const uint16_t* c16,
+                               const BiasT<T>* bias, const WebParams& wp, const ChainScalars* sc,
+                               const Fields16& out, double* partial, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cic_gather(int n, int batch, const T* gdelta, const Fields16& psi3, const Fields16& out3,
+                              cudaStream_t s);
+template <typename T>
+cudaError_t launch_alpt_adjoint(int n, int batch, const T* ga, const T* gb, const Fields16& in7,
+                                const Fields16& out7, double growth, double d2, cudaStream_t s);
+template <typename T>
+cudaError_t launch_sub(long long count, const T* r, const T* nu, T* out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_kick_drift(int n, int batch, T* p, T* nu, const T* g, double ck, double cd, double* partial,
+                              cudaStream_t s);
+template <typename T>
+cudaError_t launch_lnnbar(long long nvox, int batch, const T* lnf, const ChainScalars* sc, T* out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_eigs(int n, int batch, const Fields16& t6, const Fields16& out3, cudaStream_t s);
+
+// Reductions of the block partials (one block per chain, fixed order).
+cudaError_t launch_reduce(int what, int n, int batch, const double* partial, ChainScalars* sc, const BiasD* bias,
+                          int n_regions, cudaStream_t s);
+enum { RED_NTR = 0, RED_SUMF = 1, RED_LIK = 2, RED_BIASGRAD = 3, RED_P2 = 4 };
+
+}  // namespace bridge
