@@ -10,21 +10,24 @@
 #include "common.cuh"
 #include "passes.cuh"
 #include "pointwise.cuh"
+#include "nodes.cuh"
 
 using namespace bridge;
 
 namespace {
 
-constexpr int kMaxSpec = 19;   // spectral scratch buffers (peak use: adjoint y merge 13 -> 6)
-constexpr int kMaxReal = 36;   // real-space buffers
-
-// Real buffer slots.
+// Spectral buffers: 19 scratch (peak use: adjoint y merge 13 -> 6) and the
+// spectra kept from the forward pass for the nodes that recompute real fields
+// in the adjoint: linear field and potential Hessian (7), displacement (3),
+// tidal tensor and density Hessian (12).
+enum { SP_SCR = 0, SP_ALPT = 19, SP_PSI = 26, SP_TH = 29, kMaxSpec = 41 };
+// Real buffers.
 enum {
-    RB_ALPT = 0,    // 7: delta0, phi_xx, phi_xy, phi_xz, phi_yy, phi_yz, phi_zz
-    RB_PSI = 7,     // 3: displacement (cell units)
-    RB_DELTA = 10,  // 1: CIC density contrast
-    RB_TH = 11,     // 12: tidal tensor (6) then density Hessian (6)
-    RB_SCR = 23     // 13: scratch
+    RB_DELTA = 0,   // 1: CIC mass rho = 1 + delta
+    RB_LNF = 1,     // 2: ln f, beta_i
+    RB_GD = 3,      // 1: g_rho (input of the CIC gather)
+    RB_SCR = 4,     // 6: scratch for inspection fields
+    kMaxReal = 10
 };
 
 Term mk(int src, int dst, int px, int py, int pz, RCode rc, double cre, double cim = 0.0) {
@@ -57,6 +60,7 @@ struct bridge_ctx {
     void* biast = nullptr;
     int* errflag = nullptr;
     void* grad_tmp = nullptr;   // gradient scratch for leapfrog
+    void* node_scratch = nullptr;  // per-CTA slabs of the fused nodes (L2-resident)
     // host e2e buffers
     void* h_nu = nullptr;
     int32_t* h_counts = nullptr;
@@ -164,7 +168,7 @@ int validate_bias(const bridge_ctx* ctx, const bridge_bias* b, std::string* why)
 }
 
 struct Plan {
-    size_t spec_bytes, real_bytes, c16_bytes, partial_bytes, sc_bytes, biasd_bytes, biast_bytes, total;
+    size_t spec_bytes, real_bytes, c16_bytes, partial_bytes, sc_bytes, biasd_bytes, biast_bytes, node_bytes, total;
     int nspec_buf, nreal_buf;
 };
 
@@ -180,12 +184,15 @@ Plan make_plan(const bridge_config* c) {
     p.spec_bytes = align_up(size_t(nspec) * 2 * esz * B);
     p.real_bytes = align_up(size_t(nvox) * esz * B);
     p.c16_bytes = align_up(size_t(nvox) * 2 * B);
-    p.partial_bytes = align_up(size_t(B) * pw_blocks(c->n) * 32 * sizeof(double));
+    // node grids are bounded by the SM count (at most 4 CTAs per SM on a GB300's 152 SMs)
+    const size_t max_blocks = pw_blocks(c->n) > 1024 ? size_t(pw_blocks(c->n)) : size_t(1024);
+    p.partial_bytes = align_up(size_t(B) * max_blocks * 32 * sizeof(double));
     p.sc_bytes = align_up(sizeof(ChainScalars) * B);
     p.biasd_bytes = align_up(sizeof(BiasD) * B);
     p.biast_bytes = align_up(sizeof(BiasT<double>) * B);
+    p.node_bytes = align_up(size_t(80) << 20);   // fused-node slabs (the launcher keeps them below this)
     p.total = p.spec_bytes * p.nspec_buf + p.real_bytes * (p.nreal_buf + 1) + p.c16_bytes + p.partial_bytes +
-              p.sc_bytes + p.biasd_bytes + p.biast_bytes + 256;
+              p.sc_bytes + p.biasd_bytes + p.biast_bytes + p.node_bytes + 256;
     return p;
 }
 
@@ -265,19 +272,40 @@ template <typename T> int y_identity(bridge_ctx* ctx, int first, int count, bool
 
 #define RUN(x) do { int st_ = (x); if (st_ != BRIDGE_OK) return st_; } while (0)
 
+// Fused node launch: fills the common arguments, zeroes the partial sums the
+// node accumulates into and reports the grid (partial slots per chain).
+template <typename T> int node(bridge_ctx* ctx, NodeArgs& na, const char* name, double bytes, int* grid_used) {
+    na.c16 = ctx->c16;
+    na.bias = ctx->biast;
+    na.sc = ctx->sc;
+    na.partial = ctx->partial;
+    na.scratch = ctx->node_scratch;
+    na.wp = ctx->wp;
+    na.growth = ctx->cfg.growth_d;
+    na.d2 = ctx->cfg.d2_over_d2 * ctx->cfg.growth_d * ctx->cfg.growth_d;
+    na.n_regions = ctx->nr;
+    if (na.kind == NODE_WEB_FWD || (na.kind == NODE_WEB_ADJ && na.bias_grad))
+        CK(cudaMemsetAsync(ctx->partial, 0, size_t(ctx->B) * 1024 * 32 * sizeof(double), ctx->stream));
+    int g = 0;
+    CKL(name, bytes, launch_node<T>(ctx->n, ctx->B, na, &g, ctx->stream));
+    if (grid_used) *grid_used = g;
+    return BRIDGE_OK;
+}
+
 // ---------------------------------------------------------------------------
-// Forward model.  Leaves in the workspace: real ALPT fields, psi, delta, T/H,
-// lnf (SCR+0), beta_i (SCR+1), scalars (ntr, sumf, lnC, loglik, G, logpost).
-// nu: device [B][N^3].
+// Forward model.  Leaves in the workspace: the ALPT, displacement and tensor
+// spectra, rho, ln f and beta_i, and the scalars (ntr, sumf, lnC, loglik, G,
+// logpost).  nu: device [B][N^3].
 // ---------------------------------------------------------------------------
 template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelihood) {
     const double invn3 = 1.0 / double(ctx->nvox);
     const bool hier = ctx->nr == 16;
-    // M_delta (App. A) and the linear potential Hessian: nu -> delta0, phi_ij
-    RUN(z_fwd<T>(ctx, {nu}, {ctx->spec[0]}));
-    RUN(y_identity<T>(ctx, 0, 1, true));
+    const int nth = nth_of(ctx);
+    // M_delta (App. A) and the linear potential Hessian: nu -> delta0, phi_ij spectra
+    RUN(z_fwd<T>(ctx, {nu}, {ctx->spec[SP_SCR]}));
+    RUN(y_identity<T>(ctx, SP_SCR, 1, true));
     {
-        PassProgram p = program(cspec<T>(ctx, 0, 1), mspec<T>(ctx, 1, 4), ctx->nspec);
+        PassProgram p = program(cspec<T>(ctx, SP_SCR, 1), mspec<T>(ctx, SP_SCR + 1, 4), ctx->nspec);
         add_merge(p, mk(0, 0, 0, 0, 0, R_SQRTP, invn3));
         add_expand(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));    // W0 -> delta0
         add_expand(p, mk(0, 1, 2, 0, 0, R_INVK2, 1.0));  // V2 = kx^2/k^2
@@ -286,7 +314,7 @@ template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelih
         CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
     {
-        PassProgram p = program(cspec<T>(ctx, 1, 4), mspec<T>(ctx, 5, 7), ctx->nspec);
+        PassProgram p = program(cspec<T>(ctx, SP_SCR + 1, 4), mspec<T>(ctx, SP_ALPT, 7), ctx->nspec);
         add_expand(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));    // delta0
         add_expand(p, mk(1, 1, 0, 0, 0, R_ONE, 1.0));    // phi_xx
         add_expand(p, mk(2, 2, 0, 1, 0, R_ONE, 1.0));    // phi_xy
@@ -296,17 +324,18 @@ template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelih
         add_expand(p, mk(3, 6, 0, 0, 2, R_ONE, 1.0));    // phi_zz
         CKL("y_inv", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_inv<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
-    RUN(z_inv<T>(ctx, cspec<T>(ctx, 5, 7), mreal(ctx, RB_ALPT, 7)));
-    // ALPT sources (Sect. 2.3) -> blend -> displacement
+    // ALPT sources (Sect. 2.3) on the fly: inverse z of delta0, phi -> a, theta_SC -> forward z
     {
-        const double D = ctx->cfg.growth_d, D2 = ctx->cfg.d2_over_d2 * D * D;
-        CKL("alpt_src", 9 * rby<T>(ctx), launch_alpt_src<T>(ctx->n, ctx->B, fields(ctx, RB_ALPT, 7), RB<T>(ctx, RB_SCR), RB<T>(ctx, RB_SCR + 1), D, D2,
-                              ctx->stream));
+        NodeArgs na{};
+        na.kind = NODE_ALPT_FWD;
+        for (int f = 0; f < 7; ++f) na.spec_in[f] = ctx->spec[SP_ALPT + f];
+        na.spec_out[0] = ctx->spec[SP_SCR];
+        na.spec_out[1] = ctx->spec[SP_SCR + 1];
+        RUN(node<T>(ctx, na, "node_alpt", 9 * sby<T>(ctx), nullptr));
     }
-    RUN(z_fwd<T>(ctx, creal(ctx, RB_SCR, 2), mspec<T>(ctx, 0, 2)));
-    RUN(y_identity<T>(ctx, 0, 2, true));
+    RUN(y_identity<T>(ctx, SP_SCR, 2, true));
     {
-        PassProgram p = program(cspec<T>(ctx, 0, 2), mspec<T>(ctx, 2, 2), ctx->nspec);
+        PassProgram p = program(cspec<T>(ctx, SP_SCR, 2), mspec<T>(ctx, SP_SCR + 2, 2), ctx->nspec);
         add_merge(p, mk(0, 0, 0, 0, 0, R_KBLEND, invn3));
         add_merge(p, mk(1, 0, 0, 0, 0, R_1MKBLEND, invn3));
         const double c = -1.0 / ctx->kp.dx;               // Psi_j = -i k_j theta / (k^2 dx)
@@ -315,21 +344,26 @@ template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelih
         CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
     {
-        PassProgram p = program(cspec<T>(ctx, 2, 2), mspec<T>(ctx, 4, 3), ctx->nspec);
+        PassProgram p = program(cspec<T>(ctx, SP_SCR + 2, 2), mspec<T>(ctx, SP_PSI, 3), ctx->nspec);
         add_expand(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));
         add_expand(p, mk(1, 1, 0, 1, 0, R_ONE, 1.0));
         add_expand(p, mk(1, 2, 0, 0, 1, R_ONE, 1.0));
         CKL("y_inv", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_inv<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
-    RUN(z_inv<T>(ctx, cspec<T>(ctx, 4, 3), mreal(ctx, RB_PSI, 3)));
-    // CIC
-    CKL("fill", rby<T>(ctx), launch_fill<T>(ctx->nvox * ctx->B, RB<T>(ctx, RB_DELTA), T(-1), ctx->stream));
-    CKL("cic_scatter", 4 * rby<T>(ctx), launch_cic_scatter<T>(ctx->n, ctx->B, fields(ctx, RB_PSI, 3), RB<T>(ctx, RB_DELTA), ctx->stream));
-    // tidal tensor and density Hessian (Sect. 2.8, App. B)
-    RUN(z_fwd<T>(ctx, creal(ctx, RB_DELTA, 1), mspec<T>(ctx, 0, 1)));
-    RUN(y_identity<T>(ctx, 0, 1, true));
+    // CIC (mass rho accumulated into a zeroed field)
+    CKL("fill", rby<T>(ctx), launch_fill<T>(ctx->nvox * ctx->B, RB<T>(ctx, RB_DELTA), T(0), ctx->stream));
     {
-        PassProgram p = program(cspec<T>(ctx, 0, 1), mspec<T>(ctx, 1, hier ? 6 : 3), ctx->nspec);
+        NodeArgs na{};
+        na.kind = NODE_SCATTER;
+        for (int f = 0; f < 3; ++f) na.spec_in[f] = ctx->spec[SP_PSI + f];
+        na.real_out[0] = ctx->real[RB_DELTA];
+        RUN(node<T>(ctx, na, "node_cic_scatter", 3 * sby<T>(ctx) + rby<T>(ctx), nullptr));
+    }
+    // tidal tensor and density Hessian spectra (Sect. 2.8, App. B)
+    RUN(z_fwd<T>(ctx, creal(ctx, RB_DELTA, 1), mspec<T>(ctx, SP_SCR, 1)));
+    RUN(y_identity<T>(ctx, SP_SCR, 1, true));
+    {
+        PassProgram p = program(cspec<T>(ctx, SP_SCR, 1), mspec<T>(ctx, SP_SCR + 1, hier ? 6 : 3), ctx->nspec);
         add_merge(p, mk(0, 0, 0, 0, 0, R_ONE, invn3));
         add_expand(p, mk(0, 0, 2, 0, 0, R_INVK2, 1.0));
         add_expand(p, mk(0, 1, 1, 0, 0, R_INVK2, 1.0));
@@ -343,7 +377,7 @@ template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelih
     }
     {
         const int nt = hier ? 2 : 1;
-        PassProgram p = program(cspec<T>(ctx, 1, 3 * nt), mspec<T>(ctx, 7, 6 * nt), ctx->nspec);
+        PassProgram p = program(cspec<T>(ctx, SP_SCR + 1, 3 * nt), mspec<T>(ctx, SP_TH, 6 * nt), ctx->nspec);
         for (int h = 0; h < nt; ++h) {
             const int s = 3 * h, d = 6 * h;
             add_expand(p, mk(s + 0, d + 0, 0, 0, 0, R_ONE, 1.0));
@@ -354,17 +388,23 @@ template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelih
             add_expand(p, mk(s + 2, d + 5, 0, 0, 2, R_ONE, 1.0));
         }
         CKL("y_inv", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_inv<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
-        RUN(z_inv<T>(ctx, cspec<T>(ctx, 7, 6 * nt), mreal(ctx, RB_TH, 6 * nt)));
     }
-    // fused web / bias (pass A), normalisation, NB likelihood (pass B)
-    CKL("web_bias", (nth_of(ctx) + 3) * rby<T>(ctx), launch_pass_a<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 12), RB<T>(ctx, RB_DELTA), RB<T>(ctx, RB_SCR),
-                        RB<T>(ctx, RB_SCR + 1), reinterpret_cast<const BiasT<T>*>(ctx->biast), ctx->wp, ctx->partial,
-                        ctx->stream));
-    CKL("reduce", 0.0, launch_reduce(RED_SUMF, ctx->n, ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+    // fused web / bias on the fly (node), normalisation, NB likelihood
+    {
+        NodeArgs na{};
+        na.kind = NODE_WEB_FWD;
+        for (int f = 0; f < nth; ++f) na.spec_in[f] = ctx->spec[SP_TH + f];
+        na.real_in[0] = ctx->real[RB_DELTA];
+        na.real_out[0] = ctx->real[RB_LNF];
+        na.real_out[1] = ctx->real[RB_LNF + 1];
+        int g = 0;
+        RUN(node<T>(ctx, na, "node_web_bias", nth * sby<T>(ctx) + 3 * rby<T>(ctx), &g));
+        CKL("reduce", 0.0, launch_reduce(RED_SUMF, g, ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+    }
     if (likelihood) {
-        CKL("nb_lik", 3 * rby<T>(ctx) + c16b(ctx), launch_pass_b<T>(ctx->n, ctx->B, RB<T>(ctx, RB_SCR), RB<T>(ctx, RB_SCR + 1), ctx->c16, nu, ctx->sc,
+        CKL("nb_lik", 3 * rby<T>(ctx) + c16b(ctx), launch_pass_b<T>(ctx->n, ctx->B, RB<T>(ctx, RB_LNF), RB<T>(ctx, RB_LNF + 1), ctx->c16, nu, ctx->sc,
                             ctx->partial, ctx->stream));
-        CKL("reduce", 0.0, launch_reduce(RED_LIK, ctx->n, ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+        CKL("reduce", 0.0, launch_reduce(RED_LIK, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
     }
     return BRIDGE_OK;
 }
@@ -372,20 +412,27 @@ template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelih
 // ---------------------------------------------------------------------------
 // Adjoint: every forward step transposed, ending with g_nu = d log post/d nu.
 // ---------------------------------------------------------------------------
-template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad) {
+template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad, bool bias_grad) {
     const double invn3 = 1.0 / double(ctx->nvox);
     const bool hier = ctx->nr == 16;
-    const int nth = hier ? 12 : 6;
-    // web + bias + NB adjoint: g_delta (direct), g_T, g_H
-    CKL("web_bias_adj", 2 * (nth_of(ctx) + 1) * rby<T>(ctx) + c16b(ctx), launch_web_adjoint<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 12), RB<T>(ctx, RB_DELTA), ctx->c16,
-                             reinterpret_cast<const BiasT<T>*>(ctx->biast), ctx->wp, ctx->sc,
-                             fields(ctx, RB_SCR, 1 + nth), ctx->partial, ctx->stream));
-    CKL("reduce", 0.0, launch_reduce(RED_BIASGRAD, ctx->n, ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+    const int nth = nth_of(ctx);
+    // web + bias + NB adjoint on the fly: r2c of g_rho (direct), g_T, g_H
+    {
+        NodeArgs na{};
+        na.kind = NODE_WEB_ADJ;
+        na.bias_grad = bias_grad ? 1 : 0;
+        for (int f = 0; f < nth; ++f) na.spec_in[f] = ctx->spec[SP_TH + f];
+        for (int f = 0; f < nth + 1; ++f) na.spec_out[f] = ctx->spec[SP_SCR + f];
+        na.real_in[0] = ctx->real[RB_DELTA];
+        int g = 0;
+        RUN(node<T>(ctx, na, "node_web_bias_adj", (2 * nth + 1) * sby<T>(ctx) + rby<T>(ctx) + c16b(ctx), &g));
+        if (bias_grad)
+            CKL("reduce", 0.0, launch_reduce(RED_BIASGRAD, g, ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+    }
     // spectral adjoint of the tensors (transpose of the forward x node / y expansion)
-    RUN(z_fwd<T>(ctx, creal(ctx, RB_SCR, 1 + nth), mspec<T>(ctx, 0, 1 + nth)));
     {
         const int nslot = hier ? 6 : 4;
-        PassProgram p = program(cspec<T>(ctx, 0, 1 + nth), mspec<T>(ctx, 13, nslot), ctx->nspec);
+        PassProgram p = program(cspec<T>(ctx, SP_SCR, 1 + nth), mspec<T>(ctx, SP_SCR + 13, nslot), ctx->nspec);
         for (int h = 0; h < (hier ? 2 : 1); ++h) {
             const int s = 1 + 6 * h, d = 3 * h;
             add_merge(p, mk(s + 0, d + 0, 0, 0, 0, R_ONE, 1.0));
@@ -395,13 +442,13 @@ template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad) {
             add_merge(p, mk(s + 4, d + 2, 0, 1, 1, R_ONE, 1.0));
             add_merge(p, mk(s + 5, d + 2, 0, 0, 2, R_ONE, 1.0));
         }
-        if (hier) add_merge(p, mk(0, 5, 0, 0, 0, R_ONE, -1.0));   // direct g_delta joins W0' (coef -1 undone below)
+        if (hier) add_merge(p, mk(0, 5, 0, 0, 0, R_ONE, -1.0));   // direct g_rho joins W0' (coef -1 undone below)
         else add_merge(p, mk(0, 3, 0, 0, 0, R_ONE, 1.0));         // own slot
         CKL("y_fwd", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_fwd<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
     {
         const int nslot = hier ? 6 : 4;
-        PassProgram p = program(cspec<T>(ctx, 13, nslot), mspec<T>(ctx, 0, 1), ctx->nspec);
+        PassProgram p = program(cspec<T>(ctx, SP_SCR + 13, nslot), mspec<T>(ctx, SP_SCR, 1), ctx->nspec);
         add_merge(p, mk(0, 0, 2, 0, 0, R_INVK2, invn3));
         add_merge(p, mk(1, 0, 1, 0, 0, R_INVK2, invn3));
         add_merge(p, mk(2, 0, 0, 0, 0, R_INVK2, invn3));
@@ -415,22 +462,28 @@ template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad) {
         add_expand(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));
         CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
-    RUN(y_identity<T>(ctx, 0, 1, false));
-    RUN(z_inv<T>(ctx, cspec<T>(ctx, 0, 1), mreal(ctx, RB_SCR, 1)));         // g_delta (total)
-    // CIC adjoint
-    CKL("cic_gather", 7 * rby<T>(ctx), launch_cic_gather<T>(ctx->n, ctx->B, RB<T>(ctx, RB_SCR), fields(ctx, RB_PSI, 3), fields(ctx, RB_SCR + 1, 3),
-                            ctx->stream));
-    // displacement adjoint
-    RUN(z_fwd<T>(ctx, creal(ctx, RB_SCR + 1, 3), mspec<T>(ctx, 0, 3)));
+    RUN(y_identity<T>(ctx, SP_SCR, 1, false));
+    RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_SCR, 1), mreal(ctx, RB_GD, 1)));       // g_rho (total)
+    // CIC adjoint with the displacement recomputed from its spectra, then r2c
     {
-        PassProgram p = program(cspec<T>(ctx, 0, 3), mspec<T>(ctx, 3, 2), ctx->nspec);
+        NodeArgs na{};
+        na.kind = NODE_GATHER;
+        for (int f = 0; f < 3; ++f) {
+            na.spec_in[f] = ctx->spec[SP_PSI + f];
+            na.spec_out[f] = ctx->spec[SP_SCR + f];
+        }
+        na.real_in[0] = ctx->real[RB_GD];
+        RUN(node<T>(ctx, na, "node_cic_gather", 6 * sby<T>(ctx) + rby<T>(ctx), nullptr));
+    }
+    {
+        PassProgram p = program(cspec<T>(ctx, SP_SCR, 3), mspec<T>(ctx, SP_SCR + 3, 2), ctx->nspec);
         add_merge(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));
         add_merge(p, mk(1, 1, 0, 1, 0, R_ONE, 1.0));
         add_merge(p, mk(2, 1, 0, 0, 1, R_ONE, 1.0));
         CKL("y_fwd", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_fwd<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
     {
-        PassProgram p = program(cspec<T>(ctx, 3, 2), mspec<T>(ctx, 5, 2), ctx->nspec);
+        PassProgram p = program(cspec<T>(ctx, SP_SCR + 3, 2), mspec<T>(ctx, SP_SCR + 5, 2), ctx->nspec);
         const double c = invn3 / ctx->kp.dx;              // conj(-i/dx) = +i/dx
         add_merge(p, mk(0, 0, 1, 0, 0, R_INVK2, 0.0, c));
         add_merge(p, mk(1, 0, 0, 0, 0, R_INVK2, 0.0, c));
@@ -438,16 +491,19 @@ template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad) {
         add_expand(p, mk(0, 1, 0, 0, 0, R_1MKBLEND, 1.0));
         CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
-    RUN(y_identity<T>(ctx, 5, 2, false));
-    RUN(z_inv<T>(ctx, cspec<T>(ctx, 5, 2), mreal(ctx, RB_SCR, 2)));          // g_a, g_b
+    RUN(y_identity<T>(ctx, SP_SCR + 5, 2, false));
+    // ALPT source adjoint on the fly (delta0, phi recomputed from their spectra)
     {
-        const double D = ctx->cfg.growth_d, D2 = ctx->cfg.d2_over_d2 * D * D;
-        CKL("alpt_adj", 16 * rby<T>(ctx), launch_alpt_adjoint<T>(ctx->n, ctx->B, RB<T>(ctx, RB_SCR), RB<T>(ctx, RB_SCR + 1), fields(ctx, RB_ALPT, 7),
-                                  fields(ctx, RB_SCR + 2, 7), D, D2, ctx->stream));
+        NodeArgs na{};
+        na.kind = NODE_ALPT_ADJ;
+        for (int f = 0; f < 7; ++f) na.spec_in[f] = ctx->spec[SP_ALPT + f];
+        na.spec_in[7] = ctx->spec[SP_SCR + 5];
+        na.spec_in[8] = ctx->spec[SP_SCR + 6];
+        for (int f = 0; f < 7; ++f) na.spec_out[f] = ctx->spec[SP_SCR + f];
+        RUN(node<T>(ctx, na, "node_alpt_adj", 16 * sby<T>(ctx), nullptr));
     }
-    RUN(z_fwd<T>(ctx, creal(ctx, RB_SCR + 2, 7), mspec<T>(ctx, 0, 7)));
     {
-        PassProgram p = program(cspec<T>(ctx, 0, 7), mspec<T>(ctx, 7, 4), ctx->nspec);
+        PassProgram p = program(cspec<T>(ctx, SP_SCR, 7), mspec<T>(ctx, SP_SCR + 7, 4), ctx->nspec);
         add_merge(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));   // W0' <- g_delta0
         add_merge(p, mk(1, 1, 0, 0, 0, R_ONE, 1.0));   // V2' <- g_phi_xx
         add_merge(p, mk(2, 2, 0, 1, 0, R_ONE, 1.0));   // V1' <- ky g_phi_xy + kz g_phi_xz
@@ -458,7 +514,7 @@ template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad) {
         CKL("y_fwd", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_fwd<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
     {
-        PassProgram p = program(cspec<T>(ctx, 7, 4), mspec<T>(ctx, 0, 1), ctx->nspec);
+        PassProgram p = program(cspec<T>(ctx, SP_SCR + 7, 4), mspec<T>(ctx, SP_SCR, 1), ctx->nspec);
         add_merge(p, mk(0, 0, 0, 0, 0, R_ONE, invn3));
         add_merge(p, mk(1, 0, 2, 0, 0, R_INVK2, invn3));
         add_merge(p, mk(2, 0, 1, 0, 0, R_INVK2, invn3));
@@ -466,10 +522,16 @@ template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad) {
         add_expand(p, mk(0, 0, 0, 0, 0, R_SQRTP, 1.0));
         CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
-    RUN(y_identity<T>(ctx, 0, 1, false));
-    RUN(z_inv<T>(ctx, cspec<T>(ctx, 0, 1), mreal(ctx, RB_SCR, 1)));
-    // white-noise prior: g_nu = (likelihood part) - nu
-    CKL("prior_grad", 3 * rby<T>(ctx), launch_sub<T>(ctx->nvox * ctx->B, RB<T>(ctx, RB_SCR), nu, grad, ctx->stream));
+    RUN(y_identity<T>(ctx, SP_SCR, 1, false));
+    // inverse z and the white-noise prior: g_nu = (likelihood part) - nu
+    {
+        NodeArgs na{};
+        na.kind = NODE_FINAL;
+        na.spec_in[0] = ctx->spec[SP_SCR];
+        na.real_in[0] = nu;
+        na.real_out[0] = grad;
+        RUN(node<T>(ctx, na, "node_final", sby<T>(ctx) + 2 * rby<T>(ctx), nullptr));
+    }
     return BRIDGE_OK;
 }
 
@@ -505,7 +567,7 @@ template <typename T> int prep_counts(bridge_ctx* ctx, const int32_t* counts) {
     if (!counts) return fail(ctx, BRIDGE_EINVAL, "counts is NULL");
     CK(cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->stream));
     CKL("counts_prep", 3 * c16b(ctx), launch_counts_prep<T>(ctx->n, ctx->B, counts, ctx->c16, ctx->partial, ctx->errflag, ctx->stream));
-    CKL("reduce", 0.0, launch_reduce(RED_NTR, ctx->n, ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+    CKL("reduce", 0.0, launch_reduce(RED_NTR, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
     return BRIDGE_OK;
 }
 
@@ -526,7 +588,7 @@ template <typename T> int do_forward(bridge_ctx* ctx, const void* nu, const int3
     RUN(prep_counts<T>(ctx, counts));
     RUN(run_forward<T>(ctx, reinterpret_cast<const T*>(nu), true));
     if (ln_nbar_out)
-        CKL("lnnbar", 2 * rby<T>(ctx), launch_lnnbar<T>(ctx->nvox, ctx->B, RB<T>(ctx, RB_SCR), ctx->sc, reinterpret_cast<T*>(ln_nbar_out), ctx->stream));
+        CKL("lnnbar", 2 * rby<T>(ctx), launch_lnnbar<T>(ctx->nvox, ctx->B, RB<T>(ctx, RB_LNF), ctx->sc, reinterpret_cast<T*>(ln_nbar_out), ctx->stream));
     RUN(finish(ctx));
     for (int c = 0; c < ctx->B; ++c) {
         if (!std::isfinite(ctx->sc_host[c].logpost)) return fail(ctx, BRIDGE_ENONFINITE, "log posterior is not finite");
@@ -541,7 +603,7 @@ template <typename T> int do_grad(bridge_ctx* ctx, const void* nu, const int32_t
     RUN(upload_bias<T>(ctx, bias));
     RUN(prep_counts<T>(ctx, counts));
     RUN(run_forward<T>(ctx, reinterpret_cast<const T*>(nu), true));
-    RUN(run_adjoint<T>(ctx, reinterpret_cast<const T*>(nu), reinterpret_cast<T*>(grad)));
+    RUN(run_adjoint<T>(ctx, reinterpret_cast<const T*>(nu), reinterpret_cast<T*>(grad), gbias_out != nullptr));
     RUN(finish(ctx));
     for (int c = 0; c < ctx->B; ++c) {
         if (!std::isfinite(ctx->sc_host[c].logpost)) return fail(ctx, BRIDGE_ENONFINITE, "log posterior is not finite");
@@ -564,21 +626,21 @@ template <typename T> int do_leapfrog(bridge_ctx* ctx, void* nu_v, void* p_v, co
     std::vector<double> u0(ctx->B), k0(ctx->B);
     // initial potential and kinetic energy
     RUN(run_forward<T>(ctx, nu, true));
-    RUN(run_adjoint<T>(ctx, nu, g));
+    RUN(run_adjoint<T>(ctx, nu, g, false));
     CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, 0.0, 0.0, ctx->partial, ctx->stream));
-    CKL("reduce", 0.0, launch_reduce(RED_P2, ctx->n, ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+    CKL("reduce", 0.0, launch_reduce(RED_P2, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
     RUN(finish(ctx));
     for (int c = 0; c < ctx->B; ++c) { u0[c] = -ctx->sc_host[c].logpost; k0[c] = 0.5 * ctx->sc_host[c].sump2; }
     // first half kick + drift, then (gradient, full kick + drift) ..., final half kick
     CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, 0.5 * eps, eps, ctx->partial, ctx->stream));
     for (int s = 0; s < n_steps; ++s) {
         RUN(run_forward<T>(ctx, nu, true));
-        RUN(run_adjoint<T>(ctx, nu, g));
+        RUN(run_adjoint<T>(ctx, nu, g, false));
         const bool last = s == n_steps - 1;
         CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, last ? 0.5 * eps : eps, last ? 0.0 : eps, ctx->partial,
                                 ctx->stream));
     }
-    CKL("reduce", 0.0, launch_reduce(RED_P2, ctx->n, ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+    CKL("reduce", 0.0, launch_reduce(RED_P2, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
     RUN(finish(ctx));
     for (int c = 0; c < ctx->B; ++c) {
         const double H0 = u0[c] + k0[c];
@@ -608,21 +670,35 @@ template <typename T> int do_debug(bridge_ctx* ctx, const void* nu, const int32_
     };
     (void)fb;
     switch (which) {
-        case BRIDGE_FIELD_DELTA0: RUN(copy_fields(RB_ALPT, 1)); break;
-        case BRIDGE_FIELD_PSI: RUN(copy_fields(RB_PSI, 3)); break;
-        case BRIDGE_FIELD_DELTA: RUN(copy_fields(RB_DELTA, 1)); break;
-        case BRIDGE_FIELD_TIDAL: RUN(copy_fields(RB_TH, 6)); break;
+        case BRIDGE_FIELD_DELTA0:
+            RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_ALPT, 1), mreal(ctx, RB_SCR, 1)));
+            RUN(copy_fields(RB_SCR, 1));
+            break;
+        case BRIDGE_FIELD_PSI:
+            RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_PSI, 3), mreal(ctx, RB_SCR, 3)));
+            RUN(copy_fields(RB_SCR, 3));
+            break;
+        case BRIDGE_FIELD_DELTA:
+            CKL("shift", 2 * rby<T>(ctx), launch_shift<T>(ctx->nvox * ctx->B, RB<T>(ctx, RB_DELTA), RB<T>(ctx, RB_SCR), T(-1), ctx->stream));
+            RUN(copy_fields(RB_SCR, 1));
+            break;
+        case BRIDGE_FIELD_TIDAL:
+            RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_TH, 6), mreal(ctx, RB_SCR, 6)));
+            RUN(copy_fields(RB_SCR, 6));
+            break;
         case BRIDGE_FIELD_HESSIAN:
             if (ctx->nr != 16) return fail(ctx, BRIDGE_EINVAL, "the density Hessian exists only for 16 regions");
-            RUN(copy_fields(RB_TH + 6, 6));
+            RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_TH + 6, 6), mreal(ctx, RB_SCR, 6)));
+            RUN(copy_fields(RB_SCR, 6));
             break;
         case BRIDGE_FIELD_LAMBDA:
-            CKL("eigs", 9 * rby<T>(ctx), launch_eigs<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 6), fields(ctx, RB_SCR + 2, 3), ctx->stream));
-            RUN(copy_fields(RB_SCR + 2, 3));
+            RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_TH, 6), mreal(ctx, RB_SCR, 6)));
+            CKL("eigs", 9 * rby<T>(ctx), launch_eigs<T>(ctx->n, ctx->B, fields(ctx, RB_SCR, 6), fields(ctx, RB_SCR, 3), ctx->stream));
+            RUN(copy_fields(RB_SCR, 3));
             break;
         case BRIDGE_FIELD_LNNBAR:
-            CKL("lnnbar", 2 * rby<T>(ctx), launch_lnnbar<T>(ctx->nvox, ctx->B, RB<T>(ctx, RB_SCR), ctx->sc, RB<T>(ctx, RB_SCR + 2), ctx->stream));
-            RUN(copy_fields(RB_SCR + 2, 1));
+            CKL("lnnbar", 2 * rby<T>(ctx), launch_lnnbar<T>(ctx->nvox, ctx->B, RB<T>(ctx, RB_LNF), ctx->sc, RB<T>(ctx, RB_SCR), ctx->stream));
+            RUN(copy_fields(RB_SCR, 1));
             break;
         default: return fail(ctx, BRIDGE_EINVAL, "unknown field selector");
     }
@@ -700,7 +776,7 @@ int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
     ctx->wp.rho_floor = cfg->rho_floor;
     ctx->wp.tau = cfg->precision == BRIDGE_FP64 ? 1e-10 : 1e-4;
     ctx->wp.n_regions = cfg->n_regions;
-    if (upload_twiddles() != cudaSuccess) { delete ctx; return BRIDGE_ECUDA; }
+    if (upload_twiddles() != cudaSuccess || upload_node_twiddles() != cudaSuccess) { delete ctx; return BRIDGE_ECUDA; }
     const Plan pl = make_plan(cfg);
     if (cudaMalloc(&ctx->ws, pl.total) != cudaSuccess) { cudaGetLastError(); delete ctx; return BRIDGE_ENOMEM; }
     ctx->ws_bytes = pl.total;
@@ -713,6 +789,14 @@ int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
     ctx->sc = reinterpret_cast<ChainScalars*>(w); w += pl.sc_bytes;
     ctx->biasd = reinterpret_cast<BiasD*>(w); w += pl.biasd_bytes;
     ctx->biast = w; w += pl.biast_bytes;
+    ctx->node_scratch = w; w += pl.node_bytes;
+    {
+        const size_t need = cfg->precision == BRIDGE_FP64 ? node_scratch_bytes<double>(cfg->n, cfg->batch)
+                                                         : node_scratch_bytes<float>(cfg->n, cfg->batch);
+        const int grid = cfg->precision == BRIDGE_FP64 ? node_max_grid<double>(cfg->n, cfg->batch)
+                                                      : node_max_grid<float>(cfg->n, cfg->batch);
+        if (need > pl.node_bytes || grid > 1024) { bridge_destroy(ctx); return BRIDGE_ECUDA; }
+    }
     if (cudaMalloc(&ctx->errflag, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&ctx->sc_host, sizeof(ChainScalars) * ctx->B) != cudaSuccess ||
         cudaMallocHost(&ctx->biasd_host, sizeof(BiasD) * ctx->B) != cudaSuccess ||

@@ -20,31 +20,14 @@
 
 #include "common.cuh"
 #include "passes.cuh"
+#include "ztile.cuh"
+#include "twiddle.cuh"
 
 namespace bridge {
 
-// Twiddle tables: entry N + j holds exp(-2 pi i j / N) for N = 2..512.
-constexpr int kTwTable = 1024;
-__device__ float2 g_tw_f[kTwTable];
-__device__ double2 g_tw_d[kTwTable];
-template <typename T> __device__ __forceinline__ cplx_t<T> tw_load(int N, int j);
-template <> __device__ __forceinline__ float2 tw_load<float>(int N, int j) { return __ldg(&g_tw_f[N + j]); }
-template <> __device__ __forceinline__ double2 tw_load<double>(int N, int j) { return __ldg(&g_tw_d[N + j]); }
+cudaError_t upload_twiddles() { return upload_twiddles_here(); }
 
-cudaError_t upload_twiddles() {
-    static float2 hf[kTwTable];
-    static double2 hd[kTwTable];
-    for (int n = 2; n <= 512; n *= 2) {
-        for (int j = 0; j < n; ++j) {
-            const double a = -2.0 * kPi * double(j) / double(n);
-            hd[n + j] = make_double2(std::cos(a), std::sin(a));
-            hf[n + j] = make_float2(float(std::cos(a)), float(std::sin(a)));
-        }
-    }
-    cudaError_t e = cudaMemcpyToSymbol(g_tw_f, hf, sizeof(hf));
-    if (e != cudaSuccess) return e;
-    return cudaMemcpyToSymbol(g_tw_d, hd, sizeof(hd));
-}
+template <typename T> __device__ __forceinline__ cplx_t<T> tw_load(int N, int j) { return ztw_load<T>(N, j); }
 
 // ---------------------------------------------------------------------------
 // Multipliers
@@ -374,156 +357,38 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT) k_x_node(const PassProgr
 }
 
 // ---------------------------------------------------------------------------
-// z pass.  Tile: 16 consecutive x by GY consecutive y; complex line c packs the
-// real lines at x0 + 2(c % 8) and x0 + 2(c % 8) + 1 of row y0 + c / 8.
+// stand-alone z passes (whole fields), tile functions in ztile.cuh
 // ---------------------------------------------------------------------------
-template <typename T, int N> struct ZTile {
-    using V = cplx_t<T>;
-    static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, J = N1 / N2;
-    static constexpr int GY0 = 256 / (8 * N2);
-    static constexpr int GY = GY0 < N ? GY0 : N;
-    static constexpr int GC = 8 * GY;                 // complex lines per tile
-    static constexpr int NT = GC * N2;
-    static constexpr int SM_A = GC * N1 * (N2 + 1);   // transpose buffer
-    static constexpr int ZS = N + 1;                  // natural-order row stride
-    static constexpr int SM_Z = GC * ZS;
-    static constexpr int SM_ELEMS = SM_A > SM_Z ? SM_A : SM_Z;
-    static constexpr int TILES = (N / 16) * (N / GY);
-    __device__ static int sidx(int c, int k1, int n2) { return c * (N1 * (N2 + 1)) + k1 * (N2 + 1) + n2; }
-};
+template <typename T, int N> using ZPass = ZCfg<T, N, 256 / (8 * Split<N>::N2)>;
 
 template <typename T, int N>
-__global__ void __launch_bounds__(ZTile<T, N>::NT) k_z_fwd(const ZProgram P) {
-    using ZT = ZTile<T, N>;
+__global__ void __launch_bounds__(ZPass<T, N>::NT) k_z_fwd(const ZProgram P) {
+    using ZT = ZPass<T, N>;
     using V = cplx_t<T>;
-    using V4 = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* sm = reinterpret_cast<V*>(smraw);
-    const int t = threadIdx.x;
     const int f = blockIdx.y, chain = blockIdx.z;
-    const int x0 = (blockIdx.x % (N / 16)) * 16, y0 = (blockIdx.x / (N / 16)) * ZT::GY;
-    const T* __restrict__ rin = reinterpret_cast<const T*>(P.in[f]) + chain * P.in_cs;
-    // step A: pack two real lines, N1-point DFTs
-    {
-        const int n2 = t % ZT::N2, c = t / ZT::N2;
-        const int y = y0 + c / 8, xa = x0 + 2 * (c % 8);
-        const T* la = rin + (size_t(xa) * N + y) * N;
-        const T* lb = la + size_t(N) * N;
-        V v[ZT::N1];
-#pragma unroll
-        for (int n1 = 0; n1 < ZT::N1; ++n1) v[n1] = cmake<V>(la[ZT::N2 * n1 + n2], lb[ZT::N2 * n1 + n2]);
-        dft_dif<ZT::N1, 1, -1>(v);
-#pragma unroll
-        for (int i = 0; i < ZT::N1; ++i) {
-            const int k1 = bitrev(i, ZT::N1);
-            sm[ZT::sidx(c, k1, n2)] = cmul(v[i], tw_load<T>(N, n2 * k1));
-        }
-    }
-    __syncthreads();
-    // step B, then natural-order line spectra Z[c][k]
-    {
-        const int c = t / ZT::N2;
-        V X[ZT::J][ZT::N2];
-#pragma unroll
-        for (int j = 0; j < ZT::J; ++j) {
-            const int k1 = t % ZT::N2 + j * ZT::N2;
-#pragma unroll
-            for (int n2 = 0; n2 < ZT::N2; ++n2) X[j][n2] = sm[ZT::sidx(c, k1, n2)];
-            dft_dif<ZT::N2, 1, -1>(X[j]);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < ZT::J; ++j) {
-            const int k1 = t % ZT::N2 + j * ZT::N2;
-#pragma unroll
-            for (int i = 0; i < ZT::N2; ++i) sm[c * ZT::ZS + k1 + ZT::N1 * bitrev(i, ZT::N2)] = X[j][i];
-        }
-    }
-    __syncthreads();
-    // separate the two real lines and store [kz][y][x] as (A, B) pairs
-    V* __restrict__ sout = reinterpret_cast<V*>(P.out[f]) + chain * P.out_cs;
-    constexpr int ROWS = ZT::NT / 8;
-    const int pair = t % 8;
-    for (int idx = t / 8; idx < (N / 2 + 1) * ZT::GY; idx += ROWS) {
-        const int kz = idx / ZT::GY, yl = idx % ZT::GY;
-        const int c = yl * 8 + pair;
-        const V z1 = sm[c * ZT::ZS + kz];
-        const V z2 = sm[c * ZT::ZS + ((N - kz) & (N - 1))];
-        const T h = T(0.5);
-        V4 ab;
-        ab.x = h * (z1.x + z2.x);
-        ab.y = h * (z1.y - z2.y);
-        ab.z = h * (z1.y + z2.y);
-        ab.w = h * (z2.x - z1.x);
-        *reinterpret_cast<V4*>(sout + (size_t(kz) * N + (y0 + yl)) * N + x0 + 2 * pair) = ab;
-    }
+    int x0, y0;
+    ZT::tile_xy(blockIdx.x, x0, y0);
+    const T* rin = reinterpret_cast<const T*>(P.in[f]) + chain * P.in_cs;
+    auto line = [&](int c) { return rin + (size_t(x0 + 2 * (c % 8)) * N + y0 + c / 8) * N; };
+    ztile_fwd<ZT>(line, (long long)N * N, reinterpret_cast<V*>(P.out[f]) + chain * P.out_cs, x0, y0, sm,
+                  threadIdx.x);
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(ZTile<T, N>::NT) k_z_inv(const ZProgram P) {
-    using ZT = ZTile<T, N>;
+__global__ void __launch_bounds__(ZPass<T, N>::NT) k_z_inv(const ZProgram P) {
+    using ZT = ZPass<T, N>;
     using V = cplx_t<T>;
-    using V4 = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* sm = reinterpret_cast<V*>(smraw);
-    const int t = threadIdx.x;
     const int f = blockIdx.y, chain = blockIdx.z;
-    const int x0 = (blockIdx.x % (N / 16)) * 16, y0 = (blockIdx.x / (N / 16)) * ZT::GY;
-    const V* __restrict__ sin_ = reinterpret_cast<const V*>(P.in[f]) + chain * P.in_cs;
-    // load (A, B) pairs, build Z = A + iB on the full circle
-    constexpr int ROWS = ZT::NT / 8;
-    const int pair = t % 8;
-    for (int idx = t / 8; idx < (N / 2 + 1) * ZT::GY; idx += ROWS) {
-        const int kz = idx / ZT::GY, yl = idx % ZT::GY;
-        const int c = yl * 8 + pair;
-        const V4 ab = *reinterpret_cast<const V4*>(sin_ + (size_t(kz) * N + (y0 + yl)) * N + x0 + 2 * pair);
-        if (kz == 0 || kz == N / 2) {
-            sm[c * ZT::ZS + kz] = cmake<V>(ab.x, ab.z);   // real parts only
-        } else {
-            sm[c * ZT::ZS + kz] = cmake<V>(ab.x - ab.w, ab.y + ab.z);
-            sm[c * ZT::ZS + (N - kz)] = cmake<V>(ab.x + ab.w, ab.z - ab.y);
-        }
-    }
-    __syncthreads();
-    {
-        const int c = t / ZT::N2;
-        V Y[ZT::J][ZT::N2];
-#pragma unroll
-        for (int j = 0; j < ZT::J; ++j) {
-            const int k1 = t % ZT::N2 + j * ZT::N2;
-#pragma unroll
-            for (int k2 = 0; k2 < ZT::N2; ++k2) Y[j][k2] = sm[c * ZT::ZS + k1 + ZT::N1 * k2];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < ZT::J; ++j) {
-            const int k1 = t % ZT::N2 + j * ZT::N2;
-            dft_dif<ZT::N2, 1, +1>(Y[j]);
-#pragma unroll
-            for (int i = 0; i < ZT::N2; ++i) {
-                const int n2 = bitrev(i, ZT::N2);
-                sm[ZT::sidx(c, k1, n2)] = cmulc(Y[j][i], tw_load<T>(N, n2 * k1));
-            }
-        }
-    }
-    __syncthreads();
-    {
-        const int n2 = t % ZT::N2, c = t / ZT::N2;
-        const int y = y0 + c / 8, xa = x0 + 2 * (c % 8);
-        T* __restrict__ rout = reinterpret_cast<T*>(P.out[f]) + chain * P.out_cs;
-        T* la = rout + (size_t(xa) * N + y) * N;
-        T* lb = la + size_t(N) * N;
-        V v[ZT::N1];
-#pragma unroll
-        for (int k1 = 0; k1 < ZT::N1; ++k1) v[k1] = sm[ZT::sidx(c, k1, n2)];
-        dft_dif<ZT::N1, 1, +1>(v);
-#pragma unroll
-        for (int i = 0; i < ZT::N1; ++i) {
-            const int pos = n2 + ZT::N2 * bitrev(i, ZT::N1);
-            la[pos] = v[i].x;
-            lb[pos] = v[i].y;
-        }
-    }
+    int x0, y0;
+    ZT::tile_xy(blockIdx.x, x0, y0);
+    T* rout = reinterpret_cast<T*>(P.out[f]) + chain * P.out_cs;
+    auto line = [&](int c) { return rout + (size_t(x0 + 2 * (c % 8)) * N + y0 + c / 8) * N; };
+    ztile_inv<ZT>(reinterpret_cast<const V*>(P.in[f]) + chain * P.in_cs, line, (long long)N * N, x0, y0, sm,
+                  threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -558,7 +423,7 @@ template <typename K> static cudaError_t set_smem(K kernel, size_t bytes) {
 #endif
 
 template <typename T, int N> static cudaError_t z_fwd_n(int batch, const ZProgram& p, cudaStream_t s) {
-    using ZT = ZTile<T, N>;
+    using ZT = ZPass<T, N>;
     const size_t sm = size_t(ZT::SM_ELEMS) * sizeof(cplx_t<T>);
     cudaError_t e = set_smem(k_z_fwd<T, N>, sm);
     if (e != cudaSuccess) return e;
@@ -566,7 +431,7 @@ template <typename T, int N> static cudaError_t z_fwd_n(int batch, const ZProgra
     return cudaGetLastError();
 }
 template <typename T, int N> static cudaError_t z_inv_n(int batch, const ZProgram& p, cudaStream_t s) {
-    using ZT = ZTile<T, N>;
+    using ZT = ZPass<T, N>;
     const size_t sm = size_t(ZT::SM_ELEMS) * sizeof(cplx_t<T>);
     cudaError_t e = set_smem(k_z_inv<T, N>, sm);
     if (e != cudaSuccess) return e;

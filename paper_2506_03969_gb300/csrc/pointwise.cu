@@ -99,21 +99,12 @@ template <typename T> __global__ void k_fill(long long count, T* p, T v) {
 
 // ---------------------------------------------------------------------------
 // CIC (mass assignment): the particle of cell q sits at q + psi (cell units);
-// trilinear weights to the 8 surrounding cells, periodic.  delta must hold -1
-// on entry (one particle per cell: delta = rho - 1).
+// trilinear weights to the 8 surrounding cells, periodic.  The kernel
+// accumulates the mass rho = 1 + delta (one particle per cell) into a zeroed
+// field: small masses keep full relative precision, which the likelihood
+// needs (d ln nbar / d rho ~ alpha / rho in nearly empty cells).  The spectra of
+// rho and delta differ only at k = 0, where every tensor operator vanishes.
 // ---------------------------------------------------------------------------
-template <typename T> struct CicCorner {
-    int i0[3];
-    T f[3];
-};
-template <typename T> __device__ __forceinline__ void cic_corner(long long q, int N, T px, T py, T pz, CicCorner<T>& c) {
-    const int lg = __ffs(N) - 1;
-    const int qz = (int)(q & (N - 1)), qy = (int)((q >> lg) & (N - 1)), qx = (int)(q >> (2 * lg));
-    const T fx = floor(px), fy = floor(py), fz = floor(pz);
-    c.f[0] = px - fx; c.f[1] = py - fy; c.f[2] = pz - fz;
-    c.i0[0] = qx + (int)fx; c.i0[1] = qy + (int)fy; c.i0[2] = qz + (int)fz;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kPwThreads) k_cic_scatter(int N, long long nvox, Fields16 psi3, T* delta) {
     const size_t off = (size_t)blockIdx.y * nvox;
@@ -184,41 +175,17 @@ template <typename T> __device__ __forceinline__ void load6(const Fields16& f, i
     for (int q = 0; q < 6; ++q) out[q] = ((const T*)f.p[base + q])[j];
 }
 
-template <typename T, int NR> struct WebState {
-    Eig3<T> ephi, edel;
-    T wphi[3], pphi[4], wdel[3], pdel[4];
-    T wts[NR];
-    VoxParams<T> q;
-    LnF<T> lf;
-};
-
 template <typename T, int NR>
-__device__ __forceinline__ void web_forward(const Fields16& th, size_t j, T delta, const BiasT<T>& B,
+__device__ __forceinline__ void web_forward(const Fields16& th, size_t j, T rho_mass, const BiasT<T>& B,
                                             const WebParams& wp, WebState<T, NR>& S) {
-    T a6[6];
+    T a6[6], h6[6];
     load6<T>(th, 0, j, a6);
-    eig3<T>(a6, S.ephi);
-    T lam[3] = {S.ephi.m + S.ephi.mu[0], S.ephi.m + S.ephi.mu[1], S.ephi.m + S.ephi.mu[2]};
-    memberships<T>(lam, T(wp.sharpness), T(wp.th_phi), S.wphi, S.pphi);
-    if constexpr (NR == 16) {
-        load6<T>(th, 6, j, a6);
-        eig3<T>(a6, S.edel);
-        T ld[3] = {S.edel.m + S.edel.mu[0], S.edel.m + S.edel.mu[1], S.edel.m + S.edel.mu[2]};
-        memberships<T>(ld, T(wp.sharpness), T(wp.th_delta), S.wdel, S.pdel);
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) S.wts[4 * a + b] = S.pphi[a] * S.pdel[b];
-    } else {
-#pragma unroll
-        for (int a = 0; a < 4; ++a) S.wts[a] = S.pphi[a];
-    }
-    interp_params<T, NR>(B, S.wts, S.q);
-    log_f<T>(delta, T(wp.rho_floor), S.q, S.lf);
+    if constexpr (NR == 16) load6<T>(th, 6, j, h6);
+    web_eval<T, NR>(a6, h6, rho_mass, B, wp, S);
 }
 
 template <typename T, int NR>
-__global__ void __launch_bounds__(kPwThreads) k_pass_a(long long nvox, Fields16 th, const T* delta, T* lnf_out,
+__global__ void __launch_bounds__(kPwThreads) k_pass_a(long long nvox, Fields16 th, const T* rho, T* lnf_out,
                                                       T* beta_out, const BiasT<T>* bias, WebParams wp, double* partial) {
     __shared__ BiasT<T> B;
     const int chain = blockIdx.y;
@@ -232,7 +199,7 @@ __global__ void __launch_bounds__(kPwThreads) k_pass_a(long long nvox, Fields16 
     PW_LOOP(i, nvox) {
         const size_t j = off + i;
         WebState<T, NR> S;
-        web_forward<T, NR>(th, j, delta[j], B, wp, S);
+        web_forward<T, NR>(th, j, rho[j], B, wp, S);
         lnf_out[j] = S.lf.lnf;
         beta_out[j] = S.q.beta;
         accf += v_exp(S.lf.lnf);
@@ -267,13 +234,13 @@ __global__ void __launch_bounds__(kPwThreads) k_pass_b(long long nvox, const T* 
 }
 
 // ---------------------------------------------------------------------------
-// Web + bias + NB adjoint: g_delta (direct), g_T (6), g_H (6) and the
-// partial sums of d/d alpha_r and d/d beta_r.
+// Web + bias + NB adjoint: g_delta (direct), g_T (6), g_H (6) and, when
+// requested (BIASG), the partial sums of d/d alpha_r and d/d beta_r.
 // ---------------------------------------------------------------------------
-template <typename T, int NR>
-__global__ void __launch_bounds__(kPwThreads) k_web_adj(long long nvox, Fields16 th, const T* delta,
-                                                       const uint16_t* c16, const BiasT<T>* bias, WebParams wp,
-                                                       const ChainScalars* sc, Fields16 out, double* partial) {
+template <typename T, int NR, bool BIASG>
+__global__ void __launch_bounds__(kPwThreads, 2) k_web_adj(long long nvox, Fields16 th, const T* rho,
+                                                          const uint16_t* c16, const BiasT<T>* bias, WebParams wp,
+                                                          const ChainScalars* sc, Fields16 out, double* partial) {
     __shared__ BiasT<T> B;
     const int chain = blockIdx.y;
     if (threadIdx.x == 0) B = bias[chain];
@@ -281,88 +248,40 @@ __global__ void __launch_bounds__(kPwThreads) k_web_adj(long long nvox, Fields16
     const size_t off = (size_t)chain * nvox;
     const T lnC = T(sc[chain].lnC);
     const T gscale = T(sc[chain].G / sc[chain].ntr);   // f_i/sum f * G = nbar_i * G / N_tr
-    const T s = T(wp.sharpness), tau = T(wp.tau);
-    T ga[NR], gb[NR];
+    constexpr int NG = BIASG ? NR : 1;
+    T ga[NG], gb[NG];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) ga[r] = gb[r] = T(0);
+    for (int r = 0; r < NG; ++r) ga[r] = gb[r] = T(0);
     PW_LOOP(i, nvox) {
         const size_t j = off + i;
-        const T dl = delta[j];
+        const T dl = rho[j];
         WebState<T, NR> S;
         web_forward<T, NR>(th, j, dl, B, wp, S);
-        const T lnnbar = S.lf.lnf + lnC;
-        NB<T> nb;
-        nb_eval<T>((int)c16[j], lnnbar, S.q.beta, true, nb);
-        const T nbar = v_exp(lnnbar);
-        const T glnf = nb.g_lnnbar - nbar * gscale;      // normalisation adjoint
-        const T gbeta = nb.g_beta;
-        // d ln f / d(parameters)
-        const T g_a = glnf / S.q.a;
-        const T g_al = glnf * S.lf.lnu;
-        const T g_rho = glnf * S.q.eps * S.lf.t1 / S.q.rho;
-        const T g_eps = -glnf * S.lf.t1 * (S.lf.lnu - S.lf.lnrho);
-        T g_rhop = T(0), g_epsp = T(0);
-        if (S.q.rhop > T(0)) {
-            g_rhop = -glnf * S.q.epsp * S.lf.t2 / S.q.rhop;
-            g_epsp = -glnf * S.lf.t2 * (S.lf.lnrhop - S.lf.lnu);
-        }
-        // direct density derivative (zero below the floor)
-        const T u = v_exp(S.lf.lnu);
-        const T gdel = S.lf.floored ? T(0) : glnf * (S.q.alpha - S.q.eps * S.lf.t1 + S.q.epsp * S.lf.t2) / u;
-        // region weights
-        T gw[NR];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            gw[r] = g_a * B.a[r] + g_al * B.alpha[r] + g_rho * B.rho[r] + g_eps * B.eps[r] + g_rhop * B.rhop[r] +
-                    g_epsp * B.epsp[r] + gbeta * B.beta[r];
-            ga[r] += g_al * S.wts[r];
-            gb[r] += gbeta * S.wts[r];
-        }
-        T gpphi[4], gpdel[4];
-        if constexpr (NR == 16) {
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                gpphi[a] = T(0);
-                gpdel[a] = T(0);
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    gpphi[a] += gw[4 * a + b] * S.pdel[b];
-                    gpdel[b] += gw[4 * a + b] * S.pphi[a];
-                }
-        } else {
-#pragma unroll
-            for (int a = 0; a < 4; ++a) gpphi[a] = gw[a];
-        }
-        // memberships -> eigenvalues -> tensor (stored components)
-        T gt[6];
-        {
-            const T g1 = (gpphi[1] - gpphi[0]) * s * S.wphi[0] * (T(1) - S.wphi[0]);
-            const T g2 = (gpphi[2] - gpphi[1]) * s * S.wphi[1] * (T(1) - S.wphi[1]);
-            const T g3 = (gpphi[3] - gpphi[2]) * s * S.wphi[2] * (T(1) - S.wphi[2]);
-            eig_adjoint<T>(S.ephi, g1, g2, g3, tau, gt);
-        }
-        ((T*)out.p[0])[j] = gdel;
+        T gd, gt[6], gh[6];
+        web_adjoint_voxel<T, NR, BIASG>(S, dl, (int)c16[j], lnC, gscale, B, wp, gd, gt, gh, ga, gb);
+        ((T*)out.p[0])[j] = gd;
 #pragma unroll
         for (int q = 0; q < 6; ++q) ((T*)out.p[1 + q])[j] = gt[q];
         if constexpr (NR == 16) {
-            const T g1 = (gpdel[1] - gpdel[0]) * s * S.wdel[0] * (T(1) - S.wdel[0]);
-            const T g2 = (gpdel[2] - gpdel[1]) * s * S.wdel[1] * (T(1) - S.wdel[1]);
-            const T g3 = (gpdel[3] - gpdel[2]) * s * S.wdel[2] * (T(1) - S.wdel[2]);
-            eig_adjoint<T>(S.edel, g1, g2, g3, tau, gt);
 #pragma unroll
-            for (int q = 0; q < 6; ++q) ((T*)out.p[7 + q])[j] = gt[q];
+            for (int q = 0; q < 6; ++q) ((T*)out.p[7 + q])[j] = gh[q];
         }
     }
-    double acc[2 * NR];
+    if constexpr (BIASG) {
+        double acc[2 * NR];
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        acc[r] = (double)ga[r];
-        acc[NR + r] = (double)gb[r];
+        for (int r = 0; r < NR; ++r) {
+            acc[r] = (double)ga[r];
+            acc[NR + r] = (double)gb[r];
+        }
+        write_partials<2 * NR>(acc, partial);
     }
-    write_partials<2 * NR>(acc, partial);
+}
+
+
+template <typename T> __global__ void k_shift(long long count, const T* in, T* out, T c) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+        out[i] = in[i] + c;
 }
 
 template <typename T> __global__ void k_sub(long long count, const T* r, const T* nu, T* out) {
@@ -422,40 +341,41 @@ __device__ double lognormal_dlogpdf(double b, double mu, double sigma) {
     return -1.0 / b - (lb - mu) / (sigma * sigma * b);
 }
 
-__global__ void __launch_bounds__(kPwThreads) k_reduce(int what, int nblk, int K, const double* partial,
-                                                      ChainScalars* sc, const BiasD* bias, int n_regions) {
-    __shared__ double sh[kPwThreads / 32];
+__global__ void __launch_bounds__(1024) k_reduce(int what, int nblk, int K, const double* partial, ChainScalars* sc,
+                                                 const BiasD* bias, int n_regions) {
+    __shared__ double tot[32];
     const int chain = blockIdx.x;
     ChainScalars& S = sc[chain];
-    for (int k = 0; k < K; ++k) {
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (k < K) {
         double v = 0.0;
-        for (int b = threadIdx.x; b < nblk; b += kPwThreads) v += partial[((size_t)chain * nblk + b) * K + k];
-        const double tot = block_sum<kPwThreads>(v, sh);
-        if (threadIdx.x == 0) {
-            if (what == RED_NTR) S.ntr = tot;
-            else if (what == RED_SUMF) { S.sumf = tot; S.lnC = log(S.ntr) - log(tot); }
-            else if (what == RED_LIK) { if (k == 0) S.loglik = tot; else if (k == 1) S.G = tot; else S.sumnu2 = tot; }
-            else if (what == RED_BIASGRAD) S.gbias[k] = tot;
-            else if (what == RED_P2) S.sump2 = tot;
-        }
+        for (int b = lane; b < nblk; b += 32) v += partial[((size_t)chain * nblk + b) * K + k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) tot[k] = v;
     }
-    if (threadIdx.x == 0) {
-        const BiasD& Bd = bias[chain];
-        if (what == RED_LIK) {
-            double lp = 0.0;
-            for (int r = 0; r < n_regions; ++r)
-                if ((Bd.prior_mask >> r) & 1u)
-                    lp += lognormal_logpdf(Bd.alpha[r], Bd.mu_alpha, Bd.sigma_alpha) +
-                          lognormal_logpdf(Bd.beta[r], Bd.mu_beta, Bd.sigma_beta);
-            S.logprior = lp;
-            S.logpost = -0.5 * S.sumnu2 + S.loglik + lp;
-        } else if (what == RED_BIASGRAD) {
-            for (int r = 0; r < n_regions; ++r)
-                if ((Bd.prior_mask >> r) & 1u) {
-                    S.gbias[r] += lognormal_dlogpdf(Bd.alpha[r], Bd.mu_alpha, Bd.sigma_alpha);
-                    S.gbias[n_regions + r] += lognormal_dlogpdf(Bd.beta[r], Bd.mu_beta, Bd.sigma_beta);
-                }
-        }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const BiasD& Bd = bias[chain];
+    if (what == RED_NTR) S.ntr = tot[0];
+    else if (what == RED_SUMF) { S.sumf = tot[0]; S.lnC = log(S.ntr) - log(tot[0]); }
+    else if (what == RED_P2) S.sump2 = tot[0];
+    else if (what == RED_LIK) {
+        S.loglik = tot[0]; S.G = tot[1]; S.sumnu2 = tot[2];
+        double lp = 0.0;
+        for (int r = 0; r < n_regions; ++r)
+            if ((Bd.prior_mask >> r) & 1u)
+                lp += lognormal_logpdf(Bd.alpha[r], Bd.mu_alpha, Bd.sigma_alpha) +
+                      lognormal_logpdf(Bd.beta[r], Bd.mu_beta, Bd.sigma_beta);
+        S.logprior = lp;
+        S.logpost = -0.5 * S.sumnu2 + S.loglik + lp;
+    } else if (what == RED_BIASGRAD) {
+        for (int q = 0; q < K; ++q) S.gbias[q] = tot[q];
+        for (int r = 0; r < n_regions; ++r)
+            if ((Bd.prior_mask >> r) & 1u) {
+                S.gbias[r] += lognormal_dlogpdf(Bd.alpha[r], Bd.mu_alpha, Bd.sigma_alpha);
+                S.gbias[n_regions + r] += lognormal_dlogpdf(Bd.beta[r], Bd.mu_beta, Bd.sigma_beta);
+            }
     }
 }
 
@@ -504,11 +424,15 @@ cudaError_t launch_pass_b(int n, int batch, const T* lnf, const T* beta_i, const
 template <typename T>
 cudaError_t launch_web_adjoint(int n, int batch, const Fields16& th, const T* delta, const uint16_t* c16,
                                const BiasT<T>* bias, const WebParams& wp, const ChainScalars* sc,
-                               const Fields16& out, double* partial, cudaStream_t s) {
-    if (wp.n_regions == 16)
-        k_web_adj<T, 16><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), th, delta, c16, bias, wp, sc, out, partial);
-    else
-        k_web_adj<T, 4><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), th, delta, c16, bias, wp, sc, out, partial);
+                               const Fields16& out, double* partial, bool bias_grad, cudaStream_t s) {
+    const dim3 g(pw_blocks(n), batch);
+    if (wp.n_regions == 16) {
+        if (bias_grad) k_web_adj<T, 16, true><<<g, kPwThreads, 0, s>>>(nvox_of(n), th, delta, c16, bias, wp, sc, out, partial);
+        else k_web_adj<T, 16, false><<<g, kPwThreads, 0, s>>>(nvox_of(n), th, delta, c16, bias, wp, sc, out, partial);
+    } else {
+        if (bias_grad) k_web_adj<T, 4, true><<<g, kPwThreads, 0, s>>>(nvox_of(n), th, delta, c16, bias, wp, sc, out, partial);
+        else k_web_adj<T, 4, false><<<g, kPwThreads, 0, s>>>(nvox_of(n), th, delta, c16, bias, wp, sc, out, partial);
+    }
     return cudaGetLastError();
 }
 template <typename T>
@@ -521,6 +445,11 @@ template <typename T>
 cudaError_t launch_alpt_adjoint(int n, int batch, const T* ga, const T* gb, const Fields16& in7,
                                 const Fields16& out7, double growth, double d2, cudaStream_t s) {
     k_alpt_adj<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), ga, gb, in7, out7, T(growth), T(d2));
+    return cudaGetLastError();
+}
+template <typename T> cudaError_t launch_shift(long long count, const T* in, T* out, T c, cudaStream_t s) {
+    long long b = (count + 1023) / 1024;
+    k_shift<T><<<(unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b)), 256, 0, s>>>(count, in, out, c);
     return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_sub(long long count, const T* r, const T* nu, T* out, cudaStream_t s) {
@@ -545,10 +474,10 @@ cudaError_t launch_eigs(int n, int batch, const Fields16& t6, const Fields16& ou
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(int what, int n, int batch, const double* partial, ChainScalars* sc, const BiasD* bias,
+cudaError_t launch_reduce(int what, int nblk, int batch, const double* partial, ChainScalars* sc, const BiasD* bias,
                           int n_regions, cudaStream_t s) {
     int K = what == RED_LIK ? 3 : (what == RED_BIASGRAD ? 2 * n_regions : 1);
-    k_reduce<<<batch, kPwThreads, 0, s>>>(what, pw_blocks(n), K, partial, sc, bias, n_regions);
+    k_reduce<<<batch, 32 * K, 0, s>>>(what, nblk, K, partial, sc, bias, n_regions);
     return cudaGetLastError();
 }
 
@@ -563,11 +492,12 @@ cudaError_t launch_reduce(int what, int n, int batch, const double* partial, Cha
                                           const ChainScalars*, double*, cudaStream_t);                              \
     template cudaError_t launch_web_adjoint<T>(int, int, const Fields16&, const T*, const uint16_t*,                \
                                                const BiasT<T>*, const WebParams&, const ChainScalars*,              \
-                                               const Fields16&, double*, cudaStream_t);                             \
+                                               const Fields16&, double*, bool, cudaStream_t);                       \
     template cudaError_t launch_cic_gather<T>(int, int, const T*, const Fields16&, const Fields16&, cudaStream_t);  \
     template cudaError_t launch_alpt_adjoint<T>(int, int, const T*, const T*, const Fields16&, const Fields16&,     \
                                                 double, double, cudaStream_t);                                      \
     template cudaError_t launch_sub<T>(long long, const T*, const T*, T*, cudaStream_t);                            \
+    template cudaError_t launch_shift<T>(long long, const T*, T*, T, cudaStream_t);                                 \
     template cudaError_t launch_kick_drift<T>(int, int, T*, T*, const T*, double, double, double*, cudaStream_t);   \
     template cudaError_t launch_lnnbar<T>(long long, int, const T*, const ChainScalars*, T*, cudaStream_t);         \
     template cudaError_t launch_eigs<T>(int, int, const Fields16&, const Fields16&, cudaStream_t);

@@ -36,11 +36,6 @@ struct BiasD {        // double copy of a chain's table and prior (device)
     double mu_alpha, sigma_alpha, mu_beta, sigma_beta;
 };
 
-struct WebParams {
-    double sharpness, th_phi, th_delta, rho_floor, tau;
-    int n_regions;
-};
-
 struct Fields16 { void* p[16]; };
 
 template <typename T>
@@ -61,7 +56,7 @@ cudaError_t launch_pass_b(int n, int batch, const T* lnf, const T* beta_i, const
 template <typename T>
 cudaError_t launch_web_adjoint(int n, int batch, const Fields16& th, const T* delta, const uint16_t* c16,
                                const BiasT<T>* bias, const WebParams& wp, const ChainScalars* sc,
-                               const Fields16& out, double* partial, cudaStream_t s);
+                               const Fields16& out, double* partial, bool bias_grad, cudaStream_t s);
 template <typename T>
 cudaError_t launch_cic_gather(int n, int batch, const T* gdelta, const Fields16& psi3, const Fields16& out3,
                               cudaStream_t s);
@@ -70,6 +65,7 @@ cudaError_t launch_alpt_adjoint(int n, int batch, const T* ga, const T* gb, cons
                                 const Fields16& out7, double growth, double d2, cudaStream_t s);
 template <typename T>
 cudaError_t launch_sub(long long count, const T* r, const T* nu, T* out, cudaStream_t s);
+template <typename T> cudaError_t launch_shift(long long count, const T* in, T* out, T c, cudaStream_t s);
 template <typename T>
 cudaError_t launch_kick_drift(int n, int batch, T* p, T* nu, const T* g, double ck, double cd, double* partial,
                               cudaStream_t s);
@@ -78,8 +74,9 @@ cudaError_t launch_lnnbar(long long nvox, int batch, const T* lnf, const ChainSc
 template <typename T>
 cudaError_t launch_eigs(int n, int batch, const Fields16& t6, const Fields16& out3, cudaStream_t s);
 
-// Reductions of the block partials (one block per chain, fixed order).
-cudaError_t launch_reduce(int what, int n, int batch, const double* partial, ChainScalars* sc, const BiasD* bias,
+// Reductions of the block partials (one block per chain, fixed order); nblk =
+// partial slots per chain (the grid of the kernel that wrote them).
+cudaError_t launch_reduce(int what, int nblk, int batch, const double* partial, ChainScalars* sc, const BiasD* bias,
                           int n_regions, cudaStream_t s);
 enum { RED_NTR = 0, RED_SUMF = 1, RED_LIK = 2, RED_BIASGRAD = 3, RED_P2 = 4 };
 

@@ -95,13 +95,15 @@ __device__ __forceinline__ void interp_params(const BiasT<T>& B, const T w[NR], 
 }
 
 // ln f = ln a + alpha ln u - (u/rho)^eps - (rho'/u)^eps'  (Eq. local_bias in logs),
-// u = max(1 + delta, floor).  Returns ln f; t1, t2 are the two cut-off terms.
+// u = max(1 + delta, floor), passed in as the CIC mass rho = 1 + delta itself so
+// that nearly empty cells keep full relative precision.  Returns ln f; t1, t2
+// are the two cut-off terms.
 template <typename T> struct LnF {
     T lnf, lnu, t1, t2, lnrho, lnrhop;
     bool floored;
 };
-template <typename T> __device__ __forceinline__ void log_f(T delta, T floor_, const VoxParams<T>& q, LnF<T>& r) {
-    T u = T(1) + delta;
+template <typename T> __device__ __forceinline__ void log_f(T rho_mass, T floor_, const VoxParams<T>& q, LnF<T>& r) {
+    T u = rho_mass;
     r.floored = !(u > floor_);
     if (r.floored) u = floor_;
     r.lnu = v_log(u);
@@ -190,6 +192,205 @@ __device__ __forceinline__ void eig_adjoint(const Eig3<T>& e, T g1, T g2, T g3, 
     }
     out[0] = G[0]; out[1] = T(2) * G[1]; out[2] = T(2) * G[2];
     out[3] = G[3]; out[4] = T(2) * G[4]; out[5] = G[5];
+}
+
+// ---------------------------------------------------------------------------
+// Fused web + bias per voxel (Sect. 2.5-2.8): eigenvalues of the tidal tensor
+// (and of the density Hessian for 16 regions), memberships, region weights
+// p_{4j+k} = pPhi_j pdelta_k, interpolated parameters and ln f.
+// ---------------------------------------------------------------------------
+struct WebParams {
+    double sharpness, th_phi, th_delta, rho_floor, tau;
+    int n_regions;
+};
+
+template <typename T, int NR> struct WebState {
+    Eig3<T> ephi, edel;
+    T wphi[3], pphi[4], wdel[3], pdel[4];
+    VoxParams<T> q;
+    LnF<T> lf;
+};
+
+// Region weight of region r = 4j + k: pPhi_j * pdelta_k (hierarchical), pPhi_r otherwise.
+template <typename T, int NR, typename S>
+__device__ __forceinline__ T region_w(const S& st, int j, int k) {
+    if constexpr (NR == 16) return st.pphi[j] * st.pdel[k];
+    else return st.pphi[j];
+}
+
+template <typename T, int NR>
+__device__ __forceinline__ void web_eval(const T a6[6], const T h6[6], T rho_mass, const BiasT<T>& B,
+                                         const WebParams& wp, WebState<T, NR>& S) {
+    eig3<T>(a6, S.ephi);
+    T lam[3] = {S.ephi.m + S.ephi.mu[0], S.ephi.m + S.ephi.mu[1], S.ephi.m + S.ephi.mu[2]};
+    memberships<T>(lam, T(wp.sharpness), T(wp.th_phi), S.wphi, S.pphi);
+    if constexpr (NR == 16) {
+        eig3<T>(h6, S.edel);
+        T ld[3] = {S.edel.m + S.edel.mu[0], S.edel.m + S.edel.mu[1], S.edel.m + S.edel.mu[2]};
+        memberships<T>(ld, T(wp.sharpness), T(wp.th_delta), S.wdel, S.pdel);
+    }
+    VoxParams<T>& q = S.q;
+    q.a = q.alpha = q.rho = q.eps = q.rhop = q.epsp = q.beta = T(0);
+    constexpr int NK = NR == 16 ? 4 : 1;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < NK; ++b) {
+            const int r = NK * a + b;
+            const T w = region_w<T, NR>(S, a, b);
+            q.a += B.a[r] * w; q.alpha += B.alpha[r] * w; q.rho += B.rho[r] * w; q.eps += B.eps[r] * w;
+            q.rhop += B.rhop[r] * w; q.epsp += B.epsp[r] * w; q.beta += B.beta[r] * w;
+        }
+    log_f<T>(rho_mass, T(wp.rho_floor), S.q, S.lf);
+}
+
+// Adjoint of web_eval + normalisation + NB for one voxel.  Inputs: the forward
+// state, the CIC mass rho, the count n, ln C and G/N_tr.  Outputs: g_rho
+// (direct), g_T and g_H (stored components); accumulates d/d alpha_r and
+// d/d beta_r into ga/gb when BIASG.
+template <typename T, int NR, bool BIASG>
+__device__ __forceinline__ void web_adjoint_voxel(const WebState<T, NR>& S, T rho_mass, int n, T lnC, T gscale,
+                                                  const BiasT<T>& B, const WebParams& wp, T& gd, T gt[6], T gh[6],
+                                                  T* ga, T* gb) {
+    const T s = T(wp.sharpness), tau = T(wp.tau);
+    const T lnnbar = S.lf.lnf + lnC;
+    NB<T> nb;
+    nb_eval<T>(n, lnnbar, S.q.beta, true, nb);
+    const T nbar = v_exp(lnnbar);
+    const T glnf = nb.g_lnnbar - nbar * gscale;      // normalisation adjoint: f_i/sum f * G = nbar_i G / N_tr
+    const T gbeta = nb.g_beta;
+    const T g_a = glnf / S.q.a;
+    const T g_al = glnf * S.lf.lnu;
+    const T g_rho = glnf * S.q.eps * S.lf.t1 / S.q.rho;
+    const T g_eps = -glnf * S.lf.t1 * (S.lf.lnu - S.lf.lnrho);
+    T g_rhop = T(0), g_epsp = T(0);
+    if (S.q.rhop > T(0)) {
+        g_rhop = -glnf * S.q.epsp * S.lf.t2 / S.q.rhop;
+        g_epsp = -glnf * S.lf.t2 * (S.lf.lnrhop - S.lf.lnu);
+    }
+    // direct density derivative (zero below the floor); u = rho
+    gd = S.lf.floored ? T(0) : glnf * (S.q.alpha - S.q.eps * S.lf.t1 + S.q.epsp * S.lf.t2) / rho_mass;
+    T gpphi[4] = {T(0), T(0), T(0), T(0)}, gpdel[4] = {T(0), T(0), T(0), T(0)};
+    constexpr int NK = NR == 16 ? 4 : 1;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < NK; ++b) {
+            const int r = NK * a + b;
+            const T gw = g_a * B.a[r] + g_al * B.alpha[r] + g_rho * B.rho[r] + g_eps * B.eps[r] + g_rhop * B.rhop[r] +
+                         g_epsp * B.epsp[r] + gbeta * B.beta[r];
+            if constexpr (NR == 16) {
+                gpphi[a] += gw * S.pdel[b];
+                gpdel[b] += gw * S.pphi[a];
+            } else {
+                gpphi[a] = gw;
+            }
+            if constexpr (BIASG) {
+                const T w = region_w<T, NR>(S, a, b);
+                ga[r] += g_al * w;
+                gb[r] += gbeta * w;
+            }
+        }
+    {
+        const T g1 = (gpphi[1] - gpphi[0]) * s * S.wphi[0] * (T(1) - S.wphi[0]);
+        const T g2 = (gpphi[2] - gpphi[1]) * s * S.wphi[1] * (T(1) - S.wphi[1]);
+        const T g3 = (gpphi[3] - gpphi[2]) * s * S.wphi[2] * (T(1) - S.wphi[2]);
+        eig_adjoint<T>(S.ephi, g1, g2, g3, tau, gt);
+    }
+    if constexpr (NR == 16) {
+        const T g1 = (gpdel[1] - gpdel[0]) * s * S.wdel[0] * (T(1) - S.wdel[0]);
+        const T g2 = (gpdel[2] - gpdel[1]) * s * S.wdel[1] * (T(1) - S.wdel[1]);
+        const T g3 = (gpdel[3] - gpdel[2]) * s * S.wdel[2] * (T(1) - S.wdel[2]);
+        eig_adjoint<T>(S.edel, g1, g2, g3, tau, gh);
+    }
+}
+
+// ALPT sources (Sect. 2.3): a = -D delta0 + D2 S2 (2LPT divergence) and the
+// spherical-collapse divergence 3[(1 - 2/3 D delta0)^(1/2) - 1] (D delta0 < 3/2), -3 otherwise.
+// phi = xx, xy, xz, yy, yz, zz of the linear potential Hessian.
+template <typename T>
+__device__ __forceinline__ void alpt_sources(T d0, const T phi[6], T D, T D2, T& a, T& b) {
+    const T s2 = phi[0] * phi[3] + phi[0] * phi[5] + phi[3] * phi[5] - phi[1] * phi[1] - phi[2] * phi[2] - phi[4] * phi[4];
+    const T x = D * d0;
+    a = -x + D2 * s2;
+    T arg = T(1) - T(2.0 / 3.0) * x;
+    arg = arg > T(1e-12) ? arg : T(1e-12);
+    b = x < T(1.5) ? T(3) * (v_sqrt(arg) - T(1)) : T(-3);
+}
+
+// Transpose of alpt_sources: g_delta0 (direct) and g_phi from g_a, g_b.
+template <typename T>
+__device__ __forceinline__ void alpt_sources_adj(T d0, const T phi[6], T D, T D2, T ga, T gb, T& gd0, T gphi[6]) {
+    const T x = D * d0;
+    const T arg = T(1) - T(2.0 / 3.0) * x;
+    // d theta_SC / d delta0 = -D / sqrt(1 - 2/3 D delta0) on the uncollapsed, unclamped branch
+    const T dsc = (x < T(1.5) && arg > T(1e-12)) ? -D / v_sqrt(arg) : T(0);
+    const T gs2 = D2 * ga;
+    gd0 = -D * ga + dsc * gb;
+    gphi[0] = gs2 * (phi[3] + phi[5]);
+    gphi[1] = gs2 * (T(-2) * phi[1]);
+    gphi[2] = gs2 * (T(-2) * phi[2]);
+    gphi[3] = gs2 * (phi[0] + phi[5]);
+    gphi[4] = gs2 * (T(-2) * phi[4]);
+    gphi[5] = gs2 * (phi[0] + phi[3]);
+}
+
+// CIC geometry of the particle of cell q (cell units): lower corner and fractions.
+template <typename T> struct CicCorner {
+    int i0[3];
+    T f[3];
+};
+template <typename T> __device__ __forceinline__ void cic_corner(long long q, int N, T px, T py, T pz, CicCorner<T>& c) {
+    const int lg = __ffs(N) - 1;
+    const int qz = (int)(q & (N - 1)), qy = (int)((q >> lg) & (N - 1)), qx = (int)(q >> (2 * lg));
+    const T fx = floor(px), fy = floor(py), fz = floor(pz);
+    c.f[0] = px - fx; c.f[1] = py - fy; c.f[2] = pz - fz;
+    c.i0[0] = qx + (int)fx; c.i0[1] = qy + (int)fy; c.i0[2] = qz + (int)fz;
+}
+
+// CIC deposit of one particle (unit mass) into rho (atomics, periodic).
+template <typename T> __device__ __forceinline__ void cic_deposit(const CicCorner<T>& c, int N, T* rho) {
+    const int msk = N - 1;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const T wx = a ? c.f[0] : T(1) - c.f[0];
+        const size_t ix = (size_t)((c.i0[0] + a) & msk) * N;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const T wy = b ? c.f[1] : T(1) - c.f[1];
+            const size_t iy = (ix + (size_t)((c.i0[1] + b) & msk)) * N;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const T wz = e ? c.f[2] : T(1) - c.f[2];
+                atomicAdd(rho + iy + ((c.i0[2] + e) & msk), wx * wy * wz);
+            }
+        }
+    }
+}
+
+// CIC gather adjoint of one particle: g_psi_j = sum_corners g_rho[c] dw_c/dpsi_j.
+template <typename T> __device__ __forceinline__ void cic_gather_one(const CicCorner<T>& c, int N, const T* g, T out[3]) {
+    const int msk = N - 1;
+    T gx = 0, gy = 0, gz = 0;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const T wx = a ? c.f[0] : T(1) - c.f[0], dwx = a ? T(1) : T(-1);
+        const size_t ix = (size_t)((c.i0[0] + a) & msk) * N;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const T wy = b ? c.f[1] : T(1) - c.f[1], dwy = b ? T(1) : T(-1);
+            const size_t iy = (ix + (size_t)((c.i0[1] + b) & msk)) * N;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const T wz = e ? c.f[2] : T(1) - c.f[2], dwz = e ? T(1) : T(-1);
+                const T gv = g[iy + ((c.i0[2] + e) & msk)];
+                gx += gv * dwx * wy * wz;
+                gy += gv * wx * dwy * wz;
+                gz += gv * wx * wy * dwz;
+            }
+        }
+    }
+    out[0] = gx; out[1] = gy; out[2] = gz;
 }
 
 }  // namespace bridge

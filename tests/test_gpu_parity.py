@@ -1,8 +1,15 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Tolerances: FP32 fields relative L2 <= 1e-5, FP32 gradients <= 1e-4, log
-posterior |d|/|lp| <= 1e-6; the FP64 path <= 1e-10 (fields, gradients) and
-1e-12 (log posterior).  Nothing is bit-exact: CIC atomics reorder sums.
+Tolerances: FP32 fields relative L2 <= 1e-5, log posterior |d|/|lp| <= 1e-6;
+the FP64 path <= 1e-10 (fields) and 1e-12 (log posterior).  Gradients:
+relative L2 <= max(1e-4, 10 S) in FP32 and <= max(1e-10, 1e-8 S) in FP64,
+where S is the conditioning of the gradient at the test point, measured with
+the oracle alone: the relative change of the exact (FP64) gradient when nu is
+perturbed by 2^-23 times its standard deviation (one FP32 rounding of the
+input).  At most points S is far below 1e-5 and the 1e-4 bound governs; at
+points where a few cells with tracers but almost no model mass dominate the
+gradient, no FP32 evaluation can do better than S.  Nothing is bit-exact: CIC
+atomics reorder sums.
 """
 import math
 
@@ -58,8 +65,16 @@ def oracle_ref(key, cfg, bias, nu, counts):
     if key not in ORACLE:
         f = model.forward_fields(nu, counts, cfg, bias)
         lp, g, ga, gb = model.logpost_and_grad(nu, counts, cfg, bias)
-        ORACLE[key] = (f, lp, g, np.concatenate([ga, gb]))
+        # conditioning of the gradient at this point (oracle only)
+        pert = np.random.default_rng(12345).standard_normal(nu.shape) * (2.0 ** -23) * float(np.std(nu))
+        _, g2, _, _ = model.logpost_and_grad(nu + pert, counts, cfg, bias)
+        cond = float(np.linalg.norm(g2 - g) / np.linalg.norm(g))
+        ORACLE[key] = (f, lp, g, np.concatenate([ga, gb]), cond)
     return ORACLE[key]
+
+
+def grad_tol(precision, cond):
+    return max(FP32_GRAD, 10.0 * cond) if precision == "fp32" else max(FP64_GRAD, 1e-8 * cond)
 
 
 CASES = {
@@ -76,9 +91,12 @@ def _fields_check(ctx, nu_d, c_d, bias, f, tol):
     if f.get("H") is not None:
         checks.append((pkg.FIELD_HESSIAN, f["H"]))
     errs = {}
+    names = {pkg.FIELD_DELTA0: "delta0", pkg.FIELD_PSI: "psi", pkg.FIELD_DELTA: "delta", pkg.FIELD_TIDAL: "T",
+             pkg.FIELD_LAMBDA: "lambda", pkg.FIELD_LNNBAR: "ln_nbar", pkg.FIELD_HESSIAN: "H"}
     for which, ref in checks:
         got = ctx.bridge_debug_field(nu_d, c_d, [bias], which).double().cpu().numpy().reshape(ref.shape)
-        errs[which] = rel_l2(got, ref)
+        errs[names[which]] = rel_l2(got, ref)
+    print("field rel L2:", {k: f"{v:.2e}" for k, v in errs.items()})
     bad = {k: v for k, v in errs.items() if not v <= tol}
     assert not bad, f"field rel L2 above {tol}: {errs}"
 
@@ -87,19 +105,25 @@ def _fields_check(ctx, nu_d, c_d, bias, f, tol):
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_forward_fields_and_gradient(name, precision):
     n, box, nr, seed = CASES[name]
-    if precision == "fp64" and n > 64:
-        pytest.skip("FP64 parity covered at n <= 64")
+    if precision == "fp64" and n > 128:
+        pytest.skip("FP64 parity covered at n <= 128")
     cfg, bias, nu, counts = case(n, box, nr, seed)
-    f, lp_o, g_o, gbias_o = oracle_ref(name, cfg, bias, nu, counts)
+    f, lp_o, g_o, gbias_o, cond = oracle_ref(name, cfg, bias, nu, counts)
     prec = pkg.BRIDGE_FP64 if precision == "fp64" else pkg.BRIDGE_FP32
-    ftol, gtol, ltol = (FP64_FIELD, FP64_GRAD, FP64_LP) if precision == "fp64" else (FP32_FIELD, FP32_GRAD, FP32_LP)
+    ftol, ltol = (FP64_FIELD, FP64_LP) if precision == "fp64" else (FP32_FIELD, FP32_LP)
+    gtol = grad_tol(precision, cond)
     ctx, nu_d, c_d = run_gpu(cfg, bias, nu, counts, prec)
     _fields_check(ctx, nu_d, c_d, bias, f, ftol)
     lp, g, gb = ctx.bridge_logpost_grad(nu_d, c_d, [bias])
-    assert abs(lp[0] - lp_o) / abs(lp_o) <= ltol, (lp[0], lp_o)
-    assert rel_l2(g.double().cpu().numpy().reshape(g_o.shape), g_o) <= gtol
+    e_lp = abs(lp[0] - lp_o) / abs(lp_o)
+    e_g = rel_l2(g.double().cpu().numpy().reshape(g_o.shape), g_o)
+    e_b = np.max(np.abs(gb[0] - gbias_o)) / np.max(np.abs(gbias_o))
+    print(f"{name} {precision}: logpost rel {e_lp:.2e}  grad rel L2 {e_g:.2e} (tol {gtol:.1e}, S {cond:.1e})  "
+          f"bias grad rel {e_b:.2e}")
+    assert e_lp <= ltol, (lp[0], lp_o)
+    assert e_g <= gtol
     # bias-table gradients, relative to the largest entry
-    assert np.max(np.abs(gb[0] - gbias_o)) <= gtol * np.max(np.abs(gbias_o)) * 10
+    assert e_b <= max(gtol, FP32_GRAD if precision == "fp32" else FP64_GRAD)
     lp2, _ = ctx.bridge_forward(nu_d, c_d, [bias])
     # a second evaluation differs only by the CIC atomic summation order
     assert abs(lp2[0] - lp[0]) <= (1e-7 if precision == "fp32" else 1e-13) * abs(lp[0])
@@ -117,11 +141,13 @@ def test_batched_chains_match_single_and_oracle():
     single = pkg.Context(pkg.config_from(cfg, batch=1))
     for b in range(3):
         lp1, g1, gb1 = single.bridge_logpost_grad(nu[b].contiguous(), counts[b].contiguous(), [biases[b]])
-        assert abs(lp1[0] - lp[b]) <= 1e-7 * abs(lp[b])
-        assert rel_l2(g1.cpu().numpy(), g[b].cpu().numpy()) <= 1e-5
-        lp_o, g_o, _, _ = model.logpost_and_grad(cfgs[b][2], cfgs[b][3], cfg, biases[b])
-        assert abs(lp[b] - lp_o) / abs(lp_o) <= FP32_LP
-        assert rel_l2(g[b].double().cpu().numpy(), g_o) <= FP32_GRAD
+        _, lp_o, g_o, _, cond = oracle_ref(f"batched{b}", cfg, biases[b], cfgs[b][2], cfgs[b][3])
+        e = (abs(lp1[0] - lp[b]) / abs(lp[b]), rel_l2(g1.cpu().numpy(), g[b].cpu().numpy()),
+             abs(lp[b] - lp_o) / abs(lp_o), rel_l2(g[b].double().cpu().numpy(), g_o))
+        print(f"chain {b}: single-vs-batched lp {e[0]:.2e} grad {e[1]:.2e}; oracle lp {e[2]:.2e} grad {e[3]:.2e} "
+              f"(S {cond:.1e})")
+        assert e[0] <= 1e-7 and e[1] <= max(1e-5, 10 * cond)
+        assert e[2] <= FP32_LP and e[3] <= grad_tol("fp32", cond)
 
 
 def test_autograd_function_and_host_api():
@@ -131,7 +157,8 @@ def test_autograd_function_and_host_api():
     lp = pkg.log_posterior(ctx, x, c_d, [bias])
     (gx,) = torch.autograd.grad(lp.sum(), x)
     _, g, _ = ctx.bridge_logpost_grad(nu_d, c_d, [bias])
-    assert torch.equal(gx, g)
+    # two evaluations differ only by the CIC atomic summation order
+    assert rel_l2(gx.cpu().numpy(), g.cpu().numpy()) <= 1e-5
     nu_h = torch.tensor(nu, dtype=torch.float32).pin_memory()
     c_h = torch.tensor(counts, dtype=torch.int32).pin_memory()
     g_h = torch.empty_like(nu_h).pin_memory()
@@ -185,32 +212,28 @@ def test_invalid_inputs_return_errors():
     assert e.value.status == pkg.BRIDGE_ENONFINITE
 
 
-def test_full_size_256_properties_and_linear_field():
-    """256^3 (the timed workload): linear field and displacement equal the oracle on the
-    full mesh; mass conservation; gradient directional derivative vs FP64 finite differences."""
+def test_full_size_256_against_oracle():
+    """256^3, the timed workload and launch configuration: every intermediate field and the
+    gradient against the FP64 oracle on the full mesh.  Counts are a mock of the model at
+    nu_true (Sect. 3 protocol); the evaluation point is nu_true + 0.1 noise."""
     cfg = synth.config(2)
     bias = synth.default_bias(cfg)
-    nu = synth.white_noise(cfg.n, cfg.seed_eval)
-    counts = synth.timing_counts(cfg.n, cfg.seed_counts, cfg.mean_tracers)
-    ctx, nu_d, c_d = run_gpu(cfg, bias, nu, counts, pkg.BRIDGE_FP32)
-    d0 = ctx.bridge_debug_field(nu_d, c_d, [bias], pkg.FIELD_DELTA0).double().cpu().numpy()[0, 0]
-    with torch.no_grad():
-        d0_o = model.delta0_from_nu(torch.tensor(nu, dtype=torch.float64), cfg).numpy()
-    assert rel_l2(d0, d0_o) <= FP32_FIELD
-    delta = ctx.bridge_debug_field(nu_d, c_d, [bias], pkg.FIELD_DELTA).double().cpu().numpy()
-    assert abs(delta.sum()) <= 1e-6 * delta.size      # CIC conserves mass
-    lp, g, _ = ctx.bridge_logpost_grad(nu_d, c_d, [bias])
-    assert np.isfinite(lp[0]) and torch.isfinite(g).all()
-    # directional derivative against central differences of the FP64 GPU path
-    ctx64, nu64, _ = run_gpu(cfg, bias, nu, counts, pkg.BRIDGE_FP64)
-    d = torch.tensor(synth.directions(cfg.n, 77, 1)[0], dtype=torch.float64, device="cuda")
-    lp64, g64, _ = ctx64.bridge_logpost_grad(nu64, c_d, [bias])
-    h = 1e-3
-    lpp, _ = ctx64.bridge_forward((nu64 + h * d).contiguous(), c_d, [bias])
-    lpm, _ = ctx64.bridge_forward((nu64 - h * d).contiguous(), c_d, [bias])
-    fd = (lpp[0] - lpm[0]) / (2 * h)
-    dd64 = float((g64 * d).sum())
-    dd32 = float((g.double() * d).sum())
-    assert abs(fd - dd64) <= 1e-4 * abs(fd)
-    assert abs(dd32 - dd64) <= 1e-3 * abs(dd64)
-    assert rel_l2(g.double().cpu().numpy(), g64.cpu().numpy()) <= FP32_GRAD
+    nu_t = synth.white_noise(cfg.n, cfg.seed_truth)
+    counts = mock.mock_counts(nu_t, cfg, bias, cfg.seed_counts)
+    nu = synth.eval_point(cfg.n, cfg.seed_truth, cfg.seed_eval, scale=0.1)
+    f, lp_o, g_o, gbias_o, cond = oracle_ref("256_hier", cfg, bias, nu, counts)
+    for precision in ("fp64", "fp32"):
+        prec = pkg.BRIDGE_FP64 if precision == "fp64" else pkg.BRIDGE_FP32
+        ftol, ltol = (FP64_FIELD, FP64_LP) if precision == "fp64" else (FP32_FIELD, FP32_LP)
+        gtol = grad_tol(precision, cond)
+        ctx, nu_d, c_d = run_gpu(cfg, bias, nu, counts, prec)
+        _fields_check(ctx, nu_d, c_d, bias, f, ftol)
+        lp, g, gb = ctx.bridge_logpost_grad(nu_d, c_d, [bias])
+        e_lp = abs(lp[0] - lp_o) / abs(lp_o)
+        e_g = rel_l2(g.double().cpu().numpy().reshape(g_o.shape), g_o)
+        print(f"256 {precision}: logpost rel {e_lp:.2e} grad rel L2 {e_g:.2e} (tol {gtol:.1e}, S {cond:.1e})")
+        delta = ctx.bridge_debug_field(nu_d, c_d, [bias], pkg.FIELD_DELTA).double().cpu().numpy()
+        assert abs(delta.sum()) <= 1e-6 * delta.size      # CIC conserves mass
+        assert e_lp <= ltol and e_g <= gtol
+        ctx.close()
+        del ctx
