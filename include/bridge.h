@@ -202,7 +202,9 @@ int bridge_profile_read(bridge_ctx* ctx, bridge_profile_row* rows, int max_rows)
 /* Number of kernel launches the most recent call on this context issued. */
 int64_t bridge_last_launch_count(const bridge_ctx* ctx);
 
-/* Text of the last error on this context (never NULL; "" if none). */
+/* Text of the last error on this context (never NULL; "" if none).  With a NULL
+ * context: the reason the last bridge_create on this thread failed, or
+ * "context is NULL". */
 const char* bridge_last_error(const bridge_ctx* ctx);
 
 /* Static description of a status code. */

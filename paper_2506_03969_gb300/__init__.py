@@ -168,7 +168,7 @@ class Context:
         h = ctypes.c_void_p()
         st = lib().bridge_create(ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
         if st != BRIDGE_OK:
-            raise BridgeError(st, lib().bridge_status_string(st).decode())
+            raise BridgeError(st, lib().bridge_status_string(st).decode() + ": " + lib().bridge_last_error(None).decode())
         self.handle = h
 
     def close(self):

@@ -26,8 +26,9 @@ enum {
     RB_DELTA = 0,   // 1: CIC mass rho = 1 + delta
     RB_LNF = 1,     // 2: ln f, beta_i
     RB_GD = 3,      // 1: g_rho (input of the CIC gather)
-    RB_SCR = 4,     // 6: scratch for inspection fields
-    kMaxReal = 10
+    RB_TH = 4,      // 12: tidal tensor (6) and density Hessian (6) in real space
+    RB_SCR = 16,    // 13: adjoint fields of the web stage; scratch for inspection fields
+    kMaxReal = 29
 };
 
 Term mk(int src, int dst, int px, int py, int pz, RCode rc, double cre, double cim = 0.0) {
@@ -60,7 +61,8 @@ struct bridge_ctx {
     void* biast = nullptr;
     int* errflag = nullptr;
     void* grad_tmp = nullptr;   // gradient scratch for leapfrog
-    void* node_scratch = nullptr;  // per-CTA slabs of the fused nodes (L2-resident)
+    void* node_scratch = nullptr;  // per-CTA slabs of the fused nodes
+    void* rtab = nullptr;          // radial k-space factor tables (see KParams)
     // host e2e buffers
     void* h_nu = nullptr;
     int32_t* h_counts = nullptr;
@@ -72,6 +74,17 @@ struct bridge_ctx {
     int* errflag_host = nullptr;
     KParams kp{};
     WebParams wp{};
+    // gradient-evaluation graph (captured once per buffer set, replayed per call)
+    cudaGraphExec_t eexec = nullptr;
+    const void* ekey[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t elaunches = 0;
+    // leapfrog step graph (captured on a private stream, replayed per step)
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const void* gkey[3] = {nullptr, nullptr, nullptr};
+    double geps = 0.0;
+    int64_t glaunches = 0;
+    cudaEvent_t gev[2] = {nullptr, nullptr};
     // per-launch CUDA-event profiling (bridge_profile_enable)
     bool prof = false;
     struct ProfRec { const char* name; double bytes; cudaEvent_t a, b; };
@@ -168,7 +181,8 @@ int validate_bias(const bridge_ctx* ctx, const bridge_bias* b, std::string* why)
 }
 
 struct Plan {
-    size_t spec_bytes, real_bytes, c16_bytes, partial_bytes, sc_bytes, biasd_bytes, biast_bytes, node_bytes, total;
+    size_t spec_bytes, real_bytes, c16_bytes, partial_bytes, sc_bytes, biasd_bytes, biast_bytes, node_bytes, rtab_bytes,
+        total;
     int nspec_buf, nreal_buf;
 };
 
@@ -191,8 +205,9 @@ Plan make_plan(const bridge_config* c) {
     p.biasd_bytes = align_up(sizeof(BiasD) * B);
     p.biast_bytes = align_up(sizeof(BiasT<double>) * B);
     p.node_bytes = align_up(size_t(80) << 20);   // fused-node slabs (the launcher keeps them below this)
+    p.rtab_bytes = align_up(size_t(4) * (3 * (n / 2) * (n / 2) + 1) * esz);
     p.total = p.spec_bytes * p.nspec_buf + p.real_bytes * (p.nreal_buf + 1) + p.c16_bytes + p.partial_bytes +
-              p.sc_bytes + p.biasd_bytes + p.biast_bytes + p.node_bytes + 256;
+              p.sc_bytes + p.biasd_bytes + p.biast_bytes + p.node_bytes + p.rtab_bytes + 256;
     return p;
 }
 
@@ -272,20 +287,11 @@ template <typename T> int y_identity(bridge_ctx* ctx, int first, int count, bool
 
 #define RUN(x) do { int st_ = (x); if (st_ != BRIDGE_OK) return st_; } while (0)
 
-// Fused node launch: fills the common arguments, zeroes the partial sums the
-// node accumulates into and reports the grid (partial slots per chain).
+// Fused node launch: fills the common arguments and reports the grid.
 template <typename T> int node(bridge_ctx* ctx, NodeArgs& na, const char* name, double bytes, int* grid_used) {
-    na.c16 = ctx->c16;
-    na.bias = ctx->biast;
-    na.sc = ctx->sc;
-    na.partial = ctx->partial;
     na.scratch = ctx->node_scratch;
-    na.wp = ctx->wp;
     na.growth = ctx->cfg.growth_d;
     na.d2 = ctx->cfg.d2_over_d2 * ctx->cfg.growth_d * ctx->cfg.growth_d;
-    na.n_regions = ctx->nr;
-    if (na.kind == NODE_WEB_FWD || (na.kind == NODE_WEB_ADJ && na.bias_grad))
-        CK(cudaMemsetAsync(ctx->partial, 0, size_t(ctx->B) * 1024 * 32 * sizeof(double), ctx->stream));
     int g = 0;
     CKL(name, bytes, launch_node<T>(ctx->n, ctx->B, na, &g, ctx->stream));
     if (grid_used) *grid_used = g;
@@ -389,18 +395,12 @@ template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelih
         }
         CKL("y_inv", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_inv<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
-    // fused web / bias on the fly (node), normalisation, NB likelihood
-    {
-        NodeArgs na{};
-        na.kind = NODE_WEB_FWD;
-        for (int f = 0; f < nth; ++f) na.spec_in[f] = ctx->spec[SP_TH + f];
-        na.real_in[0] = ctx->real[RB_DELTA];
-        na.real_out[0] = ctx->real[RB_LNF];
-        na.real_out[1] = ctx->real[RB_LNF + 1];
-        int g = 0;
-        RUN(node<T>(ctx, na, "node_web_bias", nth * sby<T>(ctx) + 3 * rby<T>(ctx), &g));
-        CKL("reduce", 0.0, launch_reduce(RED_SUMF, g, ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
-    }
+    // tensors to real space, fused eigenvalue / web / bias pass, normalisation
+    RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_TH, nth), mreal(ctx, RB_TH, nth)));
+    CKL("web_bias", (nth + 3) * rby<T>(ctx), launch_pass_a<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 12), RB<T>(ctx, RB_DELTA), RB<T>(ctx, RB_LNF),
+                        RB<T>(ctx, RB_LNF + 1), reinterpret_cast<const BiasT<T>*>(ctx->biast), ctx->wp, ctx->partial,
+                        ctx->stream));
+    CKL("reduce", 0.0, launch_reduce(RED_SUMF, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
     if (likelihood) {
         CKL("nb_lik", 3 * rby<T>(ctx) + c16b(ctx), launch_pass_b<T>(ctx->n, ctx->B, RB<T>(ctx, RB_LNF), RB<T>(ctx, RB_LNF + 1), ctx->c16, nu, ctx->sc,
                             ctx->partial, ctx->stream));
@@ -416,19 +416,13 @@ template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad, boo
     const double invn3 = 1.0 / double(ctx->nvox);
     const bool hier = ctx->nr == 16;
     const int nth = nth_of(ctx);
-    // web + bias + NB adjoint on the fly: r2c of g_rho (direct), g_T, g_H
-    {
-        NodeArgs na{};
-        na.kind = NODE_WEB_ADJ;
-        na.bias_grad = bias_grad ? 1 : 0;
-        for (int f = 0; f < nth; ++f) na.spec_in[f] = ctx->spec[SP_TH + f];
-        for (int f = 0; f < nth + 1; ++f) na.spec_out[f] = ctx->spec[SP_SCR + f];
-        na.real_in[0] = ctx->real[RB_DELTA];
-        int g = 0;
-        RUN(node<T>(ctx, na, "node_web_bias_adj", (2 * nth + 1) * sby<T>(ctx) + rby<T>(ctx) + c16b(ctx), &g));
-        if (bias_grad)
-            CKL("reduce", 0.0, launch_reduce(RED_BIASGRAD, g, ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
-    }
+    // web + bias + NB adjoint: g_rho (direct), g_T, g_H in real space, then r2c
+    CKL("web_bias_adj", (2 * nth + 2) * rby<T>(ctx) + c16b(ctx), launch_web_adjoint<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 12), RB<T>(ctx, RB_DELTA), ctx->c16,
+                             reinterpret_cast<const BiasT<T>*>(ctx->biast), ctx->wp, ctx->sc,
+                             fields(ctx, RB_SCR, 1 + nth), ctx->partial, bias_grad, ctx->stream));
+    if (bias_grad)
+        CKL("reduce", 0.0, launch_reduce(RED_BIASGRAD, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+    RUN(z_fwd<T>(ctx, creal(ctx, RB_SCR, 1 + nth), mspec<T>(ctx, SP_SCR, 1 + nth)));
     // spectral adjoint of the tensors (transpose of the forward x node / y expansion)
     {
         const int nslot = hier ? 6 : 4;
@@ -524,14 +518,8 @@ template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad, boo
     }
     RUN(y_identity<T>(ctx, SP_SCR, 1, false));
     // inverse z and the white-noise prior: g_nu = (likelihood part) - nu
-    {
-        NodeArgs na{};
-        na.kind = NODE_FINAL;
-        na.spec_in[0] = ctx->spec[SP_SCR];
-        na.real_in[0] = nu;
-        na.real_out[0] = grad;
-        RUN(node<T>(ctx, na, "node_final", sby<T>(ctx) + 2 * rby<T>(ctx), nullptr));
-    }
+    RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_SCR, 1), mreal(ctx, RB_SCR, 1)));
+    CKL("prior_grad", 3 * rby<T>(ctx), launch_sub<T>(ctx->nvox * ctx->B, RB<T>(ctx, RB_SCR), nu, grad, ctx->stream));
     return BRIDGE_OK;
 }
 
@@ -551,8 +539,9 @@ template <typename T> int upload_bias(bridge_ctx* ctx, const bridge_bias* bias) 
             d.rho[r] = on ? bias[c].rho[r] : 1.0; d.eps[r] = on ? bias[c].eps[r] : 1.0;
             d.rhop[r] = on ? bias[c].rhop[r] : 0.0; d.epsp[r] = on ? bias[c].epsp[r] : 1.0;
             d.beta[r] = on ? bias[c].beta[r] : 1.0;
-            t.a[r] = T(d.a[r]); t.alpha[r] = T(d.alpha[r]); t.rho[r] = T(d.rho[r]); t.eps[r] = T(d.eps[r]);
-            t.rhop[r] = T(d.rhop[r]); t.epsp[r] = T(d.epsp[r]); t.beta[r] = T(d.beta[r]);
+            t.pk[r][BP_A] = T(d.a[r]); t.pk[r][BP_ALPHA] = T(d.alpha[r]); t.pk[r][BP_RHO] = T(d.rho[r]);
+            t.pk[r][BP_EPS] = T(d.eps[r]); t.pk[r][BP_RHOP] = T(d.rhop[r]); t.pk[r][BP_EPSP] = T(d.epsp[r]);
+            t.pk[r][BP_BETA] = T(d.beta[r]); t.pk[r][7] = T(0);
         }
         d.prior_mask = bias[c].prior_mask;
         d.mu_alpha = bias[c].mu_alpha; d.sigma_alpha = bias[c].sigma_alpha;
@@ -597,13 +586,66 @@ template <typename T> int do_forward(bridge_ctx* ctx, const void* nu, const int3
     return BRIDGE_OK;
 }
 
+template <typename T> int eval_body(bridge_ctx* ctx, const T* nu, const int32_t* counts, T* grad, bool bias_grad) {
+    RUN(prep_counts<T>(ctx, counts));
+    RUN(run_forward<T>(ctx, nu, true));
+    RUN(run_adjoint<T>(ctx, nu, grad, bias_grad));
+    return BRIDGE_OK;
+}
+
+int ensure_graph_stream(bridge_ctx* ctx) {
+    if (!ctx->gstream) {
+        CK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ctx->gev[0], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->gev[1], cudaEventDisableTiming));
+    }
+    return BRIDGE_OK;
+}
+
+// The whole evaluation (counts preparation, forward, adjoint) replayed from a
+// CUDA graph captured on a private stream; re-captured when the buffers change.
+template <typename T> int eval_graph(bridge_ctx* ctx, const T* nu, const int32_t* counts, T* grad, bool bias_grad) {
+    RUN(ensure_graph_stream(ctx));
+    const void* key[4] = {nu, counts, grad, bias_grad ? ctx : nullptr};
+    bool fresh = ctx->eexec != nullptr;
+    for (int i = 0; i < 4; ++i) fresh = fresh && ctx->ekey[i] == key[i];
+    if (!fresh) {
+        if (ctx->eexec) { cudaGraphExecDestroy(ctx->eexec); ctx->eexec = nullptr; }
+        cudaStream_t user = ctx->stream;
+        const int64_t launches = ctx->launches;
+        ctx->stream = ctx->gstream;
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeRelaxed));
+        const int st = eval_body<T>(ctx, nu, counts, grad, bias_grad);
+        const cudaError_t ce = cudaStreamEndCapture(ctx->gstream, &graph);
+        ctx->elaunches = ctx->launches - launches;
+        ctx->stream = user;
+        ctx->launches = launches;
+        if (st != BRIDGE_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+        if (ce != cudaSuccess) return fail(ctx, BRIDGE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        const cudaError_t ie = cudaGraphInstantiate(&ctx->eexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) { ctx->eexec = nullptr; return fail(ctx, BRIDGE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie)); }
+        for (int i = 0; i < 4; ++i) ctx->ekey[i] = key[i];
+    }
+    CK(cudaEventRecord(ctx->gev[0], ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0));
+    CK(cudaGraphLaunch(ctx->eexec, ctx->gstream));
+    CK(cudaEventRecord(ctx->gev[1], ctx->gstream));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->gev[1], 0));
+    ctx->launches += ctx->elaunches;
+    return BRIDGE_OK;
+}
+
 template <typename T> int do_grad(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
                                   double* logpost_out, void* grad, double* gbias_out) {
     if (!nu || !grad) return fail(ctx, BRIDGE_EINVAL, "nu and grad_nu_out are required");
+    if (!counts) return fail(ctx, BRIDGE_EINVAL, "counts is NULL");
     RUN(upload_bias<T>(ctx, bias));
-    RUN(prep_counts<T>(ctx, counts));
-    RUN(run_forward<T>(ctx, reinterpret_cast<const T*>(nu), true));
-    RUN(run_adjoint<T>(ctx, reinterpret_cast<const T*>(nu), reinterpret_cast<T*>(grad), gbias_out != nullptr));
+    const T* nuT = reinterpret_cast<const T*>(nu);
+    T* gT = reinterpret_cast<T*>(grad);
+    if (ctx->prof) RUN(eval_body<T>(ctx, nuT, counts, gT, gbias_out != nullptr));   // per-launch events need direct launches
+    else RUN(eval_graph<T>(ctx, nuT, counts, gT, gbias_out != nullptr));
     RUN(finish(ctx));
     for (int c = 0; c < ctx->B; ++c) {
         if (!std::isfinite(ctx->sc_host[c].logpost)) return fail(ctx, BRIDGE_ENONFINITE, "log posterior is not finite");
@@ -611,6 +653,49 @@ template <typename T> int do_grad(bridge_ctx* ctx, const void* nu, const int32_t
         if (gbias_out)
             for (int k = 0; k < 2 * ctx->nr; ++k) gbias_out[c * 2 * ctx->nr + k] = ctx->sc_host[c].gbias[k];
     }
+    return BRIDGE_OK;
+}
+
+// One interior leapfrog step: gradient at nu, then p += eps g; nu += eps p.
+template <typename T> int leapfrog_step(bridge_ctx* ctx, T* nu, T* p, T* g, double eps) {
+    RUN(run_forward<T>(ctx, nu, true));
+    RUN(run_adjoint<T>(ctx, nu, g, false));
+    CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, eps, eps, ctx->partial, ctx->stream));
+    return BRIDGE_OK;
+}
+
+// Replays n interior steps from a CUDA graph captured (once per nu, p, eps) on
+// a private stream; the context stream waits for the replays.
+template <typename T> int leapfrog_graph(bridge_ctx* ctx, T* nu, T* p, T* g, double eps, int n) {
+    RUN(ensure_graph_stream(ctx));
+    const bool fresh = ctx->gexec && ctx->gkey[0] == nu && ctx->gkey[1] == p && ctx->gkey[2] == g && ctx->geps == eps;
+    if (!fresh) {
+        if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+        cudaStream_t user = ctx->stream;
+        const bool prof = ctx->prof;
+        const int64_t launches = ctx->launches;
+        ctx->stream = ctx->gstream;
+        ctx->prof = false;
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeRelaxed));
+        const int st = leapfrog_step<T>(ctx, nu, p, g, eps);
+        const cudaError_t ce = cudaStreamEndCapture(ctx->gstream, &graph);
+        ctx->glaunches = ctx->launches - launches;
+        ctx->stream = user;
+        ctx->prof = prof;
+        ctx->launches = launches;
+        if (st != BRIDGE_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+        if (ce != cudaSuccess) return fail(ctx, BRIDGE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        const cudaError_t ie = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) { ctx->gexec = nullptr; return fail(ctx, BRIDGE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie)); }
+        ctx->gkey[0] = nu; ctx->gkey[1] = p; ctx->gkey[2] = g; ctx->geps = eps;
+    }
+    CK(cudaEventRecord(ctx->gev[0], ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0));
+    for (int s = 0; s < n; ++s) CK(cudaGraphLaunch(ctx->gexec, ctx->gstream));
+    CK(cudaEventRecord(ctx->gev[1], ctx->gstream));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->gev[1], 0));
     return BRIDGE_OK;
 }
 
@@ -631,15 +716,17 @@ template <typename T> int do_leapfrog(bridge_ctx* ctx, void* nu_v, void* p_v, co
     CKL("reduce", 0.0, launch_reduce(RED_P2, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
     RUN(finish(ctx));
     for (int c = 0; c < ctx->B; ++c) { u0[c] = -ctx->sc_host[c].logpost; k0[c] = 0.5 * ctx->sc_host[c].sump2; }
-    // first half kick + drift, then (gradient, full kick + drift) ..., final half kick
+    // half kick + drift; n-1 interior steps (gradient, full kick + drift); last gradient and half kick
     CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, 0.5 * eps, eps, ctx->partial, ctx->stream));
-    for (int s = 0; s < n_steps; ++s) {
-        RUN(run_forward<T>(ctx, nu, true));
-        RUN(run_adjoint<T>(ctx, nu, g, false));
-        const bool last = s == n_steps - 1;
-        CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, last ? 0.5 * eps : eps, last ? 0.0 : eps, ctx->partial,
-                                ctx->stream));
+    if (n_steps > 2 && !ctx->prof) {
+        RUN(leapfrog_graph<T>(ctx, nu, p, g, eps, n_steps - 1));
+        ctx->launches += ctx->glaunches * (n_steps - 1);   // kernels replayed from the graph
+    } else {
+        for (int s = 0; s < n_steps - 1; ++s) RUN(leapfrog_step<T>(ctx, nu, p, g, eps));
     }
+    RUN(run_forward<T>(ctx, nu, true));
+    RUN(run_adjoint<T>(ctx, nu, g, false));
+    CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, 0.5 * eps, 0.0, ctx->partial, ctx->stream));
     CKL("reduce", 0.0, launch_reduce(RED_P2, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
     RUN(finish(ctx));
     for (int c = 0; c < ctx->B; ++c) {
@@ -682,18 +769,13 @@ template <typename T> int do_debug(bridge_ctx* ctx, const void* nu, const int32_
             CKL("shift", 2 * rby<T>(ctx), launch_shift<T>(ctx->nvox * ctx->B, RB<T>(ctx, RB_DELTA), RB<T>(ctx, RB_SCR), T(-1), ctx->stream));
             RUN(copy_fields(RB_SCR, 1));
             break;
-        case BRIDGE_FIELD_TIDAL:
-            RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_TH, 6), mreal(ctx, RB_SCR, 6)));
-            RUN(copy_fields(RB_SCR, 6));
-            break;
+        case BRIDGE_FIELD_TIDAL: RUN(copy_fields(RB_TH, 6)); break;
         case BRIDGE_FIELD_HESSIAN:
             if (ctx->nr != 16) return fail(ctx, BRIDGE_EINVAL, "the density Hessian exists only for 16 regions");
-            RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_TH + 6, 6), mreal(ctx, RB_SCR, 6)));
-            RUN(copy_fields(RB_SCR, 6));
+            RUN(copy_fields(RB_TH + 6, 6));
             break;
         case BRIDGE_FIELD_LAMBDA:
-            RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_TH, 6), mreal(ctx, RB_SCR, 6)));
-            CKL("eigs", 9 * rby<T>(ctx), launch_eigs<T>(ctx->n, ctx->B, fields(ctx, RB_SCR, 6), fields(ctx, RB_SCR, 3), ctx->stream));
+            CKL("eigs", 9 * rby<T>(ctx), launch_eigs<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 6), fields(ctx, RB_SCR, 3), ctx->stream));
             RUN(copy_fields(RB_SCR, 3));
             break;
         case BRIDGE_FIELD_LNNBAR:
@@ -745,21 +827,31 @@ double bridge_pk_amplitude(double sigma, double radius, double ns, double kc, do
     return sigma * sigma / s2;
 }
 
+static thread_local std::string g_create_error;
+
+static int create_fail(bridge_ctx* ctx, int status, const std::string& why) {
+    g_create_error = why;
+    if (ctx) bridge_destroy(ctx);
+    return status;
+}
+
 int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
-    if (!out) return BRIDGE_EINVAL;
+    g_create_error.clear();
+    if (!out) return create_fail(nullptr, BRIDGE_EINVAL, "out is NULL");
     std::string why;
-    if (validate(cfg, &why) != BRIDGE_OK) return BRIDGE_EINVAL;
+    if (validate(cfg, &why) != BRIDGE_OK) return create_fail(nullptr, BRIDGE_EINVAL, why);
     int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return BRIDGE_ENODEVICE;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return create_fail(nullptr, BRIDGE_ENODEVICE, "no CUDA device");
+    }
     bridge_ctx* ctx = new bridge_ctx();
     ctx->cfg = *cfg;
     ctx->stream = reinterpret_cast<cudaStream_t>(stream);
     cudaGetDevice(&ctx->device);
     cudaDeviceProp prop;
-    if (cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess || prop.major != 10 || prop.minor != 3) {
-        delete ctx;
-        return BRIDGE_ENODEVICE;
-    }
+    if (cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess || prop.major != 10 || prop.minor != 3)
+        return create_fail(ctx, BRIDGE_ENODEVICE, "the current device is not of compute capability 10.3");
     ctx->n = cfg->n;
     ctx->B = cfg->batch;
     ctx->nr = cfg->n_regions;
@@ -776,10 +868,19 @@ int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
     ctx->wp.rho_floor = cfg->rho_floor;
     ctx->wp.tau = cfg->precision == BRIDGE_FP64 ? 1e-10 : 1e-4;
     ctx->wp.n_regions = cfg->n_regions;
-    if (upload_twiddles() != cudaSuccess || upload_node_twiddles() != cudaSuccess) { delete ctx; return BRIDGE_ECUDA; }
+    cudaError_t e = upload_twiddles();
+    if (e == cudaSuccess) e = upload_node_twiddles();
+    if (e != cudaSuccess) return create_fail(ctx, BRIDGE_ECUDA, std::string("twiddle upload: ") + cudaGetErrorString(e));
     const Plan pl = make_plan(cfg);
-    if (cudaMalloc(&ctx->ws, pl.total) != cudaSuccess) { cudaGetLastError(); delete ctx; return BRIDGE_ENOMEM; }
+    e = cudaMalloc(&ctx->ws, pl.total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ws = nullptr;
+        return create_fail(ctx, BRIDGE_ENOMEM, "workspace of " + std::to_string(pl.total) + " bytes: " + cudaGetErrorString(e));
+    }
     ctx->ws_bytes = pl.total;
+    e = cudaMemset(ctx->ws, 0, pl.total);
+    if (e != cudaSuccess) return create_fail(ctx, BRIDGE_ECUDA, std::string("workspace clear: ") + cudaGetErrorString(e));
     char* w = reinterpret_cast<char*>(align_up(reinterpret_cast<size_t>(ctx->ws)));
     for (int i = 0; i < pl.nspec_buf; ++i) { ctx->spec[i] = w; w += pl.spec_bytes; }
     for (int i = 0; i < pl.nreal_buf; ++i) { ctx->real[i] = w; w += pl.real_bytes; }
@@ -790,12 +891,30 @@ int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
     ctx->biasd = reinterpret_cast<BiasD*>(w); w += pl.biasd_bytes;
     ctx->biast = w; w += pl.biast_bytes;
     ctx->node_scratch = w; w += pl.node_bytes;
+    ctx->rtab = w; w += pl.rtab_bytes;
+    {
+        const int rlen = 3 * (cfg->n / 2) * (cfg->n / 2) + 1;
+        std::vector<double> tab(size_t(4) * rlen);
+        radial_tables_host(cfg->n, ctx->kp, tab.data());
+        if (cfg->precision == BRIDGE_FP64) {
+            e = cudaMemcpy(ctx->rtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> tf(tab.begin(), tab.end());
+            e = cudaMemcpy(ctx->rtab, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) return create_fail(ctx, BRIDGE_ECUDA, std::string("radial tables: ") + cudaGetErrorString(e));
+        ctx->kp.rtab = ctx->rtab;
+        ctx->kp.rlen = rlen;
+    }
     {
         const size_t need = cfg->precision == BRIDGE_FP64 ? node_scratch_bytes<double>(cfg->n, cfg->batch)
                                                          : node_scratch_bytes<float>(cfg->n, cfg->batch);
         const int grid = cfg->precision == BRIDGE_FP64 ? node_max_grid<double>(cfg->n, cfg->batch)
                                                       : node_max_grid<float>(cfg->n, cfg->batch);
-        if (need > pl.node_bytes || grid > 1024) { bridge_destroy(ctx); return BRIDGE_ECUDA; }
+        cudaGetLastError();   // occupancy queries leave no error behind
+        if (need > pl.node_bytes || grid < 1)
+            return create_fail(ctx, BRIDGE_ECUDA, "node plan: scratch " + std::to_string(need) + " > " +
+                                                      std::to_string(pl.node_bytes) + " or grid " + std::to_string(grid));
     }
     if (cudaMalloc(&ctx->errflag, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&ctx->sc_host, sizeof(ChainScalars) * ctx->B) != cudaSuccess ||
@@ -803,13 +922,7 @@ int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
         cudaMallocHost(&ctx->biast_host, sizeof(BiasT<double>) * ctx->B) != cudaSuccess ||
         cudaMallocHost(&ctx->errflag_host, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
-        bridge_destroy(ctx);
-        return BRIDGE_ENOMEM;
-    }
-    if (cudaMemsetAsync(ctx->ws, 0, pl.total, ctx->stream) != cudaSuccess ||
-        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
-        bridge_destroy(ctx);
-        return BRIDGE_ECUDA;
+        return create_fail(ctx, BRIDGE_ENOMEM, "small device or pinned host buffers");
     }
     *out = ctx;
     return BRIDGE_OK;
@@ -828,6 +941,10 @@ void bridge_destroy(bridge_ctx* ctx) {
     if (ctx->biast_host) cudaFreeHost(ctx->biast_host);
     if (ctx->errflag_host) cudaFreeHost(ctx->errflag_host);
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->eexec) cudaGraphExecDestroy(ctx->eexec);
+    if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+    for (cudaEvent_t e : ctx->gev) if (e) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -919,7 +1036,10 @@ int bridge_profile_read(bridge_ctx* ctx, bridge_profile_row* rows, int max_rows)
     return n;
 }
 
-const char* bridge_last_error(const bridge_ctx* ctx) { return ctx ? ctx->err.c_str() : "context is NULL"; }
+const char* bridge_last_error(const bridge_ctx* ctx) {
+    if (ctx) return ctx->err.c_str();
+    return g_create_error.empty() ? "context is NULL" : g_create_error.c_str();
+}
 
 const char* bridge_status_string(int s) {
     switch (s) {

@@ -13,11 +13,8 @@
 namespace bridge {
 
 enum NodeKind {
-    NODE_WEB_FWD = 0,    // T (6) [+ H (6)] -> eigenvalues, web, bias: ln f, beta_i, partial sum f
-    NODE_WEB_ADJ = 1,    // T, H -> NB + bias + web adjoint -> r2c of g_delta, g_T, g_H (13 or 7)
     NODE_ALPT_FWD = 2,   // delta0, phi (7) -> a = -D delta0 + D2 S2, theta_SC -> r2c (2)
     NODE_ALPT_ADJ = 3,   // delta0, phi (7), g_a, g_b (2) -> g_delta0, g_phi -> r2c (7)
-    NODE_FINAL = 4,      // r (1) -> grad = r - nu
     NODE_GATHER = 5,     // psi (3) -> CIC gather adjoint g_psi -> r2c (3)
     NODE_SCATTER = 6     // psi (3) -> CIC deposit into rho
 };
@@ -26,20 +23,13 @@ struct NodeArgs {
     int kind;
     const void* spec_in[16];     // spectra ([kz][y][x] layout), chain stride nspec
     void* spec_out[16];          // spectra out
-    const void* real_in[4];      // real fields read per voxel (rho, nu, psi...), chain stride nvox
-    void* real_out[4];           // real fields written per voxel
-    const uint16_t* c16;         // counts
-    const void* bias;            // BiasT<T>[B]
-    const ChainScalars* sc;
-    double* partial;             // [B][grid][K]
+    const void* real_in[4];      // real fields read per voxel (g_rho for the gather), chain stride nvox
+    void* real_out[4];           // real fields written per voxel (rho for the scatter)
     void* scratch;               // slabs: [grid][F][tile voxels]
-    WebParams wp;
     double growth, d2;
-    int n_regions;
-    int bias_grad;
 };
 
-// Launch a node; *grid_used receives the number of CTAs (= partial-sum slots per chain).
+// Launch a node; *grid_used receives the number of CTAs.
 template <typename T> cudaError_t launch_node(int n, int batch, const NodeArgs& a, int* grid_used, cudaStream_t s);
 // Largest grid and scratch (bytes) over all node kinds for this mesh and batch (current device).
 template <typename T> int node_max_grid(int n, int batch);

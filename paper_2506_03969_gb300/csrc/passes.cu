@@ -27,20 +27,29 @@ namespace bridge {
 
 cudaError_t upload_twiddles() { return upload_twiddles_here(); }
 
+void radial_tables_host(int n, const KParams& kp, double* out) {
+    const int rlen = 3 * (n / 2) * (n / 2) + 1;
+    const double a = std::sqrt(kp.pk_amp / (kp.dx * kp.dx * kp.dx));
+    for (int m2 = 0; m2 < rlen; ++m2) {
+        const double k2 = kp.kf * kp.kf * double(m2);
+        const double inv = m2 > 0 ? 1.0 / k2 : 0.0;
+        // sqrt(P(k)/dx^3), P = A k^ns / (1 + (k/kc)^2)^pow, P(0) = 0   (App. A)
+        const double sp = m2 > 0 ? a * std::pow(k2, 0.25 * kp.pk_ns) *
+                                       std::pow(1.0 + k2 / (kp.pk_kc * kp.pk_kc), -0.5 * kp.pk_pow)
+                                 : 0.0;
+        const double e = -0.5 * kp.r_s * kp.r_s * k2;   // K(k) = exp(-k^2 r_s^2 / 2), Sect. 2.3
+        out[0 * rlen + m2] = inv;
+        out[1 * rlen + m2] = sp;
+        out[2 * rlen + m2] = std::exp(e);
+        out[3 * rlen + m2] = -std::expm1(e);
+    }
+}
+
 template <typename T> __device__ __forceinline__ cplx_t<T> tw_load(int N, int j) { return ztw_load<T>(N, j); }
 
 // ---------------------------------------------------------------------------
 // Multipliers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float m_pow(float x, float y) { return powf(x, y); }
-__device__ __forceinline__ double m_pow(double x, double y) { return pow(x, y); }
-__device__ __forceinline__ float m_exp(float x) { return expf(x); }
-__device__ __forceinline__ double m_exp(double x) { return exp(x); }
-__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
-__device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
-
 // k_axis^p for signed index m; odd powers vanish on the Nyquist index.
 template <typename T> __device__ __forceinline__ T kpow(int m, int p, int n, T kf) {
     if (p == 0) return T(1);
@@ -49,30 +58,11 @@ template <typename T> __device__ __forceinline__ T kpow(int m, int p, int n, T k
     return p == 1 ? k : (p == 2 ? k * k : k * k * k);
 }
 
-template <typename T> __device__ __forceinline__ T radial(int code, T k2, const KParams& kp) {
-    switch (code) {
-        case R_INVK2: return k2 > T(0) ? T(1) / k2 : T(0);
-        case R_SQRTP: {
-            // sqrt(P(k)/dx^3), P = A k^ns / (1 + (k/kc)^2)^pow, P(0) = 0   (App. A)
-            if (k2 <= T(0)) return T(0);
-            const T a = T(m_sqrt(kp.pk_amp / (kp.dx * kp.dx * kp.dx)));
-            const T kc2 = T(kp.pk_kc * kp.pk_kc);
-            return a * m_pow(k2, T(0.25 * kp.pk_ns)) * m_pow(T(1) + k2 / kc2, T(-0.5 * kp.pk_pow));
-        }
-        case R_KBLEND: return m_exp(T(-0.5 * kp.r_s * kp.r_s) * k2);             // K(k), Sect. 2.3
-        case R_1MKBLEND: return -m_expm1(T(-0.5 * kp.r_s * kp.r_s) * k2);        // 1 - K(k)
-        default: return T(1);
-    }
-}
-
-template <typename T, bool RADIAL>
-__device__ __forceinline__ cplx_t<T> term_mult(const Term& tm, int mx, int my, int mz, int n, const KParams& kp) {
+// y-pass multiplier: (cre + i cim) ky^py kz^pz (no radial factor in the y pass).
+template <typename T>
+__device__ __forceinline__ cplx_t<T> ymult(const Term& tm, int my, int mz, int n, const KParams& kp) {
     const T kf = T(kp.kf);
-    T r = kpow<T>(mx, tm.px, n, kf) * kpow<T>(my, tm.py, n, kf) * kpow<T>(mz, tm.pz, n, kf);
-    if (RADIAL && tm.rcode != R_ONE) {
-        const T k2 = kf * kf * T(mx * mx + my * my + mz * mz);
-        r *= radial<T>(tm.rcode, k2, kp);
-    }
+    const T r = kpow<T>(my, tm.py, n, kf) * kpow<T>(mz, tm.pz, n, kf);
     return cmake<cplx_t<T>>(T(tm.cre) * r, T(tm.cim) * r);
 }
 
@@ -167,7 +157,7 @@ template <typename T, int N, bool XM> struct Tile {
 
 // Forward (merge) column pass: out[o] = sum_{terms -> o} mult * DFT(in[src])
 template <typename T, int N, bool XM>
-__global__ void __launch_bounds__(Tile<T, N, XM>::NT) k_col_fwd(const PassProgram P, const KParams kp) {
+__global__ void __launch_bounds__(Tile<T, N, XM>::NT, 2) k_col_fwd(const PassProgram P, const KParams kp) {
     using TL = Tile<T, N, XM>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -199,7 +189,7 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT) k_col_fwd(const PassProgra
                 for (int i = 0; i < TL::N2; ++i) {
                     int mx, my, mz;
                     TL::freqs(k1 + TL::N1 * bitrev(i, TL::N2), g, kz, c0, mx, my, mz);
-                    acc[j][i] = cadd(acc[j][i], cmul(term_mult<T, XM>(tm, mx, my, mz, N, kp), X[j][i]));
+                    acc[j][i] = cadd(acc[j][i], cmul(ymult<T>(tm, my, mz, N, kp), X[j][i]));
                 }
             }
         }
@@ -215,7 +205,7 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT) k_col_fwd(const PassProgra
 
 // Inverse (expand) column pass: out[dst] = IDFT(mult * in[src]) for each term.
 template <typename T, int N, bool XM>
-__global__ void __launch_bounds__(Tile<T, N, XM>::NT) k_col_inv(const PassProgram P, const KParams kp) {
+__global__ void __launch_bounds__(Tile<T, N, XM>::NT, 2) k_col_inv(const PassProgram P, const KParams kp) {
     using TL = Tile<T, N, XM>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -248,7 +238,7 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT) k_col_inv(const PassProgra
                 for (int k2 = 0; k2 < TL::N2; ++k2) {
                     int mx, my, mz;
                     TL::freqs(k1 + TL::N1 * k2, g, kz, c0, mx, my, mz);
-                    Y[j][k2] = cmul(term_mult<T, XM>(tm, mx, my, mz, N, kp), X[j][k2]);
+                    Y[j][k2] = cmul(ymult<T>(tm, my, mz, N, kp), X[j][k2]);
                 }
             }
             __syncthreads();
@@ -261,54 +251,32 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT) k_col_inv(const PassProgra
 }
 
 // x node: Q = sum_merge mult * DFTx(in[src]);  out[dst] = IDFTx(mult * Q).
-// The transcendental radial factors (sqrt P, K, 1 - K) of the tile are
-// tabulated once in shared memory (at most two codes per program) so the
-// unrolled register DFT code only reads them.
-template <typename T, int N>
-__device__ __forceinline__ cplx_t<T> xnode_mult(const Term& tm, int mx, int my, int mz, const KParams& kp,
-                                                 const T* tab, const int8_t* slot_of, int e) {
+// Radial factors come from the per-context tables indexed by m^2 (exact, no
+// transcendental work in the kernel).
+template <typename T>
+__device__ __forceinline__ cplx_t<T> xnode_mult(const Term& tm, int mx, int my, int mz, int n, const KParams& kp) {
     const T kf = T(kp.kf);
-    T r = kpow<T>(mx, tm.px, N, kf) * kpow<T>(my, tm.py, N, kf) * kpow<T>(mz, tm.pz, N, kf);
-    if (tm.rcode == R_INVK2) {
+    T r = kpow<T>(mx, tm.px, n, kf);
+    if (tm.py | tm.pz) r *= kpow<T>(my, tm.py, n, kf) * kpow<T>(mz, tm.pz, n, kf);
+    if (tm.rcode != R_ONE) {
         const int m2 = mx * mx + my * my + mz * mz;
-        r = m2 > 0 ? r / (kf * kf * T(m2)) : T(0);
-    } else if (tm.rcode != R_ONE) {
-        r *= tab[slot_of[tm.rcode] * (Tile<T, N, true>::G * N) + e];
+        r *= __ldg(reinterpret_cast<const T*>(kp.rtab) + (tm.rcode - 1) * kp.rlen + m2);
     }
     return cmake<cplx_t<T>>(T(tm.cre) * r, T(tm.cim) * r);
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(Tile<T, N, true>::NT) k_x_node(const PassProgram P, const KParams kp) {
+__global__ void __launch_bounds__(Tile<T, N, true>::NT, 2) k_x_node(const PassProgram P, const KParams kp) {
     using TL = Tile<T, N, true>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* sm = reinterpret_cast<V*>(smraw);
-    T* tab = reinterpret_cast<T*>(sm + TL::SM_ELEMS);      // [2][G*N]
-    __shared__ int8_t slot_of[8];
     const int t = threadIdx.x, chain = blockIdx.y;
     int kz, c0;
     TL::tile_pos(blockIdx.x, kz, c0);
     const size_t base = TL::tile_base(kz, c0);
     const int g = TL::b_g(t);
-    // radial tables
-    {
-        int codes[2] = {-1, -1}, nc = 0;
-        for (int m = 0; m < P.n_merge + P.n_expand; ++m) {
-            const int c = m < P.n_merge ? P.merge[m].rcode : P.expand[m - P.n_merge].rcode;
-            if (c == R_ONE || c == R_INVK2) continue;
-            if (c != codes[0] && c != codes[1] && nc < 2) codes[nc++] = c;
-        }
-        if (t < 8) slot_of[t] = (t == codes[0]) ? 0 : ((t == codes[1]) ? 1 : 0);
-        const T kf = T(kp.kf);
-        for (int s = 0; s < nc; ++s)
-            for (int e = t; e < TL::G * N; e += TL::NT) {
-                const int mx = signed_freq(e % N, N), my = signed_freq(c0 + e / N, N);
-                const T k2 = kf * kf * T(mx * mx + my * my + kz * kz);
-                tab[s * (TL::G * N) + e] = radial<T>(codes[s], k2, kp);
-            }
-        __syncthreads();
-    }
+    const int my = signed_freq(c0 + g, N), mz = kz;
     V Q[TL::J][TL::N2];   // bit-reversed k2 order
 #pragma unroll
     for (int j = 0; j < TL::J; ++j)
@@ -327,10 +295,8 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT) k_x_node(const PassProgr
             const int k1 = TL::b_k1(t, j);
 #pragma unroll
             for (int i = 0; i < TL::N2; ++i) {
-                const int n = k1 + TL::N1 * bitrev(i, TL::N2);
-                int mx, my, mz;
-                TL::freqs(n, g, kz, c0, mx, my, mz);
-                Q[j][i] = cadd(Q[j][i], cmul(xnode_mult<T, N>(tm, mx, my, mz, kp, tab, slot_of, g * N + n), X[j][i]));
+                const int mx = signed_freq(k1 + TL::N1 * bitrev(i, TL::N2), N);
+                Q[j][i] = cadd(Q[j][i], cmul(xnode_mult<T>(tm, mx, my, mz, N, kp), X[j][i]));
             }
         }
     }
@@ -342,10 +308,8 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT) k_x_node(const PassProgr
             const int k1 = TL::b_k1(t, j);
 #pragma unroll
             for (int k2 = 0; k2 < TL::N2; ++k2) {
-                const int n = k1 + TL::N1 * k2;
-                int mx, my, mz;
-                TL::freqs(n, g, kz, c0, mx, my, mz);
-                Y[j][k2] = cmul(xnode_mult<T, N>(tm, mx, my, mz, kp, tab, slot_of, g * N + n), Q[j][bitrev(k2, TL::N2)]);
+                const int mx = signed_freq(k1 + TL::N1 * k2, N);
+                Y[j][k2] = cmul(xnode_mult<T>(tm, mx, my, mz, N, kp), Q[j][bitrev(k2, TL::N2)]);
             }
         }
         __syncthreads();
@@ -450,7 +414,7 @@ static cudaError_t col_n(int batch, const PassProgram& p, const KParams& kp, cud
 }
 template <typename T, int N> static cudaError_t xnode_n(int batch, const PassProgram& p, const KParams& kp, cudaStream_t s) {
     using TL = Tile<T, N, true>;
-    const size_t sm = size_t(TL::SM_ELEMS) * sizeof(cplx_t<T>) + 2 * size_t(TL::G) * N * sizeof(T);
+    const size_t sm = size_t(TL::SM_ELEMS) * sizeof(cplx_t<T>);
     cudaError_t e = set_smem(k_x_node<T, N>, sm);
     if (e != cudaSuccess) return e;
     k_x_node<T, N><<<dim3(TL::TILES, batch), TL::NT, sm, s>>>(p, kp);

@@ -38,7 +38,14 @@ struct KParams {
     double dx;        // L / N
     double pk_amp, pk_ns, pk_kc, pk_pow;
     double r_s;
+    // Radial factors tabulated by the integer m^2 = mx^2 + my^2 + mz^2 (k^2 = kf^2 m^2),
+    // computed on the host in FP64: table c-1 holds R_c for c = R_INVK2 .. R_1MKBLEND.
+    const void* rtab;
+    int rlen;         // entries per table: 3 (N/2)^2 + 1
 };
+
+// Fill the radial tables (host, FP64): out[(c-1) * rlen + m2] for c = 1..4.
+void radial_tables_host(int n, const KParams& kp, double* out);
 
 // Real-space z pass.  Fields: in[f] / out[f] for f < n_fields; chain strides in elements.
 struct ZProgram {

@@ -198,8 +198,12 @@ __global__ void __launch_bounds__(kPwThreads) k_pass_a(long long nvox, Fields16 
     int cnt = 0;
     PW_LOOP(i, nvox) {
         const size_t j = off + i;
+        // re-derive the table pointer each voxel so its 112 entries are read from
+        // shared memory when used instead of being kept live in registers
+        const BiasT<T>* Bp = &B;
+        asm volatile("" : "+l"(Bp));
         WebState<T, NR> S;
-        web_forward<T, NR>(th, j, rho[j], B, wp, S);
+        web_forward<T, NR>(th, j, rho[j], *Bp, wp, S);
         lnf_out[j] = S.lf.lnf;
         beta_out[j] = S.q.beta;
         accf += v_exp(S.lf.lnf);
@@ -210,24 +214,40 @@ __global__ void __launch_bounds__(kPwThreads) k_pass_a(long long nvox, Fields16 
 }
 
 // NB likelihood (pass B): ln nbar = ln f + ln C; partial sums of log P,
-// d log P/d ln nbar and nu^2.
+// d log P/d ln nbar and nu^2.  Four voxels per thread and iteration (16-byte
+// loads of ln f, beta, nu; 8-byte load of the counts).
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4_32a; };
+
 template <typename T>
 __global__ void __launch_bounds__(kPwThreads) k_pass_b(long long nvox, const T* lnf, const T* beta_i,
                                                       const uint16_t* c16, const T* nu, const ChainScalars* sc,
                                                       double* partial) {
+    using V4 = typename Vec4<T>::type;
     const int chain = blockIdx.y;
     const size_t off = (size_t)chain * nvox;
     const T lnC = T(sc[chain].lnC);
     T a0 = 0, a1 = 0, a2 = 0;
     double acc[3] = {0.0, 0.0, 0.0};
+    const long long n4 = nvox / 4;
+    const V4* lf4 = reinterpret_cast<const V4*>(lnf + off);
+    const V4* bt4 = reinterpret_cast<const V4*>(beta_i + off);
+    const V4* nu4 = reinterpret_cast<const V4*>(nu + off);
+    const ushort4* c4 = reinterpret_cast<const ushort4*>(c16 + off);
     int cnt = 0;
-    PW_LOOP(i, nvox) {
-        const size_t j = off + i;
-        NB<T> r;
-        nb_eval<T>((int)c16[j], lnf[j] + lnC, beta_i[j], true, r);
-        const T v = nu[j];
-        a0 += r.logp; a1 += r.g_lnnbar; a2 += v * v;
-        if (++cnt == 16) { acc[0] += a0; acc[1] += a1; acc[2] += a2; a0 = a1 = a2 = T(0); cnt = 0; }
+    for (long long i = (long long)blockIdx.x * kPwThreads + threadIdx.x; i < n4; i += (long long)gridDim.x * kPwThreads) {
+        const V4 l = lf4[i], b = bt4[i], v = nu4[i];
+        const ushort4 c = c4[i];
+        const T lv[4] = {l.x, l.y, l.z, l.w}, bv[4] = {b.x, b.y, b.z, b.w}, vv[4] = {v.x, v.y, v.z, v.w};
+        const int cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            NB<T> r;
+            nb_eval<T>(cv[q], lv[q] + lnC, bv[q], true, r);
+            a0 += r.logp; a1 += r.g_lnnbar; a2 += vv[q] * vv[q];
+        }
+        if (++cnt == 4) { acc[0] += a0; acc[1] += a1; acc[2] += a2; a0 = a1 = a2 = T(0); cnt = 0; }
     }
     acc[0] += a0; acc[1] += a1; acc[2] += a2;
     write_partials<3>(acc, partial);
@@ -237,8 +257,11 @@ __global__ void __launch_bounds__(kPwThreads) k_pass_b(long long nvox, const T* 
 // Web + bias + NB adjoint: g_delta (direct), g_T (6), g_H (6) and, when
 // requested (BIASG), the partial sums of d/d alpha_r and d/d beta_r.
 // ---------------------------------------------------------------------------
+#ifndef BRIDGE_WEBADJ_MINB
+#define BRIDGE_WEBADJ_MINB 2
+#endif
 template <typename T, int NR, bool BIASG>
-__global__ void __launch_bounds__(kPwThreads, 2) k_web_adj(long long nvox, Fields16 th, const T* rho,
+__global__ void __launch_bounds__(kPwThreads, BRIDGE_WEBADJ_MINB) k_web_adj(long long nvox, Fields16 th, const T* rho,
                                                           const uint16_t* c16, const BiasT<T>* bias, WebParams wp,
                                                           const ChainScalars* sc, Fields16 out, double* partial) {
     __shared__ BiasT<T> B;
@@ -255,10 +278,16 @@ __global__ void __launch_bounds__(kPwThreads, 2) k_web_adj(long long nvox, Field
     PW_LOOP(i, nvox) {
         const size_t j = off + i;
         const T dl = rho[j];
+        const BiasT<T>* Bp = &B;            // see k_pass_a
+        asm volatile("" : "+l"(Bp));
         WebState<T, NR> S;
-        web_forward<T, NR>(th, j, dl, B, wp, S);
+        web_forward<T, NR>(th, j, dl, *Bp, wp, S);
         T gd, gt[6], gh[6];
-        web_adjoint_voxel<T, NR, BIASG>(S, dl, (int)c16[j], lnC, gscale, B, wp, gd, gt, gh, ga, gb);
+        auto reload = [&](T a6[6], T h6[6]) {
+            load6<T>(th, 0, j, a6);
+            if constexpr (NR == 16) load6<T>(th, 6, j, h6);
+        };
+        web_adjoint_voxel<T, NR, BIASG>(S, dl, (int)c16[j], lnC, gscale, *Bp, wp, reload, gd, gt, gh, ga, gb);
         ((T*)out.p[0])[j] = gd;
 #pragma unroll
         for (int q = 0; q < 6; ++q) ((T*)out.p[1 + q])[j] = gt[q];

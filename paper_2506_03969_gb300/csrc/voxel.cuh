@@ -15,8 +15,19 @@ __device__ __forceinline__ float v_log1p(float x) { return log1pf(x); }
 __device__ __forceinline__ double v_log1p(double x) { return log1p(x); }
 __device__ __forceinline__ float v_acos(float x) { return acosf(x); }
 __device__ __forceinline__ double v_acos(double x) { return acos(x); }
-__device__ __forceinline__ void v_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
-__device__ __forceinline__ void v_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+// Fast single-precision exp/log/reciprocal for the web and bias arithmetic
+// (hardware approximations with relative errors of a few 1e-7 on the argument
+// ranges that occur; FP64 keeps the correctly rounded library functions).
+__device__ __forceinline__ float v_fexp(float x) { return __expf(x); }
+__device__ __forceinline__ double v_fexp(double x) { return exp(x); }
+__device__ __forceinline__ float v_flog(float x) { return __logf(x); }
+__device__ __forceinline__ double v_flog(double x) { return log(x); }
+__device__ __forceinline__ float v_fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double v_fdiv(double a, double b) { return a / b; }
+
+// sin/cos of pi * x (no large-argument reduction path)
+__device__ __forceinline__ void v_sincospi(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void v_sincospi(double x, double* s, double* c) { sincospi(x, s, c); }
 __device__ __forceinline__ float v_fmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double v_fmax(double a, double b) { return fmax(a, b); }
 
@@ -27,15 +38,12 @@ __device__ __forceinline__ double v_fmax(double a, double b) { return fmax(a, b)
 // solution of the characteristic cubic (Smith 1961), App. B ordering.
 template <typename T> struct Eig3 {
     T m;
-    T b[6];
     T mu[3];
 };
 
 template <typename T> __device__ __forceinline__ void eig3(const T a[6], Eig3<T>& e) {
     e.m = (a[0] + a[3] + a[5]) * T(1.0 / 3.0);
-    e.b[0] = a[0] - e.m; e.b[1] = a[1]; e.b[2] = a[2];
-    e.b[3] = a[3] - e.m; e.b[4] = a[4]; e.b[5] = a[5] - e.m;
-    const T* b = e.b;
+    const T b[6] = {a[0] - e.m, a[1], a[2], a[3] - e.m, a[4], a[5] - e.m};
     const T off = b[1] * b[1] + b[2] * b[2] + b[4] * b[4];
     const T p2 = (b[0] * b[0] + b[3] * b[3] + b[5] * b[5] + T(2) * off) * T(1.0 / 6.0);
     if (!(p2 > T(0))) { e.mu[0] = e.mu[1] = e.mu[2] = T(0); return; }
@@ -44,9 +52,10 @@ template <typename T> __device__ __forceinline__ void eig3(const T a[6], Eig3<T>
                   b[2] * (b[1] * b[4] - b[3] * b[2]);
     T r = det / (T(2) * p2 * p);
     r = r < T(-1) ? T(-1) : (r > T(1) ? T(1) : r);
-    const T phi = v_acos(r) * T(1.0 / 3.0);
+    // phi = acos(r)/3 in [0, pi/3], evaluated as sin/cos of pi * (phi / pi)
+    const T phi_pi = v_acos(r) * T(0.10610329539459689051);   // 1 / (3 pi)
     T s, c;
-    v_sincos(phi, &s, &c);
+    v_sincospi(phi_pi, &s, &c);
     // cos(phi + 2pi/3) = -c/2 - (sqrt3/2) s
     const T mu1 = T(2) * p * c;
     const T mu3 = T(2) * p * (T(-0.5) * c - T(0.86602540378443864676) * s);
@@ -55,7 +64,7 @@ template <typename T> __device__ __forceinline__ void eig3(const T a[6], Eig3<T>
     e.mu[0] = mu1; e.mu[1] = mu2; e.mu[2] = mu3;
 }
 
-template <typename T> __device__ __forceinline__ T sigmoid(T x) { return T(1) / (T(1) + v_exp(-x)); }
+template <typename T> __device__ __forceinline__ T sigmoid(T x) { return v_fdiv(T(1), T(1) + v_fexp(-x)); }
 
 // Fuzzy memberships (Eq. sigmoid, Eq. soft_cweb_p): w_n = sigma(s (lambda_n - th)),
 // p = (V, S, F, K) = (1 - w1, w1 - w2, w2 - w3, w3).  1 - w1 is formed as
@@ -69,30 +78,32 @@ template <typename T> __device__ __forceinline__ void memberships(const T lam[3]
     p[3] = w[2];
 }
 
-// Bias table of one chain (precision T), Eq. local_bias + NB beta.
-template <typename T> struct BiasT {
-    T a[16], alpha[16], rho[16], eps[16], rhop[16], epsp[16], beta[16];
+// Bias table of one chain (precision T), Eq. local_bias + NB beta, stored per
+// region as (a, alpha, rho, eps, rhop, epsp, beta, 0) so that one region is two
+// 16-byte (FP32) shared-memory loads.
+template <typename T> struct __align__(16) BiasT {
+    T pk[16][8];
 };
+enum { BP_A = 0, BP_ALPHA = 1, BP_RHO = 2, BP_EPS = 3, BP_RHOP = 4, BP_EPSP = 5, BP_BETA = 6 };
+
+// The 7 parameters of region r (vector loads from shared memory).
+__device__ __forceinline__ void region_params(const BiasT<float>& B, int r, float e[8]) {
+    const float4 lo = *reinterpret_cast<const float4*>(&B.pk[r][0]);
+    const float4 hi = *reinterpret_cast<const float4*>(&B.pk[r][4]);
+    e[0] = lo.x; e[1] = lo.y; e[2] = lo.z; e[3] = lo.w; e[4] = hi.x; e[5] = hi.y; e[6] = hi.z; e[7] = hi.w;
+}
+__device__ __forceinline__ void region_params(const BiasT<double>& B, int r, double e[8]) {
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+        const double2 d = *reinterpret_cast<const double2*>(&B.pk[r][q]);
+        e[q] = d.x; e[q + 1] = d.y;
+    }
+}
 
 // Per-voxel interpolated parameters b_i = sum_r b^(r) p_i^(r) (Sect. 2.8).
 template <typename T> struct VoxParams {
     T a, alpha, rho, eps, rhop, epsp, beta;
 };
-
-template <typename T, int NR>
-__device__ __forceinline__ void interp_params(const BiasT<T>& B, const T w[NR], VoxParams<T>& q) {
-    q.a = q.alpha = q.rho = q.eps = q.rhop = q.epsp = q.beta = T(0);
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        q.a += B.a[r] * w[r];
-        q.alpha += B.alpha[r] * w[r];
-        q.rho += B.rho[r] * w[r];
-        q.eps += B.eps[r] * w[r];
-        q.rhop += B.rhop[r] * w[r];
-        q.epsp += B.epsp[r] * w[r];
-        q.beta += B.beta[r] * w[r];
-    }
-}
 
 // ln f = ln a + alpha ln u - (u/rho)^eps - (rho'/u)^eps'  (Eq. local_bias in logs),
 // u = max(1 + delta, floor), passed in as the CIC mass rho = 1 + delta itself so
@@ -106,6 +117,8 @@ template <typename T> __device__ __forceinline__ void log_f(T rho_mass, T floor_
     T u = rho_mass;
     r.floored = !(u > floor_);
     if (r.floored) u = floor_;
+    // correctly rounded exp/log here: (u/rho)^eps reaches 1e3 in dense cells and
+    // dominates ln f there
     r.lnu = v_log(u);
     r.lnrho = v_log(q.rho);
     r.t1 = v_exp(q.eps * (r.lnu - r.lnrho));
@@ -126,19 +139,19 @@ template <typename T> struct NB {
     T logp, g_lnnbar, g_beta;
 };
 template <typename T> __device__ __forceinline__ void nb_eval(int n, T lnnbar, T beta, bool want_grad, NB<T>& r) {
-    const T nbar = v_exp(lnnbar);
-    const T l1 = v_log1p(nbar / beta);               // ln((beta + nbar)/beta)
+    const T nbar = v_fexp(lnnbar);
+    const T l1 = v_log1p(v_fdiv(nbar, beta));        // ln((beta + nbar)/beta)
     T s = T(0), ds = T(0);
     for (int m = 0; m < n; ++m) {
-        s += v_log((beta + T(m)) / T(m + 1));
-        if (want_grad) ds += T(1) / (beta + T(m));
+        s += v_flog(v_fdiv(beta + T(m), T(m + 1)));
+        if (want_grad) ds += v_fdiv(T(1), beta + T(m));
     }
     const T tn = T(n);
-    r.logp = s - beta * l1 + tn * (lnnbar - v_log(beta) - l1);
+    r.logp = s - beta * l1 + (n > 0 ? tn * (lnnbar - v_flog(beta) - l1) : T(0));
     if (want_grad) {
-        const T den = nbar + beta;
-        r.g_lnnbar = beta * (tn - nbar) / den;
-        r.g_beta = ds - l1 + (nbar - tn) / den;
+        const T rden = v_fdiv(T(1), nbar + beta);
+        r.g_lnnbar = beta * (tn - nbar) * rden;
+        r.g_beta = ds - l1 + (nbar - tn) * rden;
     }
 }
 
@@ -149,7 +162,7 @@ template <typename T> __device__ __forceinline__ void nb_eval(int n, T lnnbar, T
 // subgradient; the exact gradient is not defined at a crossing).  Output is the
 // derivative with respect to the stored components (off-diagonals count twice).
 template <typename T>
-__device__ __forceinline__ void eig_adjoint(const Eig3<T>& e, T g1, T g2, T g3, T tau, T out[6]) {
+__device__ __forceinline__ void eig_adjoint(const T a[6], const Eig3<T>& e, T g1, T g2, T g3, T tau, T out[6]) {
     const T mu1 = e.mu[0], mu2 = e.mu[1], mu3 = e.mu[2];
     const T scale = v_fmax(mu1 > T(0) ? mu1 : -mu1, mu3 > T(0) ? mu3 : -mu3) + v_fmax(e.m > T(0) ? e.m : -e.m, T(0));
     const T tol = tau * scale + T(1e-30);
@@ -164,7 +177,7 @@ __device__ __forceinline__ void eig_adjoint(const Eig3<T>& e, T g1, T g2, T g3, 
         const T gm = T(0.5) * (g2 + g3);
         g2 = g3 = gm;
     }
-    const T* b = e.b;
+    const T b[6] = {a[0] - e.m, a[1], a[2], a[3] - e.m, a[4], a[5] - e.m};
     T G[6] = {g2, T(0), T(0), g2, T(0), g2};
     const T c1 = g1 - g2, c3 = g3 - g2;
     if (c1 != T(0) || c3 != T(0)) {
@@ -238,8 +251,10 @@ __device__ __forceinline__ void web_eval(const T a6[6], const T h6[6], T rho_mas
         for (int b = 0; b < NK; ++b) {
             const int r = NK * a + b;
             const T w = region_w<T, NR>(S, a, b);
-            q.a += B.a[r] * w; q.alpha += B.alpha[r] * w; q.rho += B.rho[r] * w; q.eps += B.eps[r] * w;
-            q.rhop += B.rhop[r] * w; q.epsp += B.epsp[r] * w; q.beta += B.beta[r] * w;
+            T e[8];
+            region_params(B, r, e);
+            q.a += e[BP_A] * w; q.alpha += e[BP_ALPHA] * w; q.rho += e[BP_RHO] * w; q.eps += e[BP_EPS] * w;
+            q.rhop += e[BP_RHOP] * w; q.epsp += e[BP_EPSP] * w; q.beta += e[BP_BETA] * w;
         }
     log_f<T>(rho_mass, T(wp.rho_floor), S.q, S.lf);
 }
@@ -248,28 +263,28 @@ __device__ __forceinline__ void web_eval(const T a6[6], const T h6[6], T rho_mas
 // state, the CIC mass rho, the count n, ln C and G/N_tr.  Outputs: g_rho
 // (direct), g_T and g_H (stored components); accumulates d/d alpha_r and
 // d/d beta_r into ga/gb when BIASG.
-template <typename T, int NR, bool BIASG>
+template <typename T, int NR, bool BIASG, typename LoadT>
 __device__ __forceinline__ void web_adjoint_voxel(const WebState<T, NR>& S, T rho_mass, int n, T lnC, T gscale,
-                                                  const BiasT<T>& B, const WebParams& wp, T& gd, T gt[6], T gh[6],
-                                                  T* ga, T* gb) {
+                                                  const BiasT<T>& B, const WebParams& wp, LoadT load_tensors,
+                                                  T& gd, T gt[6], T gh[6], T* ga, T* gb) {
     const T s = T(wp.sharpness), tau = T(wp.tau);
     const T lnnbar = S.lf.lnf + lnC;
     NB<T> nb;
     nb_eval<T>(n, lnnbar, S.q.beta, true, nb);
-    const T nbar = v_exp(lnnbar);
+    const T nbar = v_fexp(lnnbar);
     const T glnf = nb.g_lnnbar - nbar * gscale;      // normalisation adjoint: f_i/sum f * G = nbar_i G / N_tr
     const T gbeta = nb.g_beta;
-    const T g_a = glnf / S.q.a;
+    const T g_a = v_fdiv(glnf, S.q.a);
     const T g_al = glnf * S.lf.lnu;
-    const T g_rho = glnf * S.q.eps * S.lf.t1 / S.q.rho;
+    const T g_rho = v_fdiv(glnf * S.q.eps * S.lf.t1, S.q.rho);
     const T g_eps = -glnf * S.lf.t1 * (S.lf.lnu - S.lf.lnrho);
     T g_rhop = T(0), g_epsp = T(0);
     if (S.q.rhop > T(0)) {
-        g_rhop = -glnf * S.q.epsp * S.lf.t2 / S.q.rhop;
+        g_rhop = -v_fdiv(glnf * S.q.epsp * S.lf.t2, S.q.rhop);
         g_epsp = -glnf * S.lf.t2 * (S.lf.lnrhop - S.lf.lnu);
     }
     // direct density derivative (zero below the floor); u = rho
-    gd = S.lf.floored ? T(0) : glnf * (S.q.alpha - S.q.eps * S.lf.t1 + S.q.epsp * S.lf.t2) / rho_mass;
+    gd = S.lf.floored ? T(0) : v_fdiv(glnf * (S.q.alpha - S.q.eps * S.lf.t1 + S.q.epsp * S.lf.t2), rho_mass);
     T gpphi[4] = {T(0), T(0), T(0), T(0)}, gpdel[4] = {T(0), T(0), T(0), T(0)};
     constexpr int NK = NR == 16 ? 4 : 1;
 #pragma unroll
@@ -277,8 +292,10 @@ __device__ __forceinline__ void web_adjoint_voxel(const WebState<T, NR>& S, T rh
 #pragma unroll
         for (int b = 0; b < NK; ++b) {
             const int r = NK * a + b;
-            const T gw = g_a * B.a[r] + g_al * B.alpha[r] + g_rho * B.rho[r] + g_eps * B.eps[r] + g_rhop * B.rhop[r] +
-                         g_epsp * B.epsp[r] + gbeta * B.beta[r];
+            T e[8];
+            region_params(B, r, e);
+            const T gw = g_a * e[BP_A] + g_al * e[BP_ALPHA] + g_rho * e[BP_RHO] + g_eps * e[BP_EPS] +
+                         g_rhop * e[BP_RHOP] + g_epsp * e[BP_EPSP] + gbeta * e[BP_BETA];
             if constexpr (NR == 16) {
                 gpphi[a] += gw * S.pdel[b];
                 gpdel[b] += gw * S.pphi[a];
@@ -291,17 +308,20 @@ __device__ __forceinline__ void web_adjoint_voxel(const WebState<T, NR>& S, T rh
                 gb[r] += gbeta * w;
             }
         }
+    // eigenvalue adjoint with the tensors reloaded (they are no longer live)
+    T a6[6], h6[6];
+    load_tensors(a6, h6);
     {
         const T g1 = (gpphi[1] - gpphi[0]) * s * S.wphi[0] * (T(1) - S.wphi[0]);
         const T g2 = (gpphi[2] - gpphi[1]) * s * S.wphi[1] * (T(1) - S.wphi[1]);
         const T g3 = (gpphi[3] - gpphi[2]) * s * S.wphi[2] * (T(1) - S.wphi[2]);
-        eig_adjoint<T>(S.ephi, g1, g2, g3, tau, gt);
+        eig_adjoint<T>(a6, S.ephi, g1, g2, g3, tau, gt);
     }
     if constexpr (NR == 16) {
         const T g1 = (gpdel[1] - gpdel[0]) * s * S.wdel[0] * (T(1) - S.wdel[0]);
         const T g2 = (gpdel[2] - gpdel[1]) * s * S.wdel[1] * (T(1) - S.wdel[1]);
         const T g3 = (gpdel[3] - gpdel[2]) * s * S.wdel[2] * (T(1) - S.wdel[2]);
-        eig_adjoint<T>(S.edel, g1, g2, g3, tau, gh);
+        eig_adjoint<T>(h6, S.edel, g1, g2, g3, tau, gh);
     }
 }
 

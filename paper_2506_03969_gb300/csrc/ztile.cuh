@@ -19,7 +19,7 @@ template <typename T> __device__ __forceinline__ cplx_t<T> ztw_load(int N, int j
 
 template <typename T, int N, int GY_> struct ZCfg {
     using V = cplx_t<T>;
-    using V4 = typename std::conditional<sizeof(T) == 4, float4, double4>::type;
+    using V4 = typename std::conditional<sizeof(T) == 4, float4, double4_32a>::type;
     static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, J = N1 / N2;
     static constexpr int GY = GY_ < N ? GY_ : N;
     static constexpr int GC = 8 * GY;                 // complex lines per tile
@@ -37,10 +37,20 @@ template <typename T, int N, int GY_> struct ZCfg {
     }
 };
 
+// 16/32-byte spectrum accesses; STREAM marks data touched once (evict-first in L2).
+template <bool STREAM, typename V4> __device__ __forceinline__ V4 zld4(const V4* p) {
+    if constexpr (STREAM && std::is_same<V4, float4>::value) return __ldcs(p);
+    else return *p;
+}
+template <bool STREAM, typename V4> __device__ __forceinline__ void zst4(V4* p, const V4& v) {
+    if constexpr (STREAM && std::is_same<V4, float4>::value) __stcs(p, v);
+    else *p = v;
+}
+
 // Forward: real lines -> spectrum.  line(c) returns the pointer of real line
 // a of complex line c; line b is at line(c) + bstride.  Must be called by all
 // threads t < C::NT of the block (it synchronises with __syncthreads).
-template <typename C, typename LineFn>
+template <typename C, typename LineFn, bool STREAM = false>
 __device__ __forceinline__ void ztile_fwd(LineFn line, long long bstride, typename C::V* __restrict__ spec,
                                           int x0, int y0, typename C::V* sm, int t) {
     using V = typename C::V;
@@ -94,13 +104,13 @@ __device__ __forceinline__ void ztile_fwd(LineFn line, long long bstride, typena
         ab.y = h * (z1.y - z2.y);
         ab.z = h * (z1.y + z2.y);
         ab.w = h * (z2.x - z1.x);
-        *reinterpret_cast<V4*>(spec + (size_t(kz) * N + (y0 + yl)) * N + x0 + 2 * pair) = ab;
+        zst4<STREAM>(reinterpret_cast<V4*>(spec + (size_t(kz) * N + (y0 + yl)) * N + x0 + 2 * pair), ab);
     }
     __syncthreads();
 }
 
 // Inverse: spectrum -> real lines (unnormalised).  Same calling rules.
-template <typename C, typename LineFn>
+template <typename C, typename LineFn, bool STREAM = false>
 __device__ __forceinline__ void ztile_inv(const typename C::V* __restrict__ spec, LineFn line, long long bstride,
                                           int x0, int y0, typename C::V* sm, int t) {
     using V = typename C::V;
@@ -112,7 +122,7 @@ __device__ __forceinline__ void ztile_inv(const typename C::V* __restrict__ spec
     for (int idx = t / 8; idx < (N / 2 + 1) * C::GY; idx += ROWS) {
         const int kz = idx / C::GY, yl = idx % C::GY;
         const int c = yl * 8 + pair;
-        const V4 ab = *reinterpret_cast<const V4*>(spec + (size_t(kz) * N + (y0 + yl)) * N + x0 + 2 * pair);
+        const V4 ab = zld4<STREAM>(reinterpret_cast<const V4*>(spec + (size_t(kz) * N + (y0 + yl)) * N + x0 + 2 * pair));
         if (kz == 0 || kz == N / 2) {
             sm[c * C::ZS + kz] = cmake<V>(ab.x, ab.z);   // real parts only
         } else {

@@ -82,7 +82,7 @@ def test_pk_amplitude_matches_oracle_quadrature(pkg):
 def test_status_strings(pkg):
     for s in range(7):
         assert pkg.lib().bridge_status_string(s)
-    assert pkg.lib().bridge_last_error(None) == b"context is NULL"
+    assert pkg.lib().bridge_last_error(None)
 
 
 def test_bias_marshalling(pkg):
@@ -103,3 +103,4 @@ def test_create_without_device_fails_cleanly(pkg):
     h = ctypes.c_void_p()
     st = pkg.lib().bridge_create(ctypes.byref(cfg), None, ctypes.byref(h))
     assert st == pkg.BRIDGE_ENODEVICE and not h.value
+    assert b"device" in pkg.lib().bridge_last_error(None)
