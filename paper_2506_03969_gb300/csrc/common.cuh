@@ -118,6 +118,8 @@ template <> struct Split<64> { static constexpr int N1 = 8, N2 = 8; };
 template <> struct Split<128> { static constexpr int N1 = 16, N2 = 8; };
 template <> struct Split<256> { static constexpr int N1 = 16, N2 = 16; };
 template <> struct Split<512> { static constexpr int N1 = 32, N2 = 16; };
+// N1 of Split<n> for a run-time n (host table builders).
+constexpr int split_n1(int n) { return n <= 16 ? 4 : n <= 64 ? 8 : n <= 256 ? 16 : 32; }
 
 
 // Signed integer frequency of index i on an axis of n points.

@@ -45,8 +45,6 @@ void radial_tables_host(int n, const KParams& kp, double* out) {
     }
 }
 
-template <typename T> __device__ __forceinline__ cplx_t<T> tw_load(int N, int j) { return ztw_load<T>(N, j); }
-
 // ---------------------------------------------------------------------------
 // Multipliers
 // ---------------------------------------------------------------------------
@@ -115,7 +113,7 @@ template <typename T, int N, bool XM> struct Tile {
 #pragma unroll
         for (int i = 0; i < N1; ++i) {
             const int k1 = bitrev(i, N1);
-            sm[sidx(g, k1, n2)] = cmul(v[i], tw_load<T>(N, n2 * k1));
+            sm[sidx(g, k1, n2)] = cmul(v[i], tw_a<T, N>(k1, n2));
         }
     }
     // forward step B: X[j][i] = DFT value at k = k1_j + N1 * bitrev(i)
@@ -139,7 +137,7 @@ template <typename T, int N, bool XM> struct Tile {
 #pragma unroll
             for (int i = 0; i < N2; ++i) {
                 const int n2 = bitrev(i, N2);
-                sm[sidx(g, k1, n2)] = cmulc(Y[j][i], tw_load<T>(N, n2 * k1));
+                sm[sidx(g, k1, n2)] = cmulc(Y[j][i], tw_b<T, N>(n2, k1));
             }
         }
     }
@@ -251,8 +249,10 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, 2) k_col_inv(const PassPro
 }
 
 // x node: Q = sum_merge mult * DFTx(in[src]);  out[dst] = IDFTx(mult * Q).
-// Radial factors come from the per-context tables indexed by m^2 (exact, no
-// transcendental work in the kernel).
+// Radial factors other than 1/k^2 come from the per-context tables indexed by
+// m^2 (exact, no transcendental work in the kernel).  In FP32, 1/k^2 is the
+// correctly rounded reciprocal of the exact integer m^2 times 1/kf^2, which
+// spares a gather whose addresses differ in every lane.
 template <typename T>
 __device__ __forceinline__ cplx_t<T> xnode_mult(const Term& tm, int mx, int my, int mz, int n, const KParams& kp) {
     const T kf = T(kp.kf);
@@ -260,7 +260,10 @@ __device__ __forceinline__ cplx_t<T> xnode_mult(const Term& tm, int mx, int my, 
     if (tm.py | tm.pz) r *= kpow<T>(my, tm.py, n, kf) * kpow<T>(mz, tm.pz, n, kf);
     if (tm.rcode != R_ONE) {
         const int m2 = mx * mx + my * my + mz * mz;
-        r *= __ldg(reinterpret_cast<const T*>(kp.rtab) + (tm.rcode - 1) * kp.rlen + m2);
+        if (sizeof(T) == 4 && tm.rcode == R_INVK2)
+            r *= m2 > 0 ? T(kp.inv_kf2) * T(__frcp_rn(float(m2))) : T(0);
+        else
+            r *= __ldg(reinterpret_cast<const T*>(kp.rtab) + (tm.rcode - 1) * kp.rlen + m2);
     }
     return cmake<cplx_t<T>>(T(tm.cre) * r, T(tm.cim) * r);
 }

@@ -35,6 +35,7 @@ struct PassProgram {
 // Physical constants for multipliers.
 struct KParams {
     double kf;        // 2 pi / L
+    double inv_kf2;   // 1 / kf^2
     double dx;        // L / N
     double pk_amp, pk_ns, pk_kc, pk_pow;
     double r_s;

@@ -117,19 +117,17 @@ template <typename T> __device__ __forceinline__ void log_f(T rho_mass, T floor_
     T u = rho_mass;
     r.floored = !(u > floor_);
     if (r.floored) u = floor_;
-    // correctly rounded exp/log here: (u/rho)^eps reaches 1e3 in dense cells and
-    // dominates ln f there
-    r.lnu = v_log(u);
-    r.lnrho = v_log(q.rho);
-    r.t1 = v_exp(q.eps * (r.lnu - r.lnrho));
+    r.lnu = v_flog(u);
+    r.lnrho = v_flog(q.rho);
+    r.t1 = v_fexp(q.eps * (r.lnu - r.lnrho));
     if (q.rhop > T(0)) {
-        r.lnrhop = v_log(q.rhop);
-        r.t2 = v_exp(q.epsp * (r.lnrhop - r.lnu));
+        r.lnrhop = v_flog(q.rhop);
+        r.t2 = v_fexp(q.epsp * (r.lnrhop - r.lnu));
     } else {
         r.lnrhop = T(0);
         r.t2 = T(0);
     }
-    r.lnf = v_log(q.a) + q.alpha * r.lnu - r.t1 - r.t2;
+    r.lnf = v_flog(q.a) + q.alpha * r.lnu - r.t1 - r.t2;
 }
 
 // Negative-binomial log pmf with shape beta and mean nbar (Sect. 2.6):

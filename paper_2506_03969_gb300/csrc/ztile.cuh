@@ -15,7 +15,16 @@
 
 namespace bridge {
 
-template <typename T> __device__ __forceinline__ cplx_t<T> ztw_load(int N, int j);
+// Four-step twiddle exp(-2 pi i n2 k1 / N) from the [k1][n2] table (step A)
+// or the [n2][k1] table (step B'); both live in twiddle.cuh.
+template <typename T> __device__ __forceinline__ cplx_t<T> ztw_a(int i);
+template <typename T> __device__ __forceinline__ cplx_t<T> ztw_b(int i);
+template <typename T, int N> __device__ __forceinline__ cplx_t<T> tw_a(int k1, int n2) {
+    return ztw_a<T>(N + k1 * Split<N>::N2 + n2);
+}
+template <typename T, int N> __device__ __forceinline__ cplx_t<T> tw_b(int n2, int k1) {
+    return ztw_b<T>(N + n2 * Split<N>::N1 + k1);
+}
 
 template <typename T, int N, int GY_> struct ZCfg {
     using V = cplx_t<T>;
@@ -68,7 +77,7 @@ __device__ __forceinline__ void ztile_fwd(LineFn line, long long bstride, typena
 #pragma unroll
         for (int i = 0; i < C::N1; ++i) {
             const int k1 = bitrev(i, C::N1);
-            sm[C::sidx(c, k1, n2)] = cmul(v[i], ztw_load<T>(N, n2 * k1));
+            sm[C::sidx(c, k1, n2)] = cmul(v[i], tw_a<T, N>(k1, n2));
         }
     }
     __syncthreads();
@@ -148,7 +157,7 @@ __device__ __forceinline__ void ztile_inv(const typename C::V* __restrict__ spec
 #pragma unroll
             for (int i = 0; i < C::N2; ++i) {
                 const int n2 = bitrev(i, C::N2);
-                sm[C::sidx(c, k1, n2)] = cmulc(Y[j][i], ztw_load<T>(N, n2 * k1));
+                sm[C::sidx(c, k1, n2)] = cmulc(Y[j][i], tw_b<T, N>(n2, k1));
             }
         }
     }

@@ -1,12 +1,12 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Tolerances: FP32 fields relative L2 <= 1e-5, log posterior |d|/|lp| <= 1e-6;
-the FP64 path <= 1e-10 (fields) and 1e-12 (log posterior).  Gradients:
-relative L2 <= max(1e-4, 10 S) in FP32 and <= max(1e-10, 1e-7 S) in FP64,
-where S is the conditioning of the gradient at the test point, measured with
-the oracle alone: the relative change of the exact (FP64) gradient when nu is
-perturbed by 2^-23 times its standard deviation (one FP32 rounding of the
-input).  At most points S is far below 1e-5 and the 1e-4 bound governs; at
+Tolerances: FP32 fields relative L2 <= max(1e-5, 10 S), log posterior
+|d|/|lp| <= 1e-6; the FP64 path <= max(1e-10, 1e-7 S) (fields) and 1e-12 (log
+posterior).  Gradients: relative L2 <= max(1e-4, 10 S) in FP32 and
+<= max(1e-10, 1e-7 S) in FP64.  S is the conditioning of that output at the
+test point, measured with the oracle alone: the relative change of the exact
+(FP64) field or gradient when nu is perturbed by 2^-23 times its standard
+deviation (one FP32 rounding of the input).  At most points S is far below 1e-5 and the 1e-4 bound governs; at
 points where a few cells with tracers but almost no model mass dominate the
 gradient, no FP32 evaluation can do better than S.  Nothing is bit-exact: CIC
 atomics reorder sums.
@@ -65,16 +65,27 @@ def oracle_ref(key, cfg, bias, nu, counts):
     if key not in ORACLE:
         f = model.forward_fields(nu, counts, cfg, bias)
         lp, g, ga, gb = model.logpost_and_grad(nu, counts, cfg, bias)
-        # conditioning of the gradient at this point (oracle only)
+        # conditioning of the gradient and of every field at this point (oracle only)
         pert = np.random.default_rng(12345).standard_normal(nu.shape) * (2.0 ** -23) * float(np.std(nu))
         _, g2, _, _ = model.logpost_and_grad(nu + pert, counts, cfg, bias)
         cond = float(np.linalg.norm(g2 - g) / np.linalg.norm(g))
+        f2 = model.forward_fields(nu + pert, counts, cfg, bias)
+        f["cond"] = {k: float(np.linalg.norm(f2[k] - f[k]) / np.linalg.norm(f[k]))
+                     for k in f if isinstance(f[k], np.ndarray) and f[k] is not None}
         ORACLE[key] = (f, lp, g, np.concatenate([ga, gb]), cond)
     return ORACLE[key]
 
 
 def grad_tol(precision, cond):
     return max(FP32_GRAD, 10.0 * cond) if precision == "fp32" else max(FP64_GRAD, 1e-7 * cond)
+
+
+def field_tol(base, cond):
+    """Same rule as the gradient: the stated bound, unless the field's own conditioning S
+    at the test point puts it out of FP32 reach (ln nbar at 256^3: in cells with a CIC mass
+    below 1e-4, alpha ln(1+delta) follows the relative change of that mass, so the last bits
+    of the displacement move it by 1e-2)."""
+    return max(base, 10.0 * cond) if base >= FP32_FIELD else max(base, 1e-7 * cond)
 
 
 CASES = {
@@ -90,15 +101,17 @@ def _fields_check(ctx, nu_d, c_d, bias, f, tol):
               (pkg.FIELD_TIDAL, f["T"]), (pkg.FIELD_LAMBDA, f["lam_phi"]), (pkg.FIELD_LNNBAR, f["ln_nbar"])]
     if f.get("H") is not None:
         checks.append((pkg.FIELD_HESSIAN, f["H"]))
-    errs = {}
+    errs, tols = {}, {}
     names = {pkg.FIELD_DELTA0: "delta0", pkg.FIELD_PSI: "psi", pkg.FIELD_DELTA: "delta", pkg.FIELD_TIDAL: "T",
-             pkg.FIELD_LAMBDA: "lambda", pkg.FIELD_LNNBAR: "ln_nbar", pkg.FIELD_HESSIAN: "H"}
+             pkg.FIELD_LAMBDA: "lam_phi", pkg.FIELD_LNNBAR: "ln_nbar", pkg.FIELD_HESSIAN: "H"}
     for which, ref in checks:
         got = ctx.bridge_debug_field(nu_d, c_d, [bias], which).double().cpu().numpy().reshape(ref.shape)
-        errs[names[which]] = rel_l2(got, ref)
+        k = names[which]
+        errs[k] = rel_l2(got, ref)
+        tols[k] = field_tol(tol, f["cond"][k])
     print("field rel L2:", {k: f"{v:.2e}" for k, v in errs.items()})
-    bad = {k: v for k, v in errs.items() if not v <= tol}
-    assert not bad, f"field rel L2 above {tol}: {errs}"
+    bad = {k: (v, tols[k]) for k, v in errs.items() if not v <= tols[k]}
+    assert not bad, f"field rel L2 above tolerance (err, tol): {bad}"
 
 
 @pytest.mark.parametrize("name", ["16_phi", "32_phi", "64_hier", "128_hier"])
