@@ -202,9 +202,48 @@ int bridge_profile_read(bridge_ctx* ctx, bridge_profile_row* rows, int max_rows)
 /* Number of kernel launches the most recent call on this context issued. */
 int64_t bridge_last_launch_count(const bridge_ctx* ctx);
 
+/* Linear density delta0 = IDFT[ sqrt(P(k)/dx^3) DFT(nu) ] (M_delta, App. A)
+ * without allocating device memory and without a context.  The paper has no
+ * counterpart: this is an interface for callers that cannot allocate device
+ * memory at the point where they need initial conditions (a fixed memory
+ * budget, a pool owned by someone else, or code where a cudaMalloc would
+ * synchronise the device), while bridge_create allocates a whole workspace.
+ *
+ *   cfg     n, batch, box, pk_amp, pk_ns, pk_kc, pk_pow and precision are used;
+ *           the whole configuration must pass bridge_validate_config.
+ *   nu      device [B][N^3] white noise (float or double per precision), read.
+ *   delta0  device [B][N^3] output, same type; must not overlap nu.
+ *   stream  CUDA stream (cudaStream_t) or NULL for the legacy default stream.
+ *
+ * The result equals BRIDGE_FIELD_DELTA0 of bridge_debug_field for the same
+ * configuration and nu (the same kernels; only the radial factor table is
+ * computed on the device instead of the host).
+ *
+ * Scratch.  The intermediate half spectra and the radial table live in one
+ * static device array of 4 MiB inside the library: a call needs
+ *   align256(B (N/2+1) N^2 * 2 * esz) + align256(2 (3 (N/2)^2 + 1) * esz)
+ * bytes (esz = 4 or 8), e.g. N <= 64 with B = 1 in either precision, or B <= 3
+ * at N = 64 in FP32.  Larger problems return BRIDGE_EINVAL before anything is
+ * launched.  No part of the scratch has to start at zero.  The array is one
+ * per device: calls whose work can overlap on the device (different streams,
+ * or host threads with their own streams) race on it and give wrong results;
+ * calls on one stream are ordered and safe.
+ *
+ * The first call on each device, made with that device current, looks up the
+ * array's address (cudaGetSymbolAddress) and uploads the FFT twiddle tables;
+ * make that first call outside any stream capture.
+ *
+ * Asynchronous: returns once the work is enqueued on `stream`; delta0 is
+ * ready, and the scratch free for another stream, when the stream reaches the
+ * end of this work.  Errors: EINVAL (config, NULL pointer, size limit),
+ * ENODEVICE, ECUDA (launch failure); kernel faults surface at the caller's
+ * next synchronisation.  bridge_last_error(NULL) describes the last failure
+ * of this call on the calling thread. */
+int bridge_delta0_noalloc(const bridge_config* cfg, const void* nu, void* delta0, void* stream);
+
 /* Text of the last error on this context (never NULL; "" if none).  With a NULL
- * context: the reason the last bridge_create on this thread failed, or
- * "context is NULL". */
+ * context: the reason the last bridge_create or bridge_delta0_noalloc on this
+ * thread failed, or "context is NULL". */
 const char* bridge_last_error(const bridge_ctx* ctx);
 
 /* Static description of a status code. */

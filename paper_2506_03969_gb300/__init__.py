@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
     L.bridge_profile_enable.argtypes = [vp, ctypes.c_int]; L.bridge_profile_enable.restype = ctypes.c_int
     L.bridge_profile_read.argtypes = [vp, ctypes.POINTER(bridge_profile_row), ctypes.c_int]
     L.bridge_profile_read.restype = ctypes.c_int
+    L.bridge_delta0_noalloc.argtypes = [cp, vp, vp, vp]; L.bridge_delta0_noalloc.restype = ctypes.c_int
     L.bridge_last_error.argtypes = [vp]; L.bridge_last_error.restype = ctypes.c_char_p
     L.bridge_status_string.argtypes = [ctypes.c_int]; L.bridge_status_string.restype = ctypes.c_char_p
     _lib = L
@@ -260,6 +261,24 @@ class Context:
         self._check(lib().bridge_debug_field(self.handle, ctypes.c_void_p(_ptr(nu)), ctypes.c_void_p(_ptr(counts)),
                                              bias_array(biases), int(which), ctypes.c_void_p(_ptr(out))))
         return out
+
+
+def bridge_delta0_noalloc(cfg: bridge_config, nu, delta0, stream=None):
+    """delta0 = IDFT[sqrt(P/dx^3) DFT(nu)] (App. A) into the caller's `delta0`, with no device
+    allocation and no context (scratch is a 4 MiB static array in the library; see bridge.h).
+    nu, delta0: contiguous CUDA tensors of batch * n^3 elements (float32, or float64 for FP64).
+    Asynchronous on `stream` (default: torch's current stream)."""
+    import torch
+    dt = torch.float64 if cfg.precision == BRIDGE_FP64 else torch.float32
+    for t, name in ((nu, "nu"), (delta0, "delta0")):
+        if t.device.type != "cuda" or t.dtype != dt or not t.is_contiguous() or t.numel() != cfg.batch * cfg.n ** 3:
+            raise ValueError(f"{name} must be a contiguous CUDA {dt} tensor of batch * n^3 elements")
+    s = stream if stream is not None else torch.cuda.current_stream(nu.device)
+    st = lib().bridge_delta0_noalloc(ctypes.byref(cfg), ctypes.c_void_p(_ptr(nu)), ctypes.c_void_p(_ptr(delta0)),
+                                     ctypes.c_void_p(s.cuda_stream))
+    if st != BRIDGE_OK:
+        raise BridgeError(st, lib().bridge_status_string(st).decode() + ": " + lib().bridge_last_error(None).decode())
+    return delta0
 
 
 def _make_autograd():

@@ -24,7 +24,7 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-O2", "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["nodes_f32.cu", "nodes_f64.cu", "passes.cu", "pointwise.cu", "api.cu"]
+SOURCES = ["nodes_f32.cu", "nodes_f64.cu", "passes.cu", "pointwise.cu", "api.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

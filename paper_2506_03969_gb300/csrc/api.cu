@@ -835,6 +835,16 @@ static int create_fail(bridge_ctx* ctx, int status, const std::string& why) {
     return status;
 }
 
+}  // extern "C"
+
+namespace bridge {
+// For the context-free entry point (noalloc.cu).
+int validate_config_reason(const bridge_config* c, std::string* why) { return validate(c, why); }
+void set_noctx_error(const std::string& why) { g_create_error = why; }
+}  // namespace bridge
+
+extern "C" {
+
 int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
     g_create_error.clear();
     if (!out) return create_fail(nullptr, BRIDGE_EINVAL, "out is NULL");
@@ -859,6 +869,7 @@ int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
     ctx->nspec = (long long)(cfg->n / 2 + 1) * cfg->n * cfg->n;
     ctx->esz = cfg->precision == BRIDGE_FP64 ? 8 : 4;
     ctx->kp.kf = 2.0 * kPi / cfg->box;
+    ctx->kp.inv_kf2 = 1.0 / (ctx->kp.kf * ctx->kp.kf);
     ctx->kp.dx = cfg->box / cfg->n;
     ctx->kp.pk_amp = cfg->pk_amp; ctx->kp.pk_ns = cfg->pk_ns; ctx->kp.pk_kc = cfg->pk_kc; ctx->kp.pk_pow = cfg->pk_pow;
     ctx->kp.r_s = cfg->r_s;
