@@ -374,19 +374,32 @@ def run_extras(pkg, synth, cfg, bias, nu32, counts, args):
                              "fp32_vs_fp64_grad_rel_l2": float(torch.linalg.vector_norm(g32.double() - g64) /
                                                                torch.linalg.vector_norm(g64)),
                              "fp32_vs_fp64_logpost_rel": abs(lp32[0] - lp64[0]) / abs(lp64[0])}
-    # HMC trajectory at 256^3: 10 leapfrog steps, eps = 0.05, FP32 vs FP64 dH
+    # HMC trajectory at 256^3: 10 leapfrog steps, eps = 0.05, identity mass, FP32 vs FP64 dH.
+    # Data drawn from the model: gamma-Poisson counts (beta = 5) around the FP64 path's nbar at
+    # nu_true (the timing counts only fix N_tr there); the trajectory starts at nu_true.
+    nu_t = torch.tensor(synth.white_noise(cfg.n, cfg.seed_truth), dtype=torch.float64, device="cuda")
+    _, lnnbar = c64.bridge_forward(nu_t, counts, [bias], want_ln_nbar=True)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(cfg.seed_counts)
+    shape = torch.full_like(lnnbar, 5.0)
+    rate = torch.exp(lnnbar) * torch._standard_gamma(shape, generator=gen) / 5.0
+    counts_m = torch.poisson(rate, generator=gen).clamp_(max=65535).to(torch.int32).contiguous()
     p0 = torch.tensor(synth.momentum(cfg.n, cfg.seed_momentum), dtype=torch.float64, device="cuda")
-    n64, p64 = nu64.clone(), p0.clone()
-    h0a, h1a = c64.bridge_leapfrog(n64, p64, counts, [bias], 10, 0.05)
-    n32, p32 = nu32.clone(), p0.float()
+    n64, p64 = nu_t.clone(), p0.clone()
+    h0a, h1a = c64.bridge_leapfrog(n64, p64, counts_m, [bias], 10, 0.05)
+    n32, p32 = nu_t.float(), p0.float()
     t0 = time.perf_counter()
-    h0b, h1b = c32.bridge_leapfrog(n32, p32, counts, [bias], 10, 0.05)
+    h0b, h1b = c32.bridge_leapfrog(n32, p32, counts_m, [bias], 10, 0.05)
     torch.cuda.synchronize()
     tl = time.perf_counter() - t0
     out["hmc_256_10_steps"] = {"dH_fp64": h1a[0] - h0a[0], "dH_fp32": h1b[0] - h0b[0],
+                               "H0_fp64": h0a[0], "H0_fp32_minus_fp64": h0b[0] - h0a[0],
                                "nu_rel_l2_fp32_vs_fp64": float(torch.linalg.vector_norm(n32.double() - n64) /
                                                                torch.linalg.vector_norm(n64)),
-                               "fp32_trajectory_s": tl}
+                               "p_rel_l2_fp32_vs_fp64": float(torch.linalg.vector_norm(p32.double() - p64) /
+                                                              torch.linalg.vector_norm(p64)),
+                               "fp32_trajectory_s": tl,
+                               "data": "gamma-Poisson mock (beta 5) of the model at nu_true, start at nu_true"}
     del c64
     # batched: 16 chains at 128^3 in one launch per pass
     cb = synth.config(3)

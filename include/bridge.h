@@ -29,6 +29,11 @@
  *   p^V = 1 - w1, p^S = w1 - w2, p^F = w2 - w3, p^K = w3 (regions V,S,F,K =
  *   0..3); 16-region models use region 4*j + k for Phi class j, delta class k.
  *
+ * Alignment.  Device buffers passed to a context (nu, counts, p, outputs) must
+ * start on a 16-byte boundary (every CUDA or PyTorch allocation does, and so
+ * does any chain offset of a [B][N^3] buffer); otherwise the call returns
+ * BRIDGE_EINVAL.
+ *
  * Ownership.  The caller owns every buffer and the CUDA stream.  A context owns
  * its device workspace (allocated once in bridge_create, sized by
  * bridge_workspace_bytes) and releases it in bridge_destroy.  Calls on one

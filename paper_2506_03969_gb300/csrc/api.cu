@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -198,8 +199,8 @@ Plan make_plan(const bridge_config* c) {
     p.spec_bytes = align_up(size_t(nspec) * 2 * esz * B);
     p.real_bytes = align_up(size_t(nvox) * esz * B);
     p.c16_bytes = align_up(size_t(nvox) * 2 * B);
-    // node grids are bounded by the SM count (at most 4 CTAs per SM on a GB300's 152 SMs)
-    const size_t max_blocks = pw_blocks(c->n) > 1024 ? size_t(pw_blocks(c->n)) : size_t(1024);
+    // partial sums: one row per block of the real-space kernels
+    const size_t max_blocks = size_t(pw_blocks(c->n));
     p.partial_bytes = align_up(size_t(B) * max_blocks * 32 * sizeof(double));
     p.sc_bytes = align_up(sizeof(ChainScalars) * B);
     p.biasd_bytes = align_up(sizeof(BiasD) * B);
@@ -356,15 +357,11 @@ template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelih
         add_expand(p, mk(1, 2, 0, 0, 1, R_ONE, 1.0));
         CKL("y_inv", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_inv<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
-    // CIC (mass rho accumulated into a zeroed field)
+    // CIC (mass rho accumulated into a zeroed field); the displacement in real
+    // space borrows the tensor buffers, which are written only afterwards
+    RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_PSI, 3), mreal(ctx, RB_TH, 3)));
     CKL("fill", rby<T>(ctx), launch_fill<T>(ctx->nvox * ctx->B, RB<T>(ctx, RB_DELTA), T(0), ctx->stream));
-    {
-        NodeArgs na{};
-        na.kind = NODE_SCATTER;
-        for (int f = 0; f < 3; ++f) na.spec_in[f] = ctx->spec[SP_PSI + f];
-        na.real_out[0] = ctx->real[RB_DELTA];
-        RUN(node<T>(ctx, na, "node_cic_scatter", 3 * sby<T>(ctx) + rby<T>(ctx), nullptr));
-    }
+    CKL("cic_scatter", 4 * rby<T>(ctx), launch_cic_scatter<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 3), RB<T>(ctx, RB_DELTA), ctx->stream));
     // tidal tensor and density Hessian spectra (Sect. 2.8, App. B)
     RUN(z_fwd<T>(ctx, creal(ctx, RB_DELTA, 1), mspec<T>(ctx, SP_SCR, 1)));
     RUN(y_identity<T>(ctx, SP_SCR, 1, true));
@@ -827,6 +824,14 @@ double bridge_pk_amplitude(double sigma, double radius, double ns, double kc, do
     return sigma * sigma / s2;
 }
 
+// Device buffers are read with 16-byte vector loads.
+static bool aligned16(std::initializer_list<const void*> ptrs) {
+    for (const void* p : ptrs)
+        if (reinterpret_cast<uintptr_t>(p) & 15u) return false;
+    return true;
+}
+static const char* const kAlignMsg = "device buffers must start on a 16-byte boundary";
+
 static thread_local std::string g_create_error;
 
 static int create_fail(bridge_ctx* ctx, int status, const std::string& why) {
@@ -964,6 +969,7 @@ int bridge_forward(bridge_ctx* ctx, const void* nu, const int32_t* counts, const
     if (!ctx) return BRIDGE_EINVAL;
     ctx->launches = 0;
     ctx->err.clear();
+    if (!aligned16({nu, counts, ln_nbar_out})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
     return DISPATCH(ctx, do_forward, nu, counts, bias, ln_nbar_out, logpost_out);
 }
 
@@ -972,6 +978,7 @@ int bridge_logpost_grad(bridge_ctx* ctx, const void* nu, const int32_t* counts, 
     if (!ctx) return BRIDGE_EINVAL;
     ctx->launches = 0;
     ctx->err.clear();
+    if (!aligned16({nu, counts, grad_nu_out})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
     return DISPATCH(ctx, do_grad, nu, counts, bias, logpost_out, grad_nu_out, grad_bias_out);
 }
 
@@ -1003,6 +1010,7 @@ int bridge_leapfrog(bridge_ctx* ctx, void* nu, void* p, const int32_t* counts, c
     if (!ctx) return BRIDGE_EINVAL;
     ctx->launches = 0;
     ctx->err.clear();
+    if (!aligned16({nu, p, counts})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
     return DISPATCH(ctx, do_leapfrog, nu, p, counts, bias, n_steps, eps, h0_out, h1_out);
 }
 
@@ -1011,6 +1019,7 @@ int bridge_debug_field(bridge_ctx* ctx, const void* nu, const int32_t* counts, c
     if (!ctx) return BRIDGE_EINVAL;
     ctx->launches = 0;
     ctx->err.clear();
+    if (!aligned16({nu, counts, out})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
     return DISPATCH(ctx, do_debug, nu, counts, bias, which, out);
 }
 

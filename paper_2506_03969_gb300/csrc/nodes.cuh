@@ -15,8 +15,7 @@ namespace bridge {
 enum NodeKind {
     NODE_ALPT_FWD = 2,   // delta0, phi (7) -> a = -D delta0 + D2 S2, theta_SC -> r2c (2)
     NODE_ALPT_ADJ = 3,   // delta0, phi (7), g_a, g_b (2) -> g_delta0, g_phi -> r2c (7)
-    NODE_GATHER = 5,     // psi (3) -> CIC gather adjoint g_psi -> r2c (3)
-    NODE_SCATTER = 6     // psi (3) -> CIC deposit into rho
+    NODE_GATHER = 5      // psi (3) -> CIC gather adjoint g_psi -> r2c (3)
 };
 
 struct NodeArgs {
@@ -24,7 +23,7 @@ struct NodeArgs {
     const void* spec_in[16];     // spectra ([kz][y][x] layout), chain stride nspec
     void* spec_out[16];          // spectra out
     const void* real_in[4];      // real fields read per voxel (g_rho for the gather), chain stride nvox
-    void* real_out[4];           // real fields written per voxel (rho for the scatter)
+    void* real_out[4];           // real fields written per voxel (unused by the current kinds)
     void* scratch;               // slabs: [grid][F][tile voxels]
     double growth, d2;
 };

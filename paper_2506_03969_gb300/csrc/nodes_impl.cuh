@@ -8,8 +8,8 @@
 // CTAs are persistent (grid = resident CTAs), so each slab is rewritten tile
 // after tile and stays in L2.
 // Nodes carry the light per-voxel stages (ALPT sources and their adjoint, CIC
-// scatter and gather); the arithmetic-heavy web stages run as separate
-// full-occupancy kernels.
+// gather); the arithmetic-heavy web stages and the CIC scatter (which needs 3D
+// blocks of particles) run as separate kernels.
 #pragma once
 
 #include "common.cuh"
@@ -28,7 +28,6 @@ template <int KIND> struct NodeShape;
 template <> struct NodeShape<NODE_ALPT_FWD> { static constexpr int IN = 7, SLAB = 7, OUT = 2; };
 template <> struct NodeShape<NODE_ALPT_ADJ> { static constexpr int IN = 9, SLAB = 9, OUT = 7; };
 template <> struct NodeShape<NODE_GATHER> { static constexpr int IN = 3, SLAB = 3, OUT = 3; };
-template <> struct NodeShape<NODE_SCATTER> { static constexpr int IN = 3, SLAB = 3, OUT = 0; };
 
 template <typename T, int N, int KIND>
 __global__ void __launch_bounds__(kNodeThreads) k_node(const NodeArgs A, int batch, long long nspec) {
@@ -87,10 +86,6 @@ __global__ void __launch_bounds__(kNodeThreads) k_node(const NodeArgs A, int bat
                 slab_f(0)[v] = out[0];
                 slab_f(1)[v] = out[1];
                 slab_f(2)[v] = out[2];
-            } else if constexpr (KIND == NODE_SCATTER) {
-                CicCorner<T> c;
-                cic_corner<T>((long long)(g - coff), N, slab_f(0)[v], slab_f(1)[v], slab_f(2)[v], c);
-                cic_deposit<T>(c, N, reinterpret_cast<T*>(A.real_out[0]) + coff);
             }
         }
         __syncthreads();
@@ -150,7 +145,6 @@ static cudaError_t node_dispatch(int batch, int sms, const NodeArgs& a, cudaStre
         case NODE_ALPT_FWD: return NodeLaunch<T, N, NODE_ALPT_FWD>::run(batch, sms, a, s, nspec, gu);
         case NODE_ALPT_ADJ: return NodeLaunch<T, N, NODE_ALPT_ADJ>::run(batch, sms, a, s, nspec, gu);
         case NODE_GATHER: return NodeLaunch<T, N, NODE_GATHER>::run(batch, sms, a, s, nspec, gu);
-        case NODE_SCATTER: return NodeLaunch<T, N, NODE_SCATTER>::run(batch, sms, a, s, nspec, gu);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -158,15 +152,13 @@ static cudaError_t node_dispatch(int batch, int sms, const NodeArgs& a, cudaStre
 template <typename T, int N> static int node_grid_max(int batch, int sms) {
     int g = NodeLaunch<T, N, NODE_ALPT_FWD>::grid(batch, sms);
     g = max(g, NodeLaunch<T, N, NODE_ALPT_ADJ>::grid(batch, sms));
-    g = max(g, NodeLaunch<T, N, NODE_GATHER>::grid(batch, sms));
-    return max(g, NodeLaunch<T, N, NODE_SCATTER>::grid(batch, sms));
+    return max(g, NodeLaunch<T, N, NODE_GATHER>::grid(batch, sms));
 }
 
 template <typename T, int N> static size_t node_scratch_max(int batch, int sms) {
     size_t m = NodeLaunch<T, N, NODE_ALPT_FWD>::scratch(batch, sms);
     m = max(m, NodeLaunch<T, N, NODE_ALPT_ADJ>::scratch(batch, sms));
-    m = max(m, NodeLaunch<T, N, NODE_GATHER>::scratch(batch, sms));
-    return max(m, NodeLaunch<T, N, NODE_SCATTER>::scratch(batch, sms));
+    return max(m, NodeLaunch<T, N, NODE_GATHER>::scratch(batch, sms));
 }
 
 }  // namespace bridge

@@ -153,9 +153,12 @@ template <typename T, int N, bool XM> struct Tile {
     }
 };
 
+#ifndef BRIDGE_YPASS_MINB
+#define BRIDGE_YPASS_MINB 3
+#endif
 // Forward (merge) column pass: out[o] = sum_{terms -> o} mult * DFT(in[src])
 template <typename T, int N, bool XM>
-__global__ void __launch_bounds__(Tile<T, N, XM>::NT, 2) k_col_fwd(const PassProgram P, const KParams kp) {
+__global__ void __launch_bounds__(Tile<T, N, XM>::NT, BRIDGE_YPASS_MINB) k_col_fwd(const PassProgram P, const KParams kp) {
     using TL = Tile<T, N, XM>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -203,7 +206,7 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, 2) k_col_fwd(const PassPro
 
 // Inverse (expand) column pass: out[dst] = IDFT(mult * in[src]) for each term.
 template <typename T, int N, bool XM>
-__global__ void __launch_bounds__(Tile<T, N, XM>::NT, 2) k_col_inv(const PassProgram P, const KParams kp) {
+__global__ void __launch_bounds__(Tile<T, N, XM>::NT, BRIDGE_YPASS_MINB) k_col_inv(const PassProgram P, const KParams kp) {
     using TL = Tile<T, N, XM>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -268,8 +271,11 @@ __device__ __forceinline__ cplx_t<T> xnode_mult(const Term& tm, int mx, int my, 
     return cmake<cplx_t<T>>(T(tm.cre) * r, T(tm.cim) * r);
 }
 
+#ifndef BRIDGE_XNODE_MINB
+#define BRIDGE_XNODE_MINB 2
+#endif
 template <typename T, int N>
-__global__ void __launch_bounds__(Tile<T, N, true>::NT, 2) k_x_node(const PassProgram P, const KParams kp) {
+__global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_node(const PassProgram P, const KParams kp) {
     using TL = Tile<T, N, true>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];

@@ -33,12 +33,21 @@ __global__ void __launch_bounds__(kPwThreads) k_counts_prep(long long nvox, cons
     const size_t off = (size_t)blockIdx.y * nvox;
     double acc[1] = {0.0};
     long long s = 0;
-    PW_LOOP(i, nvox) {
-        int v = counts[off + i];
-        if (v < 0 || v > 65535) { atomicOr(err, 1); v = 0; }
-        c16[off + i] = (uint16_t)v;
-        s += v;
+    int bad = 0;
+    // four counts per 16-byte load (nvox is a multiple of 4)
+    const int4* c4 = reinterpret_cast<const int4*>(counts + off);
+    ushort4* o4 = reinterpret_cast<ushort4*>(c16 + off);
+    PW_LOOP(i, nvox / 4) {
+        const int4 v = c4[i];
+        int q[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (q[k] < 0 || q[k] > 65535) { bad = 1; q[k] = 0; }
+            s += q[k];
+        }
+        o4[i] = make_ushort4((uint16_t)q[0], (uint16_t)q[1], (uint16_t)q[2], (uint16_t)q[3]);
     }
+    if (bad) atomicOr(err, 1);
     acc[0] = (double)s;
     write_partials<1>(acc, partial);
 }
@@ -105,30 +114,119 @@ template <typename T> __global__ void k_fill(long long count, T* p, T v) {
 // needs (d ln nbar / d rho ~ alpha / rho in nearly empty cells).  The spectra of
 // rho and delta differ only at k = 0, where every tensor operator vanishes.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kPwThreads) k_cic_scatter(int N, long long nvox, Fields16 psi3, T* delta) {
+// The deposit runs over blocks of BX x BY x BZ particles (BZ consecutive z per
+// warp, so the displacement loads are contiguous).  Each block accumulates the
+// cells [x0-H, x0+BX+H) x [y0-H, y0+BY+H) x [z0-H, z0+BZ+H) in a shared-memory
+// window; a particle whose 2x2x2 footprint leaves the window (|psi| beyond
+// about H cells) adds straight to rho.  The window is then added to rho in
+// aligned groups of four z cells (one 16-byte vector atomic for FP32, zero
+// groups skipped): several times fewer global atomics than one per corner.
+// FP32 windows hold fixed-point sums (weight * 2^40, exact integer adds) as
+// two 32-bit counters per cell, the high and low 20 bits of each term, because
+// shared-memory 32-bit integer adds run about six times faster than float or
+// 64-bit adds (measured); the pair is combined and converted to FP32 once at
+// the flush, so the deposit is at least as accurate as FP32 atomics (up to
+// 4095 terms per cell).  No FP64 arithmetic: GB300's FP64 rate is low.  FP64 windows hold doubles.  Needs BX, BY, BZ <= N;
+// windows of blocks near the periodic edges overlap, which the atomics absorb.
+template <typename T> struct CicBlock;
+template <> struct CicBlock<float> { static constexpr int BX = 8, BY = 8, H = 4; };    // 16x16x40 cells, 80 KB at BZ = 32
+template <> struct CicBlock<double> { static constexpr int BX = 8, BY = 8, H = 4; };   // 80 KB at BZ = 32
+
+// Shared-memory window of `cells` cells, 8 bytes per cell.  FP32: the term
+// w * 2^40 is split in FP32 arithmetic into its integer part above 2^20
+// (hi = floor(w 2^20)) and the next 20 bits (lo, rounded), each added to its
+// own 32-bit counter; the flush forms hi 2^-20 + lo 2^-40.
+template <typename T> struct CicWin;
+template <> struct CicWin<float> {
+    unsigned* hi;
+    unsigned* lo;
+    __device__ CicWin(unsigned char* raw, int cells)
+        : hi(reinterpret_cast<unsigned*>(raw)), lo(reinterpret_cast<unsigned*>(raw) + cells) {}
+    __device__ void zero(int i) { hi[i] = 0u; lo[i] = 0u; }
+    __device__ void add(int i, float w) {   // 0 <= w <= 1
+        const float s = w * 1048576.0f;      // 2^20, exact
+        const float h = floorf(s);
+        atomicAdd(lo + i, __float2uint_rn((s - h) * 1048576.0f));
+        atomicAdd(hi + i, (unsigned)h);
+    }
+    __device__ float get(int i) const {
+        return float(hi[i]) * 9.5367431640625e-07f + float(lo[i]) * 9.094947017729282e-13f;   // 2^-20, 2^-40
+    }
+};
+template <> struct CicWin<double> {
+    double* w;
+    __device__ CicWin(unsigned char* raw, int) : w(reinterpret_cast<double*>(raw)) {}
+    __device__ void zero(int i) { w[i] = 0.0; }
+    __device__ void add(int i, double v) { atomicAdd(w + i, v); }
+    __device__ double get(int i) const { return w[i]; }
+};
+
+__device__ __forceinline__ void cic_flush4(float* g, const CicWin<float>& W, int i) {
+    const float4 v = make_float4(W.get(i), W.get(i + 1), W.get(i + 2), W.get(i + 3));
+    if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) atomicAdd(reinterpret_cast<float4*>(g), v);
+}
+__device__ __forceinline__ void cic_flush4(double* g, const CicWin<double>& W, int i) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const double v = W.get(i + q);
+        if (v != 0.0) atomicAdd(g + q, v);
+    }
+}
+
+template <typename T, int BZ>
+__global__ void __launch_bounds__(kPwThreads) k_cic_scatter(int N, long long nvox, Fields16 psi3, T* rho) {
+    using CB = CicBlock<T>;
+    constexpr int BX = CB::BX, BY = CB::BY, H = CB::H;
+    constexpr int WX = BX + 2 * H, WY = BY + 2 * H, WZ = BZ + 2 * H, CELLS = WX * WY * WZ;
+    static_assert(WZ % 4 == 0 && H % 4 == 0, "window rows are groups of four cells");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    CicWin<T> W(smraw, CELLS);
+    const int t = threadIdx.x;
     const size_t off = (size_t)blockIdx.y * nvox;
-    const T* p0 = (const T*)psi3.p[0] + off; const T* p1 = (const T*)psi3.p[1] + off; const T* p2 = (const T*)psi3.p[2] + off;
-    T* d = delta + off;
+    const T* p0 = (const T*)psi3.p[0] + off;
+    const T* p1 = (const T*)psi3.p[1] + off;
+    const T* p2 = (const T*)psi3.p[2] + off;
+    T* r = rho + off;
     const int msk = N - 1;
-    PW_LOOP(q, nvox) {
+    const int nbz = N / BZ, nby = N / BY;
+    const int b = blockIdx.x;
+    const int x0 = (b / (nbz * nby)) * BX, y0 = ((b / nbz) % nby) * BY, z0 = (b % nbz) * BZ;
+    for (int i = t; i < CELLS; i += kPwThreads) W.zero(i);
+    __syncthreads();
+    for (int p = t; p < BX * BY * BZ; p += kPwThreads) {
+        const int z = z0 + p % BZ, y = y0 + (p / BZ) % BY, x = x0 + p / (BZ * BY);
+        const size_t q = ((size_t)x * N + y) * N + z;
         CicCorner<T> c;
-        cic_corner<T>(q, N, p0[q], p1[q], p2[q], c);
+        cic_corner<T>((long long)q, N, p0[q], p1[q], p2[q], c);
+        // window coordinates of the lower corner (unwrapped)
+        const int wx = c.i0[0] - (x0 - H), wy = c.i0[1] - (y0 - H), wz = c.i0[2] - (z0 - H);
+        const bool inside = wx >= 0 && wx + 1 < WX && wy >= 0 && wy + 1 < WY && wz >= 0 && wz + 1 < WZ;
 #pragma unroll
         for (int a = 0; a < 2; ++a) {
-            const T wx = a ? c.f[0] : T(1) - c.f[0];
-            const size_t ix = (size_t)((c.i0[0] + a) & msk) * N;
+            const T fx = a ? c.f[0] : T(1) - c.f[0];
 #pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const T wy = b ? c.f[1] : T(1) - c.f[1];
-                const size_t iy = (ix + (size_t)((c.i0[1] + b) & msk)) * N;
+            for (int bb = 0; bb < 2; ++bb) {
+                const T fxy = fx * (bb ? c.f[1] : T(1) - c.f[1]);
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                    const T wz = e ? c.f[2] : T(1) - c.f[2];
-                    atomicAdd(d + iy + ((c.i0[2] + e) & msk), wx * wy * wz);
+                    const T w = fxy * (e ? c.f[2] : T(1) - c.f[2]);
+                    if (inside)
+                        W.add(((wx + a) * WY + (wy + bb)) * WZ + wz + e, w);
+                    else
+                        atomicAdd(r + ((size_t)((c.i0[0] + a) & msk) * N + ((c.i0[1] + bb) & msk)) * N +
+                                      ((c.i0[2] + e) & msk), w);
                 }
             }
         }
+    }
+    __syncthreads();
+    // flush: groups of four z cells; (z0 - H) is a multiple of 4 and so is N
+    constexpr int G = WZ / 4;
+    for (int i = t; i < WX * WY * G; i += kPwThreads) {
+        const int g = i % G, col = i / G;
+        const int wy = col % WY, wx = col / WY;
+        const int gx = (x0 - H + wx) & msk, gy = (y0 - H + wy) & msk, gz = (z0 - H + 4 * g) & msk;
+        cic_flush4(r + ((size_t)gx * N + gy) * N + gz, W, col * WZ + 4 * g);
     }
 }
 
@@ -258,7 +356,7 @@ __global__ void __launch_bounds__(kPwThreads) k_pass_b(long long nvox, const T* 
 // requested (BIASG), the partial sums of d/d alpha_r and d/d beta_r.
 // ---------------------------------------------------------------------------
 #ifndef BRIDGE_WEBADJ_MINB
-#define BRIDGE_WEBADJ_MINB 2
+#define BRIDGE_WEBADJ_MINB 3
 #endif
 template <typename T, int NR, bool BIASG>
 __global__ void __launch_bounds__(kPwThreads, BRIDGE_WEBADJ_MINB) k_web_adj(long long nvox, Fields16 th, const T* rho,
@@ -287,7 +385,11 @@ __global__ void __launch_bounds__(kPwThreads, BRIDGE_WEBADJ_MINB) k_web_adj(long
             load6<T>(th, 0, j, a6);
             if constexpr (NR == 16) load6<T>(th, 6, j, h6);
         };
-        web_adjoint_voxel<T, NR, BIASG>(S, dl, (int)c16[j], lnC, gscale, *Bp, wp, reload, gd, gt, gh, ga, gb);
+        // a second opaque copy, so that the region table is read again here instead of
+        // the compiler keeping the 112 values of the forward phase live
+        const BiasT<T>* Bq = &B;
+        asm volatile("" : "+l"(Bq));
+        web_adjoint_voxel<T, NR, BIASG>(S, dl, (int)c16[j], lnC, gscale, *Bq, wp, reload, gd, gt, gh, ga, gb);
         ((T*)out.p[0])[j] = gd;
 #pragma unroll
         for (int q = 0; q < 6; ++q) ((T*)out.p[1 + q])[j] = gt[q];
@@ -377,34 +479,60 @@ __global__ void __launch_bounds__(1024) k_reduce(int what, int nblk, int K, cons
     ChainScalars& S = sc[chain];
     const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (k < K) {
-        double v = 0.0;
-        for (int b = lane; b < nblk; b += 32) v += partial[((size_t)chain * nblk + b) * K + k];
+        // four independent accumulators combined in a fixed order: many loads in
+        // flight, same result every run
+        const double* p = partial + (size_t)chain * nblk * K + k;
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        int b = lane;
+#pragma unroll 4
+        for (; b + 96 < nblk; b += 128) {
+            v0 += p[(size_t)b * K];
+            v1 += p[(size_t)(b + 32) * K];
+            v2 += p[(size_t)(b + 64) * K];
+            v3 += p[(size_t)(b + 96) * K];
+        }
+        for (; b < nblk; b += 32) v0 += p[(size_t)b * K];
+        double v = (v0 + v1) + (v2 + v3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) tot[k] = v;
     }
     __syncthreads();
+    // log-normal priors of the bias tables (Eq. lognormal), one region per lane of warp 0,
+    // summed in a fixed order
+    double lpr = 0.0, ga_r = 0.0, gb_r = 0.0;
+    if (what == RED_LIK || what == RED_BIASGRAD) {
+        const BiasD& Bd = bias[chain];
+        const int r = threadIdx.x;
+        if (r < n_regions && ((Bd.prior_mask >> r) & 1u)) {
+            if (what == RED_LIK)
+                lpr = lognormal_logpdf(Bd.alpha[r], Bd.mu_alpha, Bd.sigma_alpha) +
+                      lognormal_logpdf(Bd.beta[r], Bd.mu_beta, Bd.sigma_beta);
+            else {
+                ga_r = lognormal_dlogpdf(Bd.alpha[r], Bd.mu_alpha, Bd.sigma_alpha);
+                gb_r = lognormal_dlogpdf(Bd.beta[r], Bd.mu_beta, Bd.sigma_beta);
+            }
+        }
+        if (threadIdx.x < 32) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) lpr += __shfl_down_sync(0xffffffffu, lpr, o);
+        }
+        if (what == RED_BIASGRAD && r < n_regions) {
+            tot[r] += ga_r;                 // each region's own entries: no ordering question
+            tot[n_regions + r] += gb_r;
+        }
+        __syncthreads();
+    }
     if (threadIdx.x != 0) return;
-    const BiasD& Bd = bias[chain];
     if (what == RED_NTR) S.ntr = tot[0];
     else if (what == RED_SUMF) { S.sumf = tot[0]; S.lnC = log(S.ntr) - log(tot[0]); }
     else if (what == RED_P2) S.sump2 = tot[0];
     else if (what == RED_LIK) {
         S.loglik = tot[0]; S.G = tot[1]; S.sumnu2 = tot[2];
-        double lp = 0.0;
-        for (int r = 0; r < n_regions; ++r)
-            if ((Bd.prior_mask >> r) & 1u)
-                lp += lognormal_logpdf(Bd.alpha[r], Bd.mu_alpha, Bd.sigma_alpha) +
-                      lognormal_logpdf(Bd.beta[r], Bd.mu_beta, Bd.sigma_beta);
-        S.logprior = lp;
-        S.logpost = -0.5 * S.sumnu2 + S.loglik + lp;
+        S.logprior = lpr;
+        S.logpost = -0.5 * S.sumnu2 + S.loglik + lpr;
     } else if (what == RED_BIASGRAD) {
         for (int q = 0; q < K; ++q) S.gbias[q] = tot[q];
-        for (int r = 0; r < n_regions; ++r)
-            if ((Bd.prior_mask >> r) & 1u) {
-                S.gbias[r] += lognormal_dlogpdf(Bd.alpha[r], Bd.mu_alpha, Bd.sigma_alpha);
-                S.gbias[n_regions + r] += lognormal_dlogpdf(Bd.beta[r], Bd.mu_beta, Bd.sigma_beta);
-            }
     }
 }
 
@@ -432,8 +560,18 @@ template <typename T> cudaError_t launch_fill(long long count, T* p, T v, cudaSt
 }
 template <typename T>
 cudaError_t launch_cic_scatter(int n, int batch, const Fields16& psi3, T* delta, cudaStream_t s) {
-    k_cic_scatter<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(n, nvox_of(n), psi3, delta);
-    return cudaGetLastError();
+    using CB = CicBlock<T>;
+    if (n < 16) return cudaErrorInvalidValue;
+    // BZ = 32 (one warp = one z run of 32 particles), 16 on the smallest mesh
+    auto run = [&](auto kern, int bz) {
+        const size_t sm = size_t(CB::BX + 2 * CB::H) * (CB::BY + 2 * CB::H) * (bz + 2 * CB::H) * 8;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+        if (e != cudaSuccess) return e;
+        const unsigned blocks = unsigned((n / CB::BX) * (n / CB::BY) * (n / bz));
+        kern<<<dim3(blocks, batch), kPwThreads, sm, s>>>(n, nvox_of(n), psi3, delta);
+        return cudaGetLastError();
+    };
+    return n >= 32 ? run(k_cic_scatter<T, 32>, 32) : run(k_cic_scatter<T, 16>, 16);
 }
 template <typename T>
 cudaError_t launch_pass_a(int n, int batch, const Fields16& th, const T* delta, T* lnf, T* beta_i,
@@ -454,7 +592,8 @@ template <typename T>
 cudaError_t launch_web_adjoint(int n, int batch, const Fields16& th, const T* delta, const uint16_t* c16,
                                const BiasT<T>* bias, const WebParams& wp, const ChainScalars* sc,
                                const Fields16& out, double* partial, bool bias_grad, cudaStream_t s) {
-    const dim3 g(pw_blocks(n), batch);
+    // partial sums (bias gradient) only with bias_grad: that launch keeps the reduction's grid
+    const dim3 g(bias_grad ? pw_blocks(n) : pw_blocks_wide(n), batch);
     if (wp.n_regions == 16) {
         if (bias_grad) k_web_adj<T, 16, true><<<g, kPwThreads, 0, s>>>(nvox_of(n), th, delta, c16, bias, wp, sc, out, partial);
         else k_web_adj<T, 16, false><<<g, kPwThreads, 0, s>>>(nvox_of(n), th, delta, c16, bias, wp, sc, out, partial);

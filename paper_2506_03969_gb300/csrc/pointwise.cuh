@@ -15,6 +15,12 @@ inline int pw_blocks(int n) {
     long long v = (long long)n * n * n / (kPwThreads * 4);
     return int(v < 1 ? 1 : (v > 1024 ? 1024 : v));
 }
+// Kernels without partial sums run on a wider grid (at 256^3: 8192 blocks,
+// eight voxels per thread), which balances the arithmetic-heavy web adjoint.
+inline int pw_blocks_wide(int n) {
+    long long v = (long long)n * n * n / (kPwThreads * 8);
+    return int(v < 1 ? 1 : (v > 8192 ? 8192 : v));
+}
 
 // Per-chain FP64 scalars kept on the device.
 struct ChainScalars {

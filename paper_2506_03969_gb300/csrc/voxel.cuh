@@ -366,26 +366,6 @@ template <typename T> __device__ __forceinline__ void cic_corner(long long q, in
     c.i0[0] = qx + (int)fx; c.i0[1] = qy + (int)fy; c.i0[2] = qz + (int)fz;
 }
 
-// CIC deposit of one particle (unit mass) into rho (atomics, periodic).
-template <typename T> __device__ __forceinline__ void cic_deposit(const CicCorner<T>& c, int N, T* rho) {
-    const int msk = N - 1;
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        const T wx = a ? c.f[0] : T(1) - c.f[0];
-        const size_t ix = (size_t)((c.i0[0] + a) & msk) * N;
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            const T wy = b ? c.f[1] : T(1) - c.f[1];
-            const size_t iy = (ix + (size_t)((c.i0[1] + b) & msk)) * N;
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const T wz = e ? c.f[2] : T(1) - c.f[2];
-                atomicAdd(rho + iy + ((c.i0[2] + e) & msk), wx * wy * wz);
-            }
-        }
-    }
-}
-
 // CIC gather adjoint of one particle: g_psi_j = sum_corners g_rho[c] dw_c/dpsi_j.
 template <typename T> __device__ __forceinline__ void cic_gather_one(const CicCorner<T>& c, int N, const T* g, T out[3]) {
     const int msk = N - 1;

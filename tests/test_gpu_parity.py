@@ -223,6 +223,13 @@ def test_invalid_inputs_return_errors():
     with pytest.raises(pkg.BridgeError) as e:
         ctx.bridge_logpost_grad(nan_nu, c_d, [bias])
     assert e.value.status == pkg.BRIDGE_ENONFINITE
+    # a buffer that does not start on a 16-byte boundary is refused before any launch
+    raw = torch.empty(nu_d.numel() + 1, dtype=nu_d.dtype, device="cuda")
+    shifted = raw[1:]
+    shifted.copy_(nu_d.reshape(-1))
+    with pytest.raises(pkg.BridgeError) as e:
+        ctx.bridge_logpost_grad(shifted, c_d, [bias])
+    assert e.value.status == pkg.BRIDGE_EINVAL and "16-byte" in str(e.value)
 
 
 def test_full_size_256_against_oracle():
