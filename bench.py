@@ -385,21 +385,28 @@ def run_extras(pkg, synth, cfg, bias, nu32, counts, args):
     rate = torch.exp(lnnbar) * torch._standard_gamma(shape, generator=gen) / 5.0
     counts_m = torch.poisson(rate, generator=gen).clamp_(max=65535).to(torch.int32).contiguous()
     p0 = torch.tensor(synth.momentum(cfg.n, cfg.seed_momentum), dtype=torch.float64, device="cuda")
-    n64, p64 = nu_t.clone(), p0.clone()
-    h0a, h1a = c64.bridge_leapfrog(n64, p64, counts_m, [bias], 10, 0.05)
-    n32, p32 = nu_t.float(), p0.float()
-    t0 = time.perf_counter()
-    h0b, h1b = c32.bridge_leapfrog(n32, p32, counts_m, [bias], 10, 0.05)
-    torch.cuda.synchronize()
-    tl = time.perf_counter() - t0
-    out["hmc_256_10_steps"] = {"dH_fp64": h1a[0] - h0a[0], "dH_fp32": h1b[0] - h0b[0],
-                               "H0_fp64": h0a[0], "H0_fp32_minus_fp64": h0b[0] - h0a[0],
-                               "nu_rel_l2_fp32_vs_fp64": float(torch.linalg.vector_norm(n32.double() - n64) /
-                                                               torch.linalg.vector_norm(n64)),
-                               "p_rel_l2_fp32_vs_fp64": float(torch.linalg.vector_norm(p32.double() - p64) /
-                                                              torch.linalg.vector_norm(p64)),
-                               "fp32_trajectory_s": tl,
-                               "data": "gamma-Poisson mock (beta 5) of the model at nu_true, start at nu_true"}
+    hmc = {"data": "gamma-Poisson mock (beta 5) of the model at nu_true, start at nu_true, identity mass",
+           "steps": 10}
+    for eps in (0.05, 0.005, 0.0005):
+        n64, p64 = nu_t.clone(), p0.clone()
+        try:
+            h0a, h1a = c64.bridge_leapfrog(n64, p64, counts_m, [bias], 10, eps)
+            n32, p32 = nu_t.float(), p0.float()
+            t0 = time.perf_counter()
+            h0b, h1b = c32.bridge_leapfrog(n32, p32, counts_m, [bias], 10, eps)
+            torch.cuda.synchronize()
+            tl = time.perf_counter() - t0
+            hmc[f"eps_{eps:g}"] = {
+                "dH_fp64": h1a[0] - h0a[0], "dH_fp32": h1b[0] - h0b[0],
+                "H0_fp64": h0a[0], "H0_fp32_minus_fp64": h0b[0] - h0a[0],
+                "nu_rel_l2_fp32_vs_fp64": float(torch.linalg.vector_norm(n32.double() - n64) /
+                                                torch.linalg.vector_norm(n64)),
+                "p_rel_l2_fp32_vs_fp64": float(torch.linalg.vector_norm(p32.double() - p64) /
+                                               torch.linalg.vector_norm(p64)),
+                "fp32_trajectory_s": tl}
+        except pkg.BridgeError as e:   # a diverged trajectory ends with a non-finite Hamiltonian
+            hmc[f"eps_{eps:g}"] = {"error": str(e)}
+    out["hmc_256"] = hmc
     del c64
     # batched: 16 chains at 128^3 in one launch per pass
     cb = synth.config(3)
@@ -416,6 +423,27 @@ def run_extras(pkg, synth, cfg, bias, nu32, counts, args):
     t1 = timed(lambda: c1.bridge_logpost_grad(nub[0].contiguous(), cnb[0].contiguous(), [biases[0]], grad_out=g1,
                                               want_bias_grad=False), 5)
     out["single_128"] = {"evals_per_s": 1.0 / t1}
+    del ctxb, c1, nub, cnb, gb
+    # four 256^3 chains in one launch per pass
+    c4 = pkg.Context(pkg.config_from(cfg, batch=4))
+    nu4 = torch.tensor(synth.white_noise(cfg.n, cfg.seed_eval, 4), dtype=torch.float32, device="cuda")
+    cn4 = torch.tensor(synth.timing_counts(cfg.n, cfg.seed_counts, cfg.mean_tracers, batch=4), dtype=torch.int32,
+                       device="cuda")
+    g4 = torch.empty_like(nu4)
+    t4 = timed(lambda: c4.bridge_logpost_grad(nu4, cn4, [bias] * 4, grad_out=g4, want_bias_grad=False), 5)
+    out["batched_4x256"] = {"chain_evals_per_s": 4 / t4, "ms_per_batched_eval": 1e3 * t4}
+    del c4, nu4, cn4, g4
+    # the large single field: 512^3, L = 2000 Mpc/h, beta = 2, 0.05 tracers per cell
+    c5 = synth.config(4)
+    b5 = synth.default_bias(c5)
+    ctx5 = pkg.Context(pkg.config_from(c5, batch=1))
+    nu5 = torch.tensor(synth.white_noise(c5.n, c5.seed_eval), dtype=torch.float32, device="cuda")
+    cn5 = torch.tensor(synth.timing_counts(c5.n, c5.seed_counts, c5.mean_tracers, beta=2.0), dtype=torch.int32,
+                       device="cuda")
+    g5 = torch.empty_like(nu5)
+    t5 = timed(lambda: ctx5.bridge_logpost_grad(nu5, cn5, [b5], grad_out=g5, want_bias_grad=False), 3)
+    out["single_512"] = {"evals_per_s": 1.0 / t5, "ms_per_eval": 1e3 * t5,
+                         "workspace_gb": pkg.lib().bridge_workspace_bytes(pkg.config_from(c5, batch=1)) / 1e9}
     return out
 
 

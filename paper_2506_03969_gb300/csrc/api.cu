@@ -205,7 +205,7 @@ Plan make_plan(const bridge_config* c) {
     p.sc_bytes = align_up(sizeof(ChainScalars) * B);
     p.biasd_bytes = align_up(sizeof(BiasD) * B);
     p.biast_bytes = align_up(sizeof(BiasT<double>) * B);
-    p.node_bytes = align_up(size_t(80) << 20);   // fused-node slabs (the launcher keeps them below this)
+    p.node_bytes = align_up(size_t(BRIDGE_NODE_L2_MB + 8) << 20);   // fused-node slabs (the launcher keeps them below the budget)
     p.rtab_bytes = align_up(size_t(4) * (3 * (n / 2) * (n / 2) + 1) * esz);
     p.total = p.spec_bytes * p.nspec_buf + p.real_bytes * (p.nreal_buf + 1) + p.c16_bytes + p.partial_bytes +
               p.sc_bytes + p.biasd_bytes + p.biast_bytes + p.node_bytes + p.rtab_bytes + 256;

@@ -103,6 +103,17 @@ __device__ __forceinline__ void dft_dif(V* v) {
     }
 }
 
+// Asynchronous 16-byte global -> shared copies (cp.async, L2 only), grouped
+// per thread; wait_all returns when this thread's copies have landed (a
+// __syncthreads then makes every thread's copies visible to the block).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
 __host__ __device__ constexpr int bitrev(int j, int R) {
     int r = 0;

@@ -22,6 +22,7 @@ namespace bridge {
 
 constexpr int kNodeThreads = 128;
 
+
 template <typename T, int N> using NodeCfg = ZCfg<T, N, 16 / Split<N>::N2>;
 
 template <int KIND> struct NodeShape;
@@ -42,6 +43,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_node(const NodeArgs A, int bat
     const int t = threadIdx.x;
     T* slab = reinterpret_cast<T*>(A.scratch) + (size_t)blockIdx.x * SH::SLAB * TV;
     auto slab_f = [&](int f) { return slab + (size_t)f * TV; };
+    const PlainLineIO io;
     const long long items = (long long)batch * C::TILES;
     for (long long item = blockIdx.x; item < items; item += gridDim.x) {
         const int chain = (int)(item / C::TILES);
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_node(const NodeArgs A, int bat
         for (int f = 0; f < SH::IN; ++f) {
             T* s = slab_f(f);
             auto line = [&](int c) { return s + ((c / 8) * 16 + 2 * (c % 8)) * N; };
-            ztile_inv<C, decltype(line), true>(reinterpret_cast<const V*>(A.spec_in[f]) + chain * nspec, line, (long long)N, x0, y0, sm, t);
+            ztile_inv<C, decltype(line), true>(reinterpret_cast<const V*>(A.spec_in[f]) + chain * nspec, line, (long long)N, x0, y0, sm, t, io);
         }
         // (2) per-voxel stage
         const size_t coff = (size_t)chain * NVOX;
@@ -61,31 +63,31 @@ __global__ void __launch_bounds__(kNodeThreads) k_node(const NodeArgs A, int bat
             const int z = v % N, xl = (v / N) % 16, yl = v / (16 * N);
             const size_t g = coff + ((size_t)(x0 + xl) * N + (y0 + yl)) * N + z;
             if constexpr (KIND == NODE_ALPT_FWD) {
-                const T d0 = slab_f(0)[v];
+                const T d0 = io.ld(slab_f(0) + v);
                 T phi[6];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) phi[q] = slab_f(1 + q)[v];
+                for (int q = 0; q < 6; ++q) phi[q] = io.ld(slab_f(1 + q) + v);
                 T a, b;
                 alpt_sources<T>(d0, phi, T(A.growth), T(A.d2), a, b);
-                slab_f(0)[v] = a;
-                slab_f(1)[v] = b;
+                io.st(slab_f(0) + v, a);
+                io.st(slab_f(1) + v, b);
             } else if constexpr (KIND == NODE_ALPT_ADJ) {
-                const T d0 = slab_f(0)[v];
+                const T d0 = io.ld(slab_f(0) + v);
                 T phi[6], gphi[6], gd0;
 #pragma unroll
-                for (int q = 0; q < 6; ++q) phi[q] = slab_f(1 + q)[v];
-                alpt_sources_adj<T>(d0, phi, T(A.growth), T(A.d2), slab_f(7)[v], slab_f(8)[v], gd0, gphi);
-                slab_f(0)[v] = gd0;
+                for (int q = 0; q < 6; ++q) phi[q] = io.ld(slab_f(1 + q) + v);
+                alpt_sources_adj<T>(d0, phi, T(A.growth), T(A.d2), io.ld(slab_f(7) + v), io.ld(slab_f(8) + v), gd0, gphi);
+                io.st(slab_f(0) + v, gd0);
 #pragma unroll
-                for (int q = 0; q < 6; ++q) slab_f(1 + q)[v] = gphi[q];
+                for (int q = 0; q < 6; ++q) io.st(slab_f(1 + q) + v, gphi[q]);
             } else if constexpr (KIND == NODE_GATHER) {
                 CicCorner<T> c;
-                cic_corner<T>((long long)(g - coff), N, slab_f(0)[v], slab_f(1)[v], slab_f(2)[v], c);
+                cic_corner<T>((long long)(g - coff), N, io.ld(slab_f(0) + v), io.ld(slab_f(1) + v), io.ld(slab_f(2) + v), c);
                 T out[3];
                 cic_gather_one<T>(c, N, reinterpret_cast<const T*>(A.real_in[0]) + coff, out);
-                slab_f(0)[v] = out[0];
-                slab_f(1)[v] = out[1];
-                slab_f(2)[v] = out[2];
+                io.st(slab_f(0) + v, out[0]);
+                io.st(slab_f(1) + v, out[1]);
+                io.st(slab_f(2) + v, out[2]);
             }
         }
         __syncthreads();
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_node(const NodeArgs A, int bat
         for (int f = 0; f < SH::OUT; ++f) {
             T* s = slab_f(f);
             auto line = [&](int c) { return s + ((c / 8) * 16 + 2 * (c % 8)) * N; };
-            ztile_fwd<C, decltype(line), true>(line, (long long)N, reinterpret_cast<V*>(A.spec_out[f]) + chain * nspec, x0, y0, sm, t);
+            ztile_fwd<C, decltype(line), true>(line, (long long)N, reinterpret_cast<V*>(A.spec_out[f]) + chain * nspec, x0, y0, sm, t, io);
         }
     }
 }
@@ -115,7 +117,7 @@ template <typename T, int N, int KIND> struct NodeLaunch {
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kNodeThreads, smem()) != cudaSuccess) occ = 1;
         }
         const size_t per_cta = size_t(SH::SLAB) * C::TILE_VOX * sizeof(T);
-        const size_t budget = size_t(72) << 20;
+        const size_t budget = size_t(BRIDGE_NODE_L2_MB) << 20;
         int cps = occ < 1 ? 1 : occ;
         while (cps > 1 && size_t(cps) * sms * per_cta > budget) --cps;
         long long items = (long long)batch * C::TILES;

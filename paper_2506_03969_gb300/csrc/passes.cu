@@ -103,12 +103,27 @@ template <typename T, int N, bool XM> struct Tile {
         else { mx = 0; my = signed_freq(n, N); }
     }
 
-    // forward step A from global (A layout) into shared memory (twiddled)
-    __device__ static void fwdA(const V* __restrict__ src, V* sm, int t) {
+    // Staged input tile in shared memory: the tile's ROWS rows of RLEN
+    // contiguous elements (x-node: G lines of N; y pass: N rows of G columns).
+    static constexpr int ROWS = XM ? G : N, RLEN = XM ? N : G;
+    static constexpr int STAGE_ELEMS = ROWS * RLEN;
+    __device__ static int soff(int n, int g) { return XM ? g * N + n : n * G + g; }
+    // issue the asynchronous copy of the tile at src (rows N elements apart)
+    __device__ static void stage(const V* __restrict__ src, V* buf, int t) {
+        constexpr int CPR = int(RLEN * sizeof(V)) / 16;   // 16-byte chunks per row
+        for (int c = t; c < ROWS * CPR; c += NT) {
+            const int row = c / CPR, part = c % CPR;
+            cp_async16(reinterpret_cast<char*>(buf + row * RLEN) + part * 16,
+                       reinterpret_cast<const char*>(src + size_t(row) * N) + part * 16);
+        }
+        cp_async_commit();
+    }
+    // forward step A from the staged tile into shared memory (twiddled)
+    __device__ static void fwdA_staged(const V* buf, V* sm, int t) {
         const int g = a_g(t), n2 = a_n2(t);
         V v[N1];
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) v[n1] = src[goff(N2 * n1 + n2, g)];
+        for (int n1 = 0; n1 < N1; ++n1) v[n1] = buf[soff(N2 * n1 + n2, g)];
         dft_dif<N1, 1, -1>(v);
 #pragma unroll
         for (int i = 0; i < N1; ++i) {
@@ -154,33 +169,39 @@ template <typename T, int N, bool XM> struct Tile {
 };
 
 #ifndef BRIDGE_YPASS_MINB
-#define BRIDGE_YPASS_MINB 3
+#define BRIDGE_YPASS_MINB 3   // FP32; the FP64 y passes (one CTA per SM by shared memory) are unbounded
 #endif
-// Forward (merge) column pass: out[o] = sum_{terms -> o} mult * DFT(in[src])
+// Forward (merge) column pass: out[o] = sum_{terms -> o} mult * DFT(in[src]).
+// The host orders the merge terms by output; the tile of the next term is
+// copied into shared memory (cp.async) while the current one is transformed.
 template <typename T, int N, bool XM>
-__global__ void __launch_bounds__(Tile<T, N, XM>::NT, BRIDGE_YPASS_MINB) k_col_fwd(const PassProgram P, const KParams kp) {
+__global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YPASS_MINB : 1) k_col_fwd(const PassProgram P, const KParams kp) {
     using TL = Tile<T, N, XM>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* sm = reinterpret_cast<V*>(smraw);
+    V* buf = sm + TL::SM_ELEMS;
     const int t = threadIdx.x, chain = blockIdx.y;
     int kz, c0;
     TL::tile_pos(blockIdx.x, kz, c0);
     const size_t base = TL::tile_base(kz, c0);
     const int g = TL::b_g(t);
+    auto src_of = [&](int m) { return reinterpret_cast<const V*>(P.in[P.merge[m].src]) + chain * P.in_cs + base; };
+    if (P.n_merge > 0) TL::stage(src_of(0), buf, t);
+    int m = 0;
     for (int o = 0; o < P.n_out; ++o) {
         V acc[TL::J][TL::N2];
 #pragma unroll
         for (int j = 0; j < TL::J; ++j)
 #pragma unroll
             for (int i = 0; i < TL::N2; ++i) acc[j][i] = cmake<V>(T(0), T(0));
-        for (int m = 0; m < P.n_merge; ++m) {
+        for (; m < P.n_merge && P.merge[m].dst == o; ++m) {
             const Term tm = P.merge[m];
-            if (tm.dst != o) continue;
-            const V* src = reinterpret_cast<const V*>(P.in[tm.src]) + chain * P.in_cs + base;
-            __syncthreads();
-            TL::fwdA(src, sm, t);
-            __syncthreads();
+            cp_async_wait_all();
+            __syncthreads();                  // tile m visible; sm free
+            TL::fwdA_staged(buf, sm, t);
+            __syncthreads();                  // buf free, sm complete
+            if (m + 1 < P.n_merge) TL::stage(src_of(m + 1), buf, t);
             V X[TL::J][TL::N2];
             TL::fwdB(sm, t, X);
 #pragma unroll
@@ -206,7 +227,7 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, BRIDGE_YPASS_MINB) k_col_f
 
 // Inverse (expand) column pass: out[dst] = IDFT(mult * in[src]) for each term.
 template <typename T, int N, bool XM>
-__global__ void __launch_bounds__(Tile<T, N, XM>::NT, BRIDGE_YPASS_MINB) k_col_inv(const PassProgram P, const KParams kp) {
+__global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YPASS_MINB : 1) k_col_inv(const PassProgram P, const KParams kp) {
     using TL = Tile<T, N, XM>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -252,23 +273,35 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, BRIDGE_YPASS_MINB) k_col_i
 }
 
 // x node: Q = sum_merge mult * DFTx(in[src]);  out[dst] = IDFTx(mult * Q).
-// Radial factors other than 1/k^2 come from the per-context tables indexed by
-// m^2 (exact, no transcendental work in the kernel).  In FP32, 1/k^2 is the
-// correctly rounded reciprocal of the exact integer m^2 times 1/kf^2, which
-// spares a gather whose addresses differ in every lane.
+// Within a tile every thread has one (ky, kz), so each term's ky/kz powers and
+// complex coefficient fold into one per-thread constant; per element only the
+// kx power and the radial factor remain.  Radial factors other than 1/k^2 come
+// from the per-context tables indexed by m^2 (exact, no transcendental work in
+// the kernel).  In FP32, 1/k^2 is the correctly rounded reciprocal of the exact
+// integer m^2 times 1/kf^2, which spares a gather whose addresses differ in
+// every lane.
+template <typename T> struct XTerm {
+    T cr, ci;          // (cre + i cim) ky^py kz^pz
+    int px, rcode;
+};
 template <typename T>
-__device__ __forceinline__ cplx_t<T> xnode_mult(const Term& tm, int mx, int my, int mz, int n, const KParams& kp) {
+__device__ __forceinline__ XTerm<T> xterm(const Term& tm, int my, int mz, int n, const KParams& kp) {
     const T kf = T(kp.kf);
-    T r = kpow<T>(mx, tm.px, n, kf);
-    if (tm.py | tm.pz) r *= kpow<T>(my, tm.py, n, kf) * kpow<T>(mz, tm.pz, n, kf);
-    if (tm.rcode != R_ONE) {
-        const int m2 = mx * mx + my * my + mz * mz;
-        if (sizeof(T) == 4 && tm.rcode == R_INVK2)
+    const T cyz = kpow<T>(my, tm.py, n, kf) * kpow<T>(mz, tm.pz, n, kf);
+    return XTerm<T>{T(tm.cre) * cyz, T(tm.cim) * cyz, tm.px, tm.rcode};
+}
+// multiplier of element mx; m2yz = my^2 + mz^2
+template <typename T>
+__device__ __forceinline__ cplx_t<T> xmult(const XTerm<T>& x, int mx, int m2yz, int n, const KParams& kp) {
+    T r = kpow<T>(mx, x.px, n, T(kp.kf));
+    if (x.rcode != R_ONE) {
+        const int m2 = mx * mx + m2yz;
+        if (sizeof(T) == 4 && x.rcode == R_INVK2)
             r *= m2 > 0 ? T(kp.inv_kf2) * T(__frcp_rn(float(m2))) : T(0);
         else
-            r *= __ldg(reinterpret_cast<const T*>(kp.rtab) + (tm.rcode - 1) * kp.rlen + m2);
+            r *= __ldg(reinterpret_cast<const T*>(kp.rtab) + (x.rcode - 1) * kp.rlen + m2);
     }
-    return cmake<cplx_t<T>>(T(tm.cre) * r, T(tm.cim) * r);
+    return cmake<cplx_t<T>>(x.cr * r, x.ci * r);
 }
 
 #ifndef BRIDGE_XNODE_MINB
@@ -286,17 +319,24 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_n
     const size_t base = TL::tile_base(kz, c0);
     const int g = TL::b_g(t);
     const int my = signed_freq(c0 + g, N), mz = kz;
+    const int m2yz = my * my + mz * mz;
     V Q[TL::J][TL::N2];   // bit-reversed k2 order
 #pragma unroll
     for (int j = 0; j < TL::J; ++j)
 #pragma unroll
         for (int i = 0; i < TL::N2; ++i) Q[j][i] = cmake<V>(T(0), T(0));
+    // the tile of input m + 1 is copied into shared memory while input m is transformed
+    V* buf = sm + TL::SM_ELEMS;
+    auto src_of = [&](int m) { return reinterpret_cast<const V*>(P.in[P.merge[m].src]) + chain * P.in_cs + base; };
+    if (P.n_merge > 0) TL::stage(src_of(0), buf, t);
     for (int m = 0; m < P.n_merge; ++m) {
         const Term tm = P.merge[m];
-        const V* src = reinterpret_cast<const V*>(P.in[tm.src]) + chain * P.in_cs + base;
+        const XTerm<T> xt = xterm<T>(tm, my, mz, N, kp);
+        cp_async_wait_all();
         __syncthreads();
-        TL::fwdA(src, sm, t);
+        TL::fwdA_staged(buf, sm, t);
         __syncthreads();
+        if (m + 1 < P.n_merge) TL::stage(src_of(m + 1), buf, t);
         V X[TL::J][TL::N2];
         TL::fwdB(sm, t, X);
 #pragma unroll
@@ -305,12 +345,13 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_n
 #pragma unroll
             for (int i = 0; i < TL::N2; ++i) {
                 const int mx = signed_freq(k1 + TL::N1 * bitrev(i, TL::N2), N);
-                Q[j][i] = cadd(Q[j][i], cmul(xnode_mult<T>(tm, mx, my, mz, N, kp), X[j][i]));
+                Q[j][i] = cadd(Q[j][i], cmul(xmult<T>(xt, mx, m2yz, N, kp), X[j][i]));
             }
         }
     }
     for (int m = 0; m < P.n_expand; ++m) {
         const Term tm = P.expand[m];
+        const XTerm<T> xt = xterm<T>(tm, my, mz, N, kp);
         V Y[TL::J][TL::N2];   // natural k2 order
 #pragma unroll
         for (int j = 0; j < TL::J; ++j) {
@@ -318,7 +359,7 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_n
 #pragma unroll
             for (int k2 = 0; k2 < TL::N2; ++k2) {
                 const int mx = signed_freq(k1 + TL::N1 * k2, N);
-                Y[j][k2] = cmul(xnode_mult<T>(tm, mx, my, mz, N, kp), Q[j][bitrev(k2, TL::N2)]);
+                Y[j][k2] = cmul(xmult<T>(xt, mx, m2yz, N, kp), Q[j][bitrev(k2, TL::N2)]);
             }
         }
         __syncthreads();
@@ -414,16 +455,27 @@ template <typename T, int N> static cudaError_t z_inv_n(int batch, const ZProgra
 template <typename T, int N, bool XM, bool FWD>
 static cudaError_t col_n(int batch, const PassProgram& p, const KParams& kp, cudaStream_t s) {
     using TL = Tile<T, N, XM>;
-    const size_t sm = size_t(TL::SM_ELEMS) * sizeof(cplx_t<T>);
+    const size_t sm = size_t(TL::SM_ELEMS + (FWD ? TL::STAGE_ELEMS : 0)) * sizeof(cplx_t<T>);
     auto kern = FWD ? k_col_fwd<T, N, XM> : k_col_inv<T, N, XM>;
     cudaError_t e = set_smem(kern, sm);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(TL::TILES, batch), TL::NT, sm, s>>>(p, kp);
+    if (FWD) {
+        // merge terms grouped by output, in their original order within each output
+        PassProgram q = p;
+        int k = 0;
+        for (int o = 0; o < p.n_out; ++o)
+            for (int m = 0; m < p.n_merge; ++m)
+                if (p.merge[m].dst == o) q.merge[k++] = p.merge[m];
+        q.n_merge = k;
+        kern<<<dim3(TL::TILES, batch), TL::NT, sm, s>>>(q, kp);
+    } else {
+        kern<<<dim3(TL::TILES, batch), TL::NT, sm, s>>>(p, kp);
+    }
     return cudaGetLastError();
 }
 template <typename T, int N> static cudaError_t xnode_n(int batch, const PassProgram& p, const KParams& kp, cudaStream_t s) {
     using TL = Tile<T, N, true>;
-    const size_t sm = size_t(TL::SM_ELEMS) * sizeof(cplx_t<T>);
+    const size_t sm = size_t(TL::SM_ELEMS + TL::STAGE_ELEMS) * sizeof(cplx_t<T>);
     cudaError_t e = set_smem(k_x_node<T, N>, sm);
     if (e != cudaSuccess) return e;
     k_x_node<T, N><<<dim3(TL::TILES, batch), TL::NT, sm, s>>>(p, kp);

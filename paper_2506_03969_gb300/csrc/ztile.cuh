@@ -46,6 +46,12 @@ template <typename T, int N, int GY_> struct ZCfg {
     }
 };
 
+// Real-line accesses (a policy hook: the fused nodes and the passes use plain
+// loads and stores; an L2 evict-last variant measured no difference).
+struct PlainLineIO {
+    template <typename T> __device__ __forceinline__ T ld(const T* p) const { return *p; }
+    template <typename T> __device__ __forceinline__ void st(T* p, T v) const { *p = v; }
+};
 // 16/32-byte spectrum accesses; STREAM marks data touched once (evict-first in L2).
 template <bool STREAM, typename V4> __device__ __forceinline__ V4 zld4(const V4* p) {
     if constexpr (STREAM && std::is_same<V4, float4>::value) return __ldcs(p);
@@ -59,9 +65,9 @@ template <bool STREAM, typename V4> __device__ __forceinline__ void zst4(V4* p, 
 // Forward: real lines -> spectrum.  line(c) returns the pointer of real line
 // a of complex line c; line b is at line(c) + bstride.  Must be called by all
 // threads t < C::NT of the block (it synchronises with __syncthreads).
-template <typename C, typename LineFn, bool STREAM = false>
+template <typename C, typename LineFn, bool STREAM = false, typename IO = PlainLineIO>
 __device__ __forceinline__ void ztile_fwd(LineFn line, long long bstride, typename C::V* __restrict__ spec,
-                                          int x0, int y0, typename C::V* sm, int t) {
+                                          int x0, int y0, typename C::V* sm, int t, const IO& io = IO()) {
     using V = typename C::V;
     using T = decltype(V{}.x);
     using V4 = typename C::V4;
@@ -72,7 +78,7 @@ __device__ __forceinline__ void ztile_fwd(LineFn line, long long bstride, typena
         const T* lb = la + bstride;
         V v[C::N1];
 #pragma unroll
-        for (int n1 = 0; n1 < C::N1; ++n1) v[n1] = cmake<V>(la[C::N2 * n1 + n2], lb[C::N2 * n1 + n2]);
+        for (int n1 = 0; n1 < C::N1; ++n1) v[n1] = cmake<V>(io.ld(la + C::N2 * n1 + n2), io.ld(lb + C::N2 * n1 + n2));
         dft_dif<C::N1, 1, -1>(v);
 #pragma unroll
         for (int i = 0; i < C::N1; ++i) {
@@ -119,9 +125,9 @@ __device__ __forceinline__ void ztile_fwd(LineFn line, long long bstride, typena
 }
 
 // Inverse: spectrum -> real lines (unnormalised).  Same calling rules.
-template <typename C, typename LineFn, bool STREAM = false>
+template <typename C, typename LineFn, bool STREAM = false, typename IO = PlainLineIO>
 __device__ __forceinline__ void ztile_inv(const typename C::V* __restrict__ spec, LineFn line, long long bstride,
-                                          int x0, int y0, typename C::V* sm, int t) {
+                                          int x0, int y0, typename C::V* sm, int t, const IO& io = IO()) {
     using V = typename C::V;
     using T = decltype(V{}.x);
     using V4 = typename C::V4;
@@ -173,8 +179,8 @@ __device__ __forceinline__ void ztile_inv(const typename C::V* __restrict__ spec
 #pragma unroll
         for (int i = 0; i < C::N1; ++i) {
             const int pos = n2 + C::N2 * bitrev(i, C::N1);
-            la[pos] = v[i].x;
-            lb[pos] = v[i].y;
+            io.st(la + pos, v[i].x);
+            io.st(lb + pos, v[i].y);
         }
     }
     __syncthreads();
