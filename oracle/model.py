@@ -257,6 +257,16 @@ def nb_logpmf(n: torch.Tensor, nbar: torch.Tensor, beta: torch.Tensor) -> torch.
             + beta * torch.log(beta / (beta + nbar)) + n * torch.log(nbar / (beta + nbar)))
 
 
+def nb_logpmf_ln(n: torch.Tensor, ln_nbar: torch.Tensor, beta: torch.Tensor) -> torch.Tensor:
+    """The same log pmf with the mean given by its logarithm (Sect. 2.6, Eq. log_likelihood in
+    log space): n (ln nbar - ln(beta + nbar)) - beta log1p(nbar / beta), so that a mean that
+    underflows to 0 (the cut-offs of Eq. local_bias in empty cells) gives the limit log P(0) = 0
+    instead of 0 * log 0."""
+    nbar = torch.exp(ln_nbar)
+    return (torch.lgamma(n + beta) - torch.lgamma(beta) - torch.lgamma(n + 1.0)
+            - beta * torch.log1p(nbar / beta) + n * (ln_nbar - torch.log(beta + nbar)))
+
+
 def lognormal_logpdf(b: torch.Tensor, mu: float, sigma: float) -> torch.Tensor:
     lb = torch.log(b)
     return -lb - math.log(sigma * math.sqrt(2.0 * math.pi)) - (lb - mu) ** 2 / (2.0 * sigma ** 2)
@@ -314,7 +324,7 @@ def log_posterior(nu: torch.Tensor, counts: torch.Tensor, cfg, bias, tables=None
     tables = tables if tables is not None else bias_tables(bias)
     fw = forward(nu, cfg, tables, counts=counts, keep=keep)
     n = counts.to(DT)
-    loglik = nb_logpmf(n, torch.exp(fw["ln_nbar"]), fw["beta"]).sum()
+    loglik = nb_logpmf_ln(n, fw["ln_nbar"], fw["beta"]).sum()
     lp = -0.5 * (nu ** 2).sum() + loglik + log_prior_bias(tables, bias)
     if keep:
         fw["loglik"] = loglik

@@ -409,6 +409,23 @@ def test_nb_matches_scipy_and_poisson_limit():
     np.testing.assert_allclose(got_p, stats.poisson.logpmf(n, nbar), rtol=1e-6, atol=1e-6)
 
 
+
+def test_nb_log_space_form_matches_and_handles_underflow():
+    """The log-space form equals the library NB where the mean is representable, and reaches the
+    exact limit log P(n=0) = 0 (with zero derivative) when the mean underflows to 0."""
+    rng = np.random.default_rng(7)
+    n = rng.integers(0, 12, 300).astype(float)
+    nbar = np.exp(rng.uniform(-6, 3, 300))
+    beta = rng.uniform(0.5, 8.0, 300)
+    got = model.nb_logpmf_ln(torch.tensor(n), torch.tensor(np.log(nbar)), torch.tensor(beta)).numpy()
+    ref = stats.nbinom.logpmf(n, beta, beta / (beta + nbar))
+    assert np.max(np.abs(got - ref)) < 1e-10
+    ln_nbar = torch.tensor([-2.0e6, -800.0], dtype=torch.float64, requires_grad=True)
+    lp = model.nb_logpmf_ln(torch.zeros(2, dtype=torch.float64), ln_nbar, torch.tensor([1.5, 4.0], dtype=torch.float64))
+    lp.sum().backward()
+    assert torch.all(torch.isfinite(lp)) and float(lp.abs().max()) == 0.0
+    assert float(ln_nbar.grad.abs().max()) < 1e-300
+
 def test_lognormal_prior_matches_scipy():
     b = np.array([0.3, 1.0, 1.3, 8.0, 11.0])
     for mu, s in ((0.27, 0.30), (2.12, 0.20)):
