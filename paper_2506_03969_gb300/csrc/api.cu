@@ -538,8 +538,11 @@ template <typename T> int upload_bias(bridge_ctx* ctx, const bridge_bias* bias) 
             d.beta[r] = on ? bias[c].beta[r] : 1.0;
             t.pk[r][BP_A] = T(d.a[r]); t.pk[r][BP_ALPHA] = T(d.alpha[r]); t.pk[r][BP_RHO] = T(d.rho[r]);
             t.pk[r][BP_EPS] = T(d.eps[r]); t.pk[r][BP_RHOP] = T(d.rhop[r]); t.pk[r][BP_EPSP] = T(d.epsp[r]);
-            t.pk[r][BP_BETA] = T(d.beta[r]); t.pk[r][7] = T(0);
+            t.pk[r][BP_BETA] = T(d.beta[r]); t.pk[r][BP_FLAGS] = T(0);
         }
+        // flag in slot 7 of region 0: some region of this chain has a second cut-off (rho' > 0)
+        for (int r = 0; r < ctx->nr; ++r)
+            if (d.rhop[r] > 0.0) t.pk[0][BP_FLAGS] = T(1);
         d.prior_mask = bias[c].prior_mask;
         d.mu_alpha = bias[c].mu_alpha; d.sigma_alpha = bias[c].sigma_alpha;
         d.mu_beta = bias[c].mu_beta; d.sigma_beta = bias[c].sigma_beta;

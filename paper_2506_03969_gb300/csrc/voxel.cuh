@@ -50,7 +50,7 @@ template <typename T> __device__ __forceinline__ void eig3(const T a[6], Eig3<T>
     const T p = v_sqrt(p2);
     const T det = b[0] * (b[3] * b[5] - b[4] * b[4]) - b[1] * (b[1] * b[5] - b[4] * b[2]) +
                   b[2] * (b[1] * b[4] - b[3] * b[2]);
-    T r = det / (T(2) * p2 * p);
+    T r = v_fdiv(det, T(2) * p2 * p);
     r = r < T(-1) ? T(-1) : (r > T(1) ? T(1) : r);
     // phi = acos(r)/3 in [0, pi/3], evaluated as sin/cos of pi * (phi / pi)
     const T phi_pi = v_acos(r) * T(0.10610329539459689051);   // 1 / (3 pi)
@@ -79,12 +79,14 @@ template <typename T> __device__ __forceinline__ void memberships(const T lam[3]
 }
 
 // Bias table of one chain (precision T), Eq. local_bias + NB beta, stored per
-// region as (a, alpha, rho, eps, rhop, epsp, beta, 0) so that one region is two
-// 16-byte (FP32) shared-memory loads.
+// region as (a, alpha, rho, eps, rhop, epsp, beta, flags) so that one region is
+// two 16-byte (FP32) shared-memory loads.  flags of region 0: 1 if any region
+// has a second cut-off (rho' > 0), else 0 (then rho', eps' and their
+// derivatives are skipped: they would only add zeros).
 template <typename T> struct __align__(16) BiasT {
     T pk[16][8];
 };
-enum { BP_A = 0, BP_ALPHA = 1, BP_RHO = 2, BP_EPS = 3, BP_RHOP = 4, BP_EPSP = 5, BP_BETA = 6 };
+enum { BP_A = 0, BP_ALPHA = 1, BP_RHO = 2, BP_EPS = 3, BP_RHOP = 4, BP_EPSP = 5, BP_BETA = 6, BP_FLAGS = 7 };
 
 // The 7 parameters of region r (vector loads from shared memory).
 __device__ __forceinline__ void region_params(const BiasT<float>& B, int r, float e[8]) {
@@ -187,14 +189,14 @@ __device__ __forceinline__ void eig_adjoint(const T a[6], const Eig3<T>& e, T g1
         b2[4] = b[1] * b[2] + b[3] * b[4] + b[4] * b[5];
         b2[5] = b[2] * b[2] + b[4] * b[4] + b[5] * b[5];
         if (c1 != T(0)) {
-            const T s = c1 / ((mu1 - mu2) * (mu1 - mu3));
+            const T s = v_fdiv(c1, (mu1 - mu2) * (mu1 - mu3));
             const T lin = -(mu2 + mu3), cst = mu2 * mu3;
 #pragma unroll
             for (int q = 0; q < 6; ++q) G[q] += s * (b2[q] + lin * b[q]);
             G[0] += s * cst; G[3] += s * cst; G[5] += s * cst;
         }
         if (c3 != T(0)) {
-            const T s = c3 / ((mu3 - mu1) * (mu3 - mu2));
+            const T s = v_fdiv(c3, (mu3 - mu1) * (mu3 - mu2));
             const T lin = -(mu1 + mu2), cst = mu1 * mu2;
 #pragma unroll
             for (int q = 0; q < 6; ++q) G[q] += s * (b2[q] + lin * b[q]);
@@ -243,6 +245,7 @@ __device__ __forceinline__ void web_eval(const T a6[6], const T h6[6], T rho_mas
     VoxParams<T>& q = S.q;
     q.a = q.alpha = q.rho = q.eps = q.rhop = q.epsp = q.beta = T(0);
     constexpr int NK = NR == 16 ? 4 : 1;
+    const bool cut2 = B.pk[0][BP_FLAGS] != T(0);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -252,7 +255,8 @@ __device__ __forceinline__ void web_eval(const T a6[6], const T h6[6], T rho_mas
             T e[8];
             region_params(B, r, e);
             q.a += e[BP_A] * w; q.alpha += e[BP_ALPHA] * w; q.rho += e[BP_RHO] * w; q.eps += e[BP_EPS] * w;
-            q.rhop += e[BP_RHOP] * w; q.epsp += e[BP_EPSP] * w; q.beta += e[BP_BETA] * w;
+            q.beta += e[BP_BETA] * w;
+            if (cut2) { q.rhop += e[BP_RHOP] * w; q.epsp += e[BP_EPSP] * w; }
         }
     log_f<T>(rho_mass, T(wp.rho_floor), S.q, S.lf);
 }
@@ -285,6 +289,7 @@ __device__ __forceinline__ void web_adjoint_voxel(const WebState<T, NR>& S, T rh
     gd = S.lf.floored ? T(0) : v_fdiv(glnf * (S.q.alpha - S.q.eps * S.lf.t1 + S.q.epsp * S.lf.t2), rho_mass);
     T gpphi[4] = {T(0), T(0), T(0), T(0)}, gpdel[4] = {T(0), T(0), T(0), T(0)};
     constexpr int NK = NR == 16 ? 4 : 1;
+    const bool cut2 = B.pk[0][BP_FLAGS] != T(0);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -292,8 +297,8 @@ __device__ __forceinline__ void web_adjoint_voxel(const WebState<T, NR>& S, T rh
             const int r = NK * a + b;
             T e[8];
             region_params(B, r, e);
-            const T gw = g_a * e[BP_A] + g_al * e[BP_ALPHA] + g_rho * e[BP_RHO] + g_eps * e[BP_EPS] +
-                         g_rhop * e[BP_RHOP] + g_epsp * e[BP_EPSP] + gbeta * e[BP_BETA];
+            T gw = g_a * e[BP_A] + g_al * e[BP_ALPHA] + g_rho * e[BP_RHO] + g_eps * e[BP_EPS] + gbeta * e[BP_BETA];
+            if (cut2) gw += g_rhop * e[BP_RHOP] + g_epsp * e[BP_EPSP];
             if constexpr (NR == 16) {
                 gpphi[a] += gw * S.pdel[b];
                 gpdel[b] += gw * S.pphi[a];

@@ -143,6 +143,36 @@ def test_forward_fields_and_gradient(name, precision):
     ctx.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_second_cutoff_against_oracle(precision):
+    """Eq. local_bias with the second cut-off switched on (rho' > 0 in every region; Table 3 has
+    rho' = 0, so the default workloads never exercise it).  Evaluated at the field the mock
+    counts were drawn from: away from it the cut-off sends nbar to 0 in nearly empty cells that
+    hold counts, and the log posterior is -inf for the oracle and the GPU alike."""
+    cfg = synth.Config("32^3 cut2", 32, 300.0, n_regions=16, mean_tracers=0.5, seed_truth=1501,
+                       seed_counts=1502, seed_eval=1503)
+    bias = synth.default_bias(cfg).copy()
+    bias.rhop = [0.2] * 16
+    bias.epsp = [1.2] * 16
+    nu_t = synth.white_noise(cfg.n, cfg.seed_truth)
+    counts = mock.mock_counts(nu_t, cfg, bias, cfg.seed_counts)
+    nu = nu_t
+    f, lp_o, g_o, gbias_o, cond = oracle_ref("32_cut2", cfg, bias, nu, counts)
+    prec = pkg.BRIDGE_FP64 if precision == "fp64" else pkg.BRIDGE_FP32
+    ftol, ltol = (FP64_FIELD, FP64_LP) if precision == "fp64" else (FP32_FIELD, FP32_LP)
+    gtol = grad_tol(precision, cond)
+    ctx, nu_d, c_d = run_gpu(cfg, bias, nu, counts, prec)
+    _fields_check(ctx, nu_d, c_d, bias, f, ftol)
+    lp, g, gb = ctx.bridge_logpost_grad(nu_d, c_d, [bias])
+    e_lp = abs(lp[0] - lp_o) / abs(lp_o)
+    e_g = rel_l2(g.double().cpu().numpy().reshape(g_o.shape), g_o)
+    e_b = np.max(np.abs(gb[0] - gbias_o)) / np.max(np.abs(gbias_o))
+    print(f"cut2 {precision}: logpost rel {e_lp:.2e} grad rel L2 {e_g:.2e} (tol {gtol:.1e}) bias grad rel {e_b:.2e}")
+    assert e_lp <= ltol and e_g <= gtol
+    assert e_b <= max(gtol, FP32_GRAD if precision == "fp32" else FP64_GRAD)
+    ctx.close()
+
+
 def test_batched_chains_match_single_and_oracle():
     cfgs = [case(32, 300.0, 4, 1001 + 10 * b) for b in range(3)]
     biases = synth.perturbed_biases(cfgs[0][1], 3, 6001)
