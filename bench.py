@@ -253,6 +253,16 @@ def run_ours(args):
     grad = torch.empty_like(nu)
     stream = ctx.stream
 
+    # launch shapes picked on this problem before the warm-up (outside every timed region)
+    tune = None
+    if not args.no_autotune:
+        t_tune = time.perf_counter()
+        ch = ctx.bridge_autotune(nu, counts, [bias])
+        torch.cuda.synchronize()
+        tune = {"node_alpt_cps": ch[0], "node_alpt_adj_cps": ch[1], "node_cic_gather_cps": ch[2],
+                "web_bias_adj_blocks": ch[3], "note": "0 = built-in choice",
+                "seconds": round(time.perf_counter() - t_tune, 2)}
+
     for _ in range(args.warmup):
         ctx.bridge_logpost_grad(nu, counts, [bias], grad_out=grad, want_bias_grad=False)
     launches_per_step = ctx.launches()
@@ -338,6 +348,7 @@ def run_ours(args):
             "clocks": clocks,
             "cpu_baseline": cpu,
             "logpost": float(lp[0]),
+            "autotune": tune,
             "extras": extras,
         }
         print(json.dumps(line))
@@ -454,6 +465,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=60.0, help="seconds for the oracle sample")
     args = ap.parse_args()

@@ -204,6 +204,23 @@ typedef struct {
  * returns the number written, or a negative BRIDGE_* status. */
 int bridge_profile_read(bridge_ctx* ctx, bridge_profile_row* rows, int max_rows);
 
+/* Launch-shape autotuner (no counterpart in the paper; a GB300 launch choice).
+ * Times whole gradient evaluations of (nu, counts, bias) -- same arguments and
+ * layout as bridge_logpost_grad, device buffers, 16-byte aligned -- and picks
+ * for this context: CTAs per SM of the three fused real-space nodes (ALPT,
+ * ALPT adjoint, CIC gather) among {built-in, 1..6, 8}, clamped to the
+ * occupancy limit and to the context's node scratch, and thread blocks per
+ * chain of the web/bias adjoint.  The tuned kernels compute the same values
+ * under every choice (each tile or voxel is handled whole by one thread block);
+ * only the time differs.  About 30 evaluations of the problem; the gradient scratch
+ * of the context is overwritten and the captured CUDA graphs are dropped (the
+ * next call re-captures them).  choices_out (host, 4 int32, may be NULL)
+ * receives the choices, 0 meaning the built-in one.  Errors: EINVAL (NULL
+ * context, buffers, alignment), ECUDA; on error every choice returns to the
+ * built-in one. */
+int bridge_autotune(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
+                    int32_t* choices_out);
+
 /* Number of kernel launches the most recent call on this context issued. */
 int64_t bridge_last_launch_count(const bridge_ctx* ctx);
 

@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
     L.bridge_profile_enable.argtypes = [vp, ctypes.c_int]; L.bridge_profile_enable.restype = ctypes.c_int
     L.bridge_profile_read.argtypes = [vp, ctypes.POINTER(bridge_profile_row), ctypes.c_int]
     L.bridge_profile_read.restype = ctypes.c_int
+    L.bridge_autotune.argtypes = [vp, vp, i32p, bp, i32p]; L.bridge_autotune.restype = ctypes.c_int
     L.bridge_delta0_noalloc.argtypes = [cp, vp, vp, vp]; L.bridge_delta0_noalloc.restype = ctypes.c_int
     L.bridge_last_error.argtypes = [vp]; L.bridge_last_error.restype = ctypes.c_char_p
     L.bridge_status_string.argtypes = [ctypes.c_int]; L.bridge_status_string.restype = ctypes.c_char_p
@@ -252,6 +253,16 @@ class Context:
                                           ctypes.c_void_p(_ptr(counts)), bias_array(biases), int(n_steps), float(eps),
                                           h0, h1))
         return np.array(h0[:]), np.array(h1[:])
+
+    def bridge_autotune(self, nu, counts, biases):
+        """Pick launch shapes for this context by timing evaluations of this problem.
+        Returns [ALPT node, ALPT-adjoint node, gather node CTAs per SM, web-adjoint blocks per chain]
+        (0 = built-in choice)."""
+        self._field(nu, "nu"); self._counts(counts)
+        ch = (ctypes.c_int32 * 4)()
+        self._check(lib().bridge_autotune(self.handle, ctypes.c_void_p(_ptr(nu)), ctypes.c_void_p(_ptr(counts)),
+                                          bias_array(biases), ctypes.cast(ch, ctypes.c_void_p)))
+        return [int(v) for v in ch]
 
     def bridge_debug_field(self, nu, counts, biases, which: int):
         torch = self.torch

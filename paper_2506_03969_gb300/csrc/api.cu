@@ -2,6 +2,7 @@
 // forward model and of its adjoint, and the leapfrog driver.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <initializer_list>
 #include <string>
@@ -63,6 +64,10 @@ struct bridge_ctx {
     int* errflag = nullptr;
     void* grad_tmp = nullptr;   // gradient scratch for leapfrog
     void* node_scratch = nullptr;  // per-CTA slabs of the fused nodes
+    size_t node_cap = 0;           // bytes of node_scratch
+    // launch choices (bridge_autotune; 0 = built-in): CTAs per SM of the ALPT,
+    // ALPT-adjoint and gather nodes, blocks per chain of the web adjoint
+    int tune[4] = {0, 0, 0, 0};
     void* rtab = nullptr;          // radial k-space factor tables (see KParams)
     // host e2e buffers
     void* h_nu = nullptr;
@@ -291,6 +296,8 @@ template <typename T> int y_identity(bridge_ctx* ctx, int first, int count, bool
 // Fused node launch: fills the common arguments and reports the grid.
 template <typename T> int node(bridge_ctx* ctx, NodeArgs& na, const char* name, double bytes, int* grid_used) {
     na.scratch = ctx->node_scratch;
+    na.scratch_bytes = ctx->node_cap;
+    na.cps = na.kind == NODE_ALPT_FWD ? ctx->tune[0] : na.kind == NODE_ALPT_ADJ ? ctx->tune[1] : ctx->tune[2];
     na.growth = ctx->cfg.growth_d;
     na.d2 = ctx->cfg.d2_over_d2 * ctx->cfg.growth_d * ctx->cfg.growth_d;
     int g = 0;
@@ -416,7 +423,7 @@ template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad, boo
     // web + bias + NB adjoint: g_rho (direct), g_T, g_H in real space, then r2c
     CKL("web_bias_adj", (2 * nth + 2) * rby<T>(ctx) + c16b(ctx), launch_web_adjoint<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 12), RB<T>(ctx, RB_DELTA), ctx->c16,
                              reinterpret_cast<const BiasT<T>*>(ctx->biast), ctx->wp, ctx->sc,
-                             fields(ctx, RB_SCR, 1 + nth), ctx->partial, bias_grad, ctx->stream));
+                             fields(ctx, RB_SCR, 1 + nth), ctx->partial, bias_grad, ctx->stream, ctx->tune[3]));
     if (bias_grad)
         CKL("reduce", 0.0, launch_reduce(RED_BIASGRAD, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
     RUN(z_fwd<T>(ctx, creal(ctx, RB_SCR, 1 + nth), mspec<T>(ctx, SP_SCR, 1 + nth)));
@@ -806,6 +813,84 @@ double sigma2_unit(double R, double ns, double kc, double pw) {
     return s * h / 3.0 / (2.0 * kPi * kPi);
 }
 
+// Sum of the CUDA-event times of one kernel class in the current profile.
+int prof_class_ms(bridge_ctx* ctx, const char* name, double* ms_out) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    double tot = 0.0;
+    for (const auto& r : ctx->prof_recs) {
+        if (std::strcmp(r.name, name) != 0) continue;
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        tot += ms;
+    }
+    *ms_out = tot;
+    return BRIDGE_OK;
+}
+
+// Captured graphs hold the launch shapes of their capture: drop them when those change.
+void drop_graphs(bridge_ctx* ctx) {
+    if (ctx->eexec) { cudaGraphExecDestroy(ctx->eexec); ctx->eexec = nullptr; }
+    if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+    for (auto& k : ctx->ekey) k = nullptr;
+    for (auto& k : ctx->gkey) k = nullptr;
+}
+
+// Launch-shape search on the caller's own problem: for each tuned kernel class
+// in turn, every candidate runs three whole gradient evaluations with per-launch
+// events and scores the best of the last two; the others keep their current
+// choice.  The tuned kernels compute the same values under every candidate
+// (each tile or voxel is handled whole by one thread block, no cross-block
+// sums), so only the time differs.
+template <typename T> int do_autotune(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
+                                      int32_t* choices) {
+    if (!nu || !counts) return fail(ctx, BRIDGE_EINVAL, "nu and counts are required");
+    RUN(upload_bias<T>(ctx, bias));
+    const T* nuT = reinterpret_cast<const T*>(nu);
+    T* g = reinterpret_cast<T*>(ctx->grad_tmp);
+    const bool prof0 = ctx->prof;
+    drop_graphs(ctx);
+    const char* cls[4] = {"node_alpt", "node_alpt_adj", "node_cic_gather", "web_bias_adj"};
+    const int wide = pw_blocks_wide(ctx->n);
+    std::vector<int> cand[4];
+    for (int k = 0; k < 3; ++k) cand[k] = {0, 1, 2, 3, 4, 5, 6, 8};
+    cand[3] = {0, pw_blocks(ctx->n), std::max(1, wide / 4), std::max(1, wide / 2), 2 * wide};
+    int st = BRIDGE_OK;
+    for (int k = 0; k < 4 && st == BRIDGE_OK; ++k) {
+        double best = 1e300;
+        int best_c = ctx->tune[k];
+        std::vector<int> seen;
+        for (int c : cand[k]) {
+            if (std::find(seen.begin(), seen.end(), c) != seen.end()) continue;
+            seen.push_back(c);
+            ctx->tune[k] = c;
+            double t = 1e300;
+            for (int rep = 0; rep < 3 && st == BRIDGE_OK; ++rep) {
+                ctx->prof = true;
+                ctx->prof_recs.clear();
+                ctx->prof_used = 0;
+                st = eval_body<T>(ctx, nuT, counts, g, false);
+                double ms = 0.0;
+                if (st == BRIDGE_OK) st = prof_class_ms(ctx, cls[k], &ms);
+                if (rep > 0) t = std::min(t, ms);
+            }
+            if (st != BRIDGE_OK) break;
+            if (t < best) { best = t; best_c = c; }
+        }
+        ctx->tune[k] = best_c;
+    }
+    ctx->prof = prof0;
+    ctx->prof_recs.clear();
+    ctx->prof_used = 0;
+    if (st == BRIDGE_OK) st = finish(ctx);
+    if (st != BRIDGE_OK) {
+        for (auto& v : ctx->tune) v = 0;
+        return st;
+    }
+    if (choices)
+        for (int k = 0; k < 4; ++k) choices[k] = ctx->tune[k];
+    return BRIDGE_OK;
+}
+
 }  // namespace
 
 #define DISPATCH(ctx, fn, ...) \
@@ -910,6 +995,7 @@ int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
     ctx->biasd = reinterpret_cast<BiasD*>(w); w += pl.biasd_bytes;
     ctx->biast = w; w += pl.biast_bytes;
     ctx->node_scratch = w; w += pl.node_bytes;
+    ctx->node_cap = pl.node_bytes;
     ctx->rtab = w; w += pl.rtab_bytes;
     {
         const int rlen = 3 * (cfg->n / 2) * (cfg->n / 2) + 1;
@@ -1024,6 +1110,14 @@ int bridge_debug_field(bridge_ctx* ctx, const void* nu, const int32_t* counts, c
     ctx->err.clear();
     if (!aligned16({nu, counts, out})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
     return DISPATCH(ctx, do_debug, nu, counts, bias, which, out);
+}
+
+int bridge_autotune(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
+                    int32_t* choices_out) {
+    if (!ctx) return BRIDGE_EINVAL;
+    ctx->err.clear();
+    if (!aligned16({nu, counts})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
+    return DISPATCH(ctx, do_autotune, nu, counts, bias, choices_out);
 }
 
 int64_t bridge_last_launch_count(const bridge_ctx* ctx) { return ctx ? ctx->launches : 0; }

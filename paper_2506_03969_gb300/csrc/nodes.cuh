@@ -29,6 +29,8 @@ struct NodeArgs {
     const void* real_in[4];      // real fields read per voxel (g_rho for the gather), chain stride nvox
     void* real_out[4];           // real fields written per voxel (unused by the current kinds)
     void* scratch;               // slabs: [grid][F][tile voxels]
+    size_t scratch_bytes;        // size of scratch; the grid is capped so that all slabs fit (0: no cap)
+    int cps;                     // CTAs per SM (0: built-in choice; clamped to the occupancy limit)
     double growth, d2;
 };
 

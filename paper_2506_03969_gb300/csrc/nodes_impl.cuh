@@ -108,8 +108,10 @@ template <typename T, int N, int KIND> struct NodeLaunch {
     using C = NodeCfg<T, N>;
     using SH = NodeShape<KIND>;
     static size_t smem() { return size_t(C::SM_ELEMS) * sizeof(cplx_t<T>); }
-    static int grid(int batch, int sms) {
-        // resident CTAs, bounded so that all slabs together stay well below the 129 MB L2
+    static int grid(int batch, int sms, int cps_override = 0, size_t cap = 0) {
+        // resident CTAs, bounded so that all slabs together stay well below the
+        // 129 MB L2 (built-in choice) or as requested, within occupancy and the
+        // scratch the caller owns
         static int occ = -1;
         if (occ < 0) {
             auto kern = k_node<T, N, KIND>;
@@ -119,9 +121,12 @@ template <typename T, int N, int KIND> struct NodeLaunch {
         const size_t per_cta = size_t(SH::SLAB) * C::TILE_VOX * sizeof(T);
         const size_t budget = size_t(BRIDGE_NODE_L2_MB) << 20;
         int cps = occ < 1 ? 1 : occ;
-        while (cps > 1 && size_t(cps) * sms * per_cta > budget) --cps;
+        if (cps_override > 0) cps = min(cps_override, cps);
+        else while (cps > 1 && size_t(cps) * sms * per_cta > budget) --cps;
         long long items = (long long)batch * C::TILES;
         long long g = (long long)cps * sms;
+        if (cap > 0) g = min(g, (long long)(cap / per_cta));
+        if (g < 1) g = 1;
         return int(g < items ? g : items);
     }
     static cudaError_t run(int batch, int sms, const NodeArgs& a, cudaStream_t s, long long nspec, int* gu) {
@@ -132,7 +137,9 @@ template <typename T, int N, int KIND> struct NodeLaunch {
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        const int g = grid(batch, sms);
+        const int g = grid(batch, sms, a.cps, a.scratch_bytes);
+        if (a.scratch_bytes > 0 && size_t(g) * SH::SLAB * C::TILE_VOX * sizeof(T) > a.scratch_bytes)
+            return cudaErrorInvalidValue;   // not even one slab fits
         if (gu) *gu = g;
         kern<<<g, kNodeThreads, smem(), s>>>(a, batch, nspec);
         return cudaGetLastError();

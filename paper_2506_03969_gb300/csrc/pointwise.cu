@@ -591,9 +591,10 @@ cudaError_t launch_pass_b(int n, int batch, const T* lnf, const T* beta_i, const
 template <typename T>
 cudaError_t launch_web_adjoint(int n, int batch, const Fields16& th, const T* delta, const uint16_t* c16,
                                const BiasT<T>* bias, const WebParams& wp, const ChainScalars* sc,
-                               const Fields16& out, double* partial, bool bias_grad, cudaStream_t s) {
-    // partial sums (bias gradient) only with bias_grad: that launch keeps the reduction's grid
-    const dim3 g(bias_grad ? pw_blocks(n) : pw_blocks_wide(n), batch);
+                               const Fields16& out, double* partial, bool bias_grad, cudaStream_t s, int blocks) {
+    // partial sums (bias gradient) only with bias_grad: that launch keeps the reduction's grid;
+    // otherwise blocks per chain as requested (grid-stride loop), else the wide grid
+    const dim3 g(bias_grad ? pw_blocks(n) : (blocks > 0 ? blocks : pw_blocks_wide(n)), batch);
     if (wp.n_regions == 16) {
         if (bias_grad) k_web_adj<T, 16, true><<<g, kPwThreads, 0, s>>>(nvox_of(n), th, delta, c16, bias, wp, sc, out, partial);
         else k_web_adj<T, 16, false><<<g, kPwThreads, 0, s>>>(nvox_of(n), th, delta, c16, bias, wp, sc, out, partial);
@@ -660,7 +661,7 @@ cudaError_t launch_reduce(int what, int nblk, int batch, const double* partial, 
                                           const ChainScalars*, double*, cudaStream_t);                              \
     template cudaError_t launch_web_adjoint<T>(int, int, const Fields16&, const T*, const uint16_t*,                \
                                                const BiasT<T>*, const WebParams&, const ChainScalars*,              \
-                                               const Fields16&, double*, bool, cudaStream_t);                       \
+                                               const Fields16&, double*, bool, cudaStream_t, int);                  \
     template cudaError_t launch_cic_gather<T>(int, int, const T*, const Fields16&, const Fields16&, cudaStream_t);  \
     template cudaError_t launch_alpt_adjoint<T>(int, int, const T*, const T*, const Fields16&, const Fields16&,     \
                                                 double, double, cudaStream_t);                                      \

@@ -62,7 +62,8 @@ cudaError_t launch_pass_b(int n, int batch, const T* lnf, const T* beta_i, const
 template <typename T>
 cudaError_t launch_web_adjoint(int n, int batch, const Fields16& th, const T* delta, const uint16_t* c16,
                                const BiasT<T>* bias, const WebParams& wp, const ChainScalars* sc,
-                               const Fields16& out, double* partial, bool bias_grad, cudaStream_t s);
+                               const Fields16& out, double* partial, bool bias_grad, cudaStream_t s,
+                               int blocks = 0);   // blocks per chain without bias_grad (0: built-in)
 template <typename T>
 cudaError_t launch_cic_gather(int n, int batch, const T* gdelta, const Fields16& psi3, const Fields16& out3,
                               cudaStream_t s);

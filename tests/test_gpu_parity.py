@@ -173,6 +173,36 @@ def test_second_cutoff_against_oracle(precision):
     ctx.close()
 
 
+@pytest.mark.parametrize("name,precision", [("64_hier", "fp32"), ("16_phi", "fp64")])
+def test_autotune_keeps_results_and_later_calls_work(name, precision):
+    """bridge_autotune only changes launch shapes: the gradient after tuning matches the oracle
+    and the one before tuning, on two calls, and a leapfrog trajectory (its own captured graph)
+    still runs.  Before and after are not bit-identical: the CIC deposit flushes into global
+    memory with float atomics, whose order changes from one evaluation to the next, so they
+    are compared at a tenth of the oracle bound (FP32 max(1e-5, S), FP64 max(1e-11, 1e-8 S))."""
+    n, box, nr, seed = CASES[name]
+    cfg, bias, nu, counts = case(n, box, nr, seed)
+    f, lp_o, g_o, _, cond = oracle_ref(name, cfg, bias, nu, counts)
+    prec = pkg.BRIDGE_FP64 if precision == "fp64" else pkg.BRIDGE_FP32
+    ctx, nu_d, c_d = run_gpu(cfg, bias, nu, counts, prec)
+    _, g0, _ = ctx.bridge_logpost_grad(nu_d, c_d, [bias], want_bias_grad=False)
+    g0 = g0.double().cpu().numpy()
+    choices = ctx.bridge_autotune(nu_d, c_d, [bias])
+    print(f"autotune {name} {precision}: {choices}")
+    assert len(choices) == 4 and all(c in (0, 1, 2, 3, 4, 5, 6, 8) for c in choices[:3]) and choices[3] >= 0
+    ltol = FP64_LP if precision == "fp64" else FP32_LP
+    for _ in range(2):
+        lp, g, _ = ctx.bridge_logpost_grad(nu_d, c_d, [bias], want_bias_grad=False)
+        g = g.double().cpu().numpy()
+        assert abs(lp[0] - lp_o) <= ltol * abs(lp_o)
+        assert rel_l2(g.reshape(g_o.shape), g_o) <= grad_tol(precision, cond)
+        assert rel_l2(g, g0) <= 0.1 * grad_tol(precision, cond)
+    p_d = torch.tensor(synth.momentum(n, seed + 7), dtype=nu_d.dtype, device="cuda").contiguous()
+    h0, h1 = ctx.bridge_leapfrog(nu_d.clone(), p_d, c_d, [bias], 3, 1e-4)
+    assert np.all(np.isfinite(h0)) and np.all(np.isfinite(h1))
+    ctx.close()
+
+
 def test_batched_chains_match_single_and_oracle():
     cfgs = [case(32, 300.0, 4, 1001 + 10 * b) for b in range(3)]
     biases = synth.perturbed_biases(cfgs[0][1], 3, 6001)
