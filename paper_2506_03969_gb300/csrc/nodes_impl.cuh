@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_node(const NodeArgs A, int bat
         for (int f = 0; f < SH::IN; ++f) {
             T* s = slab_f(f);
             auto line = [&](int c) { return s + ((c / 8) * 16 + 2 * (c % 8)) * N; };
-            ztile_inv<C, decltype(line), true>(reinterpret_cast<const V*>(A.spec_in[f]) + chain * nspec, line, (long long)N, x0, y0, sm, t, io);
+            ztile_inv<C, decltype(line), true, PlainLineIO, 1>(reinterpret_cast<const V*>(A.spec_in[f]) + chain * nspec, line, (long long)N, x0, y0, sm, t, io);
         }
         // (2) per-voxel stage
         const size_t coff = (size_t)chain * NVOX;

@@ -280,26 +280,45 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YP
 // the kernel).  In FP32, 1/k^2 is the correctly rounded reciprocal of the exact
 // integer m^2 times 1/kf^2, which spares a gather whose addresses differ in
 // every lane.
+//
+// The ALPT blend K(k) = exp(-r_s^2 k^2 / 2) (Sect. 2.3) is a product of an x
+// factor and a (y, z) factor.  In FP32 the x factor comes from a per-CTA
+// shared-memory copy of K at m^2 = mx^2 and the (y, z) factor, K at
+// m^2 = my^2 + mz^2, is one per-thread constant; 1 - K is formed from that
+// product.  Both factors are entries of the same FP64-computed table.
 template <typename T> struct XTerm {
     T cr, ci;          // (cre + i cim) ky^py kz^pz
+    T kyz;             // K at m^2 = my^2 + mz^2 (FP32 blend codes)
     int px, rcode;
 };
+template <typename T> __device__ __forceinline__ bool sep_blend(int rcode) {
+    return sizeof(T) == 4 && (rcode == R_KBLEND || rcode == R_1MKBLEND);
+}
 template <typename T>
 __device__ __forceinline__ XTerm<T> xterm(const Term& tm, int my, int mz, int n, const KParams& kp) {
     const T kf = T(kp.kf);
     const T cyz = kpow<T>(my, tm.py, n, kf) * kpow<T>(mz, tm.pz, n, kf);
-    return XTerm<T>{T(tm.cre) * cyz, T(tm.cim) * cyz, tm.px, tm.rcode};
+    const T kyz = sep_blend<T>(tm.rcode)
+                      ? __ldg(reinterpret_cast<const T*>(kp.rtab) + (R_KBLEND - 1) * kp.rlen + my * my + mz * mz)
+                      : T(0);
+    return XTerm<T>{T(tm.cre) * cyz, T(tm.cim) * cyz, kyz, tm.px, tm.rcode};
 }
-// multiplier of element mx; m2yz = my^2 + mz^2
+// multiplier of element mx (x index ix); m2yz = my^2 + mz^2; skx: the CTA's
+// K(mx^2) by x index (filled when the program has FP32 blend codes)
 template <typename T>
-__device__ __forceinline__ cplx_t<T> xmult(const XTerm<T>& x, int mx, int m2yz, int n, const KParams& kp) {
+__device__ __forceinline__ cplx_t<T> xmult(const XTerm<T>& x, int mx, int ix, int m2yz, int n, const KParams& kp,
+                                           const T* skx) {
     T r = kpow<T>(mx, x.px, n, T(kp.kf));
     if (x.rcode != R_ONE) {
         const int m2 = mx * mx + m2yz;
-        if (sizeof(T) == 4 && x.rcode == R_INVK2)
+        if (sizeof(T) == 4 && x.rcode == R_INVK2) {
             r *= m2 > 0 ? T(kp.inv_kf2) * T(__frcp_rn(float(m2))) : T(0);
-        else
+        } else if (sep_blend<T>(x.rcode)) {
+            const T k = skx[ix] * x.kyz;
+            r *= x.rcode == R_KBLEND ? k : T(1) - k;
+        } else {
             r *= __ldg(reinterpret_cast<const T*>(kp.rtab) + (x.rcode - 1) * kp.rlen + m2);
+        }
     }
     return cmake<cplx_t<T>>(x.cr * r, x.ci * r);
 }
@@ -320,6 +339,19 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_n
     const int g = TL::b_g(t);
     const int my = signed_freq(c0 + g, N), mz = kz;
     const int m2yz = my * my + mz * mz;
+    // x factor of the blend, when a term of the program uses it
+    T* skx = reinterpret_cast<T*>(sm + TL::SM_ELEMS + TL::STAGE_ELEMS);
+    bool blend = false;
+    for (int m = 0; m < P.n_merge; ++m) blend |= sep_blend<T>(P.merge[m].rcode);
+    for (int m = 0; m < P.n_expand; ++m) blend |= sep_blend<T>(P.expand[m].rcode);
+    if (blend) {
+        const T* ktab = reinterpret_cast<const T*>(kp.rtab) + (R_KBLEND - 1) * kp.rlen;
+        for (int ix = t; ix < N; ix += TL::NT) {
+            const int mx = signed_freq(ix, N);
+            skx[ix] = __ldg(ktab + mx * mx);
+        }
+        __syncthreads();
+    }
     V Q[TL::J][TL::N2];   // bit-reversed k2 order
 #pragma unroll
     for (int j = 0; j < TL::J; ++j)
@@ -344,8 +376,8 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_n
             const int k1 = TL::b_k1(t, j);
 #pragma unroll
             for (int i = 0; i < TL::N2; ++i) {
-                const int mx = signed_freq(k1 + TL::N1 * bitrev(i, TL::N2), N);
-                Q[j][i] = cadd(Q[j][i], cmul(xmult<T>(xt, mx, m2yz, N, kp), X[j][i]));
+                const int ix = k1 + TL::N1 * bitrev(i, TL::N2);
+                Q[j][i] = cadd(Q[j][i], cmul(xmult<T>(xt, signed_freq(ix, N), ix, m2yz, N, kp, skx), X[j][i]));
             }
         }
     }
@@ -358,8 +390,8 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_n
             const int k1 = TL::b_k1(t, j);
 #pragma unroll
             for (int k2 = 0; k2 < TL::N2; ++k2) {
-                const int mx = signed_freq(k1 + TL::N1 * k2, N);
-                Y[j][k2] = cmul(xmult<T>(xt, mx, m2yz, N, kp), Q[j][bitrev(k2, TL::N2)]);
+                const int ix = k1 + TL::N1 * k2;
+                Y[j][k2] = cmul(xmult<T>(xt, signed_freq(ix, N), ix, m2yz, N, kp, skx), Q[j][bitrev(k2, TL::N2)]);
             }
         }
         __syncthreads();
@@ -475,7 +507,7 @@ static cudaError_t col_n(int batch, const PassProgram& p, const KParams& kp, cud
 }
 template <typename T, int N> static cudaError_t xnode_n(int batch, const PassProgram& p, const KParams& kp, cudaStream_t s) {
     using TL = Tile<T, N, true>;
-    const size_t sm = size_t(TL::SM_ELEMS + TL::STAGE_ELEMS) * sizeof(cplx_t<T>);
+    const size_t sm = size_t(TL::SM_ELEMS + TL::STAGE_ELEMS) * sizeof(cplx_t<T>) + N * sizeof(T);
     cudaError_t e = set_smem(k_x_node<T, N>, sm);
     if (e != cudaSuccess) return e;
     k_x_node<T, N><<<dim3(TL::TILES, batch), TL::NT, sm, s>>>(p, kp);

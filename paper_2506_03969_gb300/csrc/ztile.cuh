@@ -125,7 +125,10 @@ __device__ __forceinline__ void ztile_fwd(LineFn line, long long bstride, typena
 }
 
 // Inverse: spectrum -> real lines (unnormalised).  Same calling rules.
-template <typename C, typename LineFn, bool STREAM = false, typename IO = PlainLineIO>
+// LOADS: spectrum rows a thread keeps in flight (0: 9 in FP32, 5 in FP64).  The
+// fused nodes pass 1: with 8-9 CTAs per SM their load phases already overlap
+// other CTAs' arithmetic, and more rows in flight only raised their registers.
+template <typename C, typename LineFn, bool STREAM = false, typename IO = PlainLineIO, int LOADS = 0>
 __device__ __forceinline__ void ztile_inv(const typename C::V* __restrict__ spec, LineFn line, long long bstride,
                                           int x0, int y0, typename C::V* sm, int t, const IO& io = IO()) {
     using V = typename C::V;
@@ -133,16 +136,52 @@ __device__ __forceinline__ void ztile_inv(const typename C::V* __restrict__ spec
     using V4 = typename C::V4;
     constexpr int N = C::N1 * C::N2;
     constexpr int ROWS = C::NT / 8;
+    constexpr int TOTAL = (N / 2 + 1) * C::GY;            // (kz, y) rows of the tile
+    constexpr int ITERS = (TOTAL + ROWS - 1) / ROWS;      // rows per thread
+    // all of a thread's row loads are issued before the first is used (one DRAM
+    // latency per batch instead of one per row); batches bound the registers
+    constexpr int MAXB = LOADS > 0 ? LOADS : (sizeof(T) == 4 ? 9 : 5);
+    constexpr int NB = (ITERS + MAXB - 1) / MAXB;
+    constexpr int PB = (ITERS + NB - 1) / NB;
     const int pair = t % 8;
-    for (int idx = t / 8; idx < (N / 2 + 1) * C::GY; idx += ROWS) {
-        const int kz = idx / C::GY, yl = idx % C::GY;
-        const int c = yl * 8 + pair;
-        const V4 ab = zld4<STREAM>(reinterpret_cast<const V4*>(spec + (size_t(kz) * N + (y0 + yl)) * N + x0 + 2 * pair));
-        if (kz == 0 || kz == N / 2) {
-            sm[c * C::ZS + kz] = cmake<V>(ab.x, ab.z);   // real parts only
-        } else {
-            sm[c * C::ZS + kz] = cmake<V>(ab.x - ab.w, ab.y + ab.z);
-            sm[c * C::ZS + (N - kz)] = cmake<V>(ab.x + ab.w, ab.z - ab.y);
+    if constexpr (MAXB == 1) {
+        for (int idx = t / 8; idx < TOTAL; idx += ROWS) {
+            const int kz = idx / C::GY, yl = idx % C::GY;
+            const int c = yl * 8 + pair;
+            const V4 ab = zld4<STREAM>(reinterpret_cast<const V4*>(spec + (size_t(kz) * N + (y0 + yl)) * N + x0 + 2 * pair));
+            if (kz == 0 || kz == N / 2) {
+                sm[c * C::ZS + kz] = cmake<V>(ab.x, ab.z);   // real parts only
+            } else {
+                sm[c * C::ZS + kz] = cmake<V>(ab.x - ab.w, ab.y + ab.z);
+                sm[c * C::ZS + (N - kz)] = cmake<V>(ab.x + ab.w, ab.z - ab.y);
+            }
+        }
+    } else {
+#pragma unroll 1
+        for (int b0 = 0; b0 < ITERS; b0 += PB) {
+            V4 ab[PB];
+#pragma unroll
+            for (int u = 0; u < PB; ++u) {
+                const int idx = t / 8 + (b0 + u) * ROWS;
+                if (b0 + u < ITERS && idx < TOTAL) {
+                    const int kz = idx / C::GY, yl = idx % C::GY;
+                    ab[u] = zld4<STREAM>(reinterpret_cast<const V4*>(spec + (size_t(kz) * N + (y0 + yl)) * N + x0 + 2 * pair));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < PB; ++u) {
+                const int idx = t / 8 + (b0 + u) * ROWS;
+                if (b0 + u < ITERS && idx < TOTAL) {
+                    const int kz = idx / C::GY, yl = idx % C::GY;
+                    const int c = yl * 8 + pair;
+                    if (kz == 0 || kz == N / 2) {
+                        sm[c * C::ZS + kz] = cmake<V>(ab[u].x, ab[u].z);   // real parts only
+                    } else {
+                        sm[c * C::ZS + kz] = cmake<V>(ab[u].x - ab[u].w, ab[u].y + ab[u].z);
+                        sm[c * C::ZS + (N - kz)] = cmake<V>(ab[u].x + ab[u].w, ab[u].z - ab[u].y);
+                    }
+                }
+            }
         }
     }
     __syncthreads();
