@@ -57,37 +57,64 @@ __global__ void __launch_bounds__(kNodeThreads) k_node(const NodeArgs A, int bat
             auto line = [&](int c) { return s + ((c / 8) * 16 + 2 * (c % 8)) * N; };
             ztile_inv<C, decltype(line), true, PlainLineIO, 1>(reinterpret_cast<const V*>(A.spec_in[f]) + chain * nspec, line, (long long)N, x0, y0, sm, t, io);
         }
-        // (2) per-voxel stage
+        // (2) per-voxel stage, U voxels per thread step: the slab (and g_rho)
+        // loads of all U voxels are issued before any result is stored, so a
+        // step waits for one L2 round trip instead of U
         const size_t coff = (size_t)chain * NVOX;
-        for (int v = t; v < TV; v += kNodeThreads) {
-            const int z = v % N, xl = (v / N) % 16, yl = v / (16 * N);
-            const size_t g = coff + ((size_t)(x0 + xl) * N + (y0 + yl)) * N + z;
+        constexpr int U = 4;
+        static_assert(TV % (U * kNodeThreads) == 0, "tile voxels must split into whole steps");
+        for (int v0 = t; v0 < TV; v0 += U * kNodeThreads) {
             if constexpr (KIND == NODE_ALPT_FWD) {
-                const T d0 = io.ld(slab_f(0) + v);
-                T phi[6];
+                T in[U][7];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) phi[q] = io.ld(slab_f(1 + q) + v);
-                T a, b;
-                alpt_sources<T>(d0, phi, T(A.growth), T(A.d2), a, b);
-                io.st(slab_f(0) + v, a);
-                io.st(slab_f(1) + v, b);
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int q = 0; q < 7; ++q) in[u][q] = io.ld(slab_f(q) + v0 + u * kNodeThreads);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int v = v0 + u * kNodeThreads;
+                    T a, b;
+                    alpt_sources<T>(in[u][0], &in[u][1], T(A.growth), T(A.d2), a, b);
+                    io.st(slab_f(0) + v, a);
+                    io.st(slab_f(1) + v, b);
+                }
             } else if constexpr (KIND == NODE_ALPT_ADJ) {
-                const T d0 = io.ld(slab_f(0) + v);
-                T phi[6], gphi[6], gd0;
+                T in[U][9];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) phi[q] = io.ld(slab_f(1 + q) + v);
-                alpt_sources_adj<T>(d0, phi, T(A.growth), T(A.d2), io.ld(slab_f(7) + v), io.ld(slab_f(8) + v), gd0, gphi);
-                io.st(slab_f(0) + v, gd0);
+                for (int u = 0; u < U; ++u)
 #pragma unroll
-                for (int q = 0; q < 6; ++q) io.st(slab_f(1 + q) + v, gphi[q]);
+                    for (int q = 0; q < 9; ++q) in[u][q] = io.ld(slab_f(q) + v0 + u * kNodeThreads);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int v = v0 + u * kNodeThreads;
+                    T gphi[6], gd0;
+                    alpt_sources_adj<T>(in[u][0], &in[u][1], T(A.growth), T(A.d2), in[u][7], in[u][8], gd0, gphi);
+                    io.st(slab_f(0) + v, gd0);
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) io.st(slab_f(1 + q) + v, gphi[q]);
+                }
             } else if constexpr (KIND == NODE_GATHER) {
-                CicCorner<T> c;
-                cic_corner<T>((long long)(g - coff), N, io.ld(slab_f(0) + v), io.ld(slab_f(1) + v), io.ld(slab_f(2) + v), c);
-                T out[3];
-                cic_gather_one<T>(c, N, reinterpret_cast<const T*>(A.real_in[0]) + coff, out);
-                io.st(slab_f(0) + v, out[0]);
-                io.st(slab_f(1) + v, out[1]);
-                io.st(slab_f(2) + v, out[2]);
+                const T* grho = reinterpret_cast<const T*>(A.real_in[0]) + coff;
+                CicCorner<T> c[U];
+                T gv[U][8];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int v = v0 + u * kNodeThreads;
+                    const int z = v % N, xl = (v / N) % 16, yl = v / (16 * N);
+                    const long long q = ((long long)(x0 + xl) * N + (y0 + yl)) * N + z;
+                    cic_corner<T>(q, N, io.ld(slab_f(0) + v), io.ld(slab_f(1) + v), io.ld(slab_f(2) + v), c[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) cic_gather_loads<T>(c[u], N, grho, gv[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int v = v0 + u * kNodeThreads;
+                    T out[3];
+                    cic_gather_combine<T>(c[u], gv[u], out);
+                    io.st(slab_f(0) + v, out[0]);
+                    io.st(slab_f(1) + v, out[1]);
+                    io.st(slab_f(2) + v, out[2]);
+                }
             }
         }
         __syncthreads();

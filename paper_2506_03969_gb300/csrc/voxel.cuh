@@ -372,28 +372,46 @@ template <typename T> __device__ __forceinline__ void cic_corner(long long q, in
 }
 
 // CIC gather adjoint of one particle: g_psi_j = sum_corners g_rho[c] dw_c/dpsi_j.
-template <typename T> __device__ __forceinline__ void cic_gather_one(const CicCorner<T>& c, int N, const T* g, T out[3]) {
+// Split into the eight corner loads (corner index 4a + 2b + e for offsets a, b, e
+// along x, y, z) and their combination, so that callers can issue the loads of
+// several particles before combining any of them.
+template <typename T> __device__ __forceinline__ void cic_gather_loads(const CicCorner<T>& c, int N, const T* g, T gv[8]) {
     const int msk = N - 1;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const size_t ix = (size_t)((c.i0[0] + a) & msk) * N;
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const size_t iy = (ix + (size_t)((c.i0[1] + b) & msk)) * N;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) gv[4 * a + 2 * b + e] = g[iy + ((c.i0[2] + e) & msk)];
+        }
+    }
+}
+template <typename T> __device__ __forceinline__ void cic_gather_combine(const CicCorner<T>& c, const T gv[8], T out[3]) {
     T gx = 0, gy = 0, gz = 0;
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
         const T wx = a ? c.f[0] : T(1) - c.f[0], dwx = a ? T(1) : T(-1);
-        const size_t ix = (size_t)((c.i0[0] + a) & msk) * N;
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
             const T wy = b ? c.f[1] : T(1) - c.f[1], dwy = b ? T(1) : T(-1);
-            const size_t iy = (ix + (size_t)((c.i0[1] + b) & msk)) * N;
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const T wz = e ? c.f[2] : T(1) - c.f[2], dwz = e ? T(1) : T(-1);
-                const T gv = g[iy + ((c.i0[2] + e) & msk)];
-                gx += gv * dwx * wy * wz;
-                gy += gv * wx * dwy * wz;
-                gz += gv * wx * wy * dwz;
+                const T v = gv[4 * a + 2 * b + e];
+                gx += v * dwx * wy * wz;
+                gy += v * wx * dwy * wz;
+                gz += v * wx * wy * dwz;
             }
         }
     }
     out[0] = gx; out[1] = gy; out[2] = gz;
+}
+template <typename T> __device__ __forceinline__ void cic_gather_one(const CicCorner<T>& c, int N, const T* g, T out[3]) {
+    T gv[8];
+    cic_gather_loads<T>(c, N, g, gv);
+    cic_gather_combine<T>(c, gv, out);
 }
 
 }  // namespace bridge
