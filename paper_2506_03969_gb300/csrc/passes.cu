@@ -204,14 +204,23 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YP
             if (m + 1 < P.n_merge) TL::stage(src_of(m + 1), buf, t);
             V X[TL::J][TL::N2];
             TL::fwdB(sm, t, X);
+            if (!XM && tm.py == 0) {
+                // no ky power: one complex factor (cre + i cim) kz^pz for the whole tile
+                const V c = ymult<T>(tm, 0, kz, N, kp);
 #pragma unroll
-            for (int j = 0; j < TL::J; ++j) {
-                const int k1 = TL::b_k1(t, j);
+                for (int j = 0; j < TL::J; ++j)
 #pragma unroll
-                for (int i = 0; i < TL::N2; ++i) {
-                    int mx, my, mz;
-                    TL::freqs(k1 + TL::N1 * bitrev(i, TL::N2), g, kz, c0, mx, my, mz);
-                    acc[j][i] = cadd(acc[j][i], cmul(ymult<T>(tm, my, mz, N, kp), X[j][i]));
+                    for (int i = 0; i < TL::N2; ++i) acc[j][i] = cadd(acc[j][i], cmul(c, X[j][i]));
+            } else {
+#pragma unroll
+                for (int j = 0; j < TL::J; ++j) {
+                    const int k1 = TL::b_k1(t, j);
+#pragma unroll
+                    for (int i = 0; i < TL::N2; ++i) {
+                        int mx, my, mz;
+                        TL::freqs(k1 + TL::N1 * bitrev(i, TL::N2), g, kz, c0, mx, my, mz);
+                        acc[j][i] = cadd(acc[j][i], cmul(ymult<T>(tm, my, mz, N, kp), X[j][i]));
+                    }
                 }
             }
         }
@@ -253,14 +262,23 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YP
             const Term tm = P.expand[m];
             if (tm.src != s) continue;
             V Y[TL::J][TL::N2];
+            if (!XM && tm.py == 0) {
+                // no ky power: one complex factor (cre + i cim) kz^pz for the whole tile
+                const V c = ymult<T>(tm, 0, kz, N, kp);
 #pragma unroll
-            for (int j = 0; j < TL::J; ++j) {
-                const int k1 = TL::b_k1(t, j);
+                for (int j = 0; j < TL::J; ++j)
 #pragma unroll
-                for (int k2 = 0; k2 < TL::N2; ++k2) {
-                    int mx, my, mz;
-                    TL::freqs(k1 + TL::N1 * k2, g, kz, c0, mx, my, mz);
-                    Y[j][k2] = cmul(ymult<T>(tm, my, mz, N, kp), X[j][k2]);
+                    for (int k2 = 0; k2 < TL::N2; ++k2) Y[j][k2] = cmul(c, X[j][k2]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < TL::J; ++j) {
+                    const int k1 = TL::b_k1(t, j);
+#pragma unroll
+                    for (int k2 = 0; k2 < TL::N2; ++k2) {
+                        int mx, my, mz;
+                        TL::freqs(k1 + TL::N1 * k2, g, kz, c0, mx, my, mz);
+                        Y[j][k2] = cmul(ymult<T>(tm, my, mz, N, kp), X[j][k2]);
+                    }
                 }
             }
             __syncthreads();
@@ -277,9 +295,9 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YP
 // complex coefficient fold into one per-thread constant; per element only the
 // kx power and the radial factor remain.  Radial factors other than 1/k^2 come
 // from the per-context tables indexed by m^2 (exact, no transcendental work in
-// the kernel).  In FP32, 1/k^2 is the correctly rounded reciprocal of the exact
-// integer m^2 times 1/kf^2, which spares a gather whose addresses differ in
-// every lane.
+// the kernel).  In FP32, 1/k^2 is 1/kf^2 divided by the exact integer m^2 with
+// the hardware reciprocal (within 2 ulp), which spares a gather whose addresses
+// differ in every lane.
 //
 // The ALPT blend K(k) = exp(-r_s^2 k^2 / 2) (Sect. 2.3) is a product of an x
 // factor and a (y, z) factor.  In FP32 the x factor comes from a per-CTA
@@ -312,7 +330,7 @@ __device__ __forceinline__ cplx_t<T> xmult(const XTerm<T>& x, int mx, int ix, in
     if (x.rcode != R_ONE) {
         const int m2 = mx * mx + m2yz;
         if (sizeof(T) == 4 && x.rcode == R_INVK2) {
-            r *= m2 > 0 ? T(kp.inv_kf2) * T(__frcp_rn(float(m2))) : T(0);
+            r *= m2 > 0 ? T(__fdividef(float(kp.inv_kf2), float(m2))) : T(0);
         } else if (sep_blend<T>(x.rcode)) {
             const T k = skx[ix] * x.kyz;
             r *= x.rcode == R_KBLEND ? k : T(1) - k;
