@@ -168,6 +168,64 @@ template <typename T, int N, bool XM> struct Tile {
     }
 };
 
+// FP32 multiplier specialised at compile time for the term shapes the programs
+// use: kx^PX times 1 (RC = R_ONE) or 1/k^2 (RC = R_INVK2); HI is the
+// compile-time part N1 * k2 of the element's x index k1 + HI, so the signed
+// frequency and the Nyquist test reduce to one add and one compare.
+template <typename T, int N, int PX, int RC, int HI>
+__device__ __forceinline__ T xfac(int k1, int m2yz, const KParams& kp) {
+    const int mx = HI < N / 2 ? k1 + HI : k1 + HI - N;
+    T r = T(1);
+    if constexpr (PX > 0) {
+        const T kx = T(kp.kf) * T(mx);
+        r = PX == 1 ? kx : kx * kx;
+        if constexpr (PX == 1) r = (mx == -(N / 2)) ? T(0) : r;
+    }
+    if constexpr (RC == R_INVK2) {
+        const int m2 = mx * mx + m2yz;
+        r *= m2 > 0 ? T(__fdividef(float(kp.inv_kf2), float(m2))) : T(0);
+    }
+    return r;
+}
+template <int V> using IC = std::integral_constant<int, V>;
+// Compile-time loop: f(IC<I>{}) for I = B .. E-1.
+template <int B, int E, typename F> __device__ __forceinline__ void sfor(F&& f) {
+    if constexpr (B < E) {
+        f(IC<B>{});
+        sfor<B + 1, E>(f);
+    }
+}
+// Calls f(IC<PX>, IC<RC>) for the specialised shapes; false for any other term.
+// FP32 up to N = 256 only (FP64 and N = 512 have no registers to spare for the
+// extra code paths).
+template <typename T, int N, typename F> __device__ __forceinline__ bool xdispatch(const Term& tm, F&& f) {
+    if constexpr (sizeof(T) != 4 || N > 256) {
+        return false;
+    } else {
+        switch (tm.px * 8 + tm.rcode) {
+            case 0 * 8 + R_ONE: f(IC<0>{}, IC<R_ONE>{}); return true;
+            case 1 * 8 + R_ONE: f(IC<1>{}, IC<R_ONE>{}); return true;
+            case 2 * 8 + R_ONE: f(IC<2>{}, IC<R_ONE>{}); return true;
+            case 0 * 8 + R_INVK2: f(IC<0>{}, IC<R_INVK2>{}); return true;
+            case 1 * 8 + R_INVK2: f(IC<1>{}, IC<R_INVK2>{}); return true;
+            case 2 * 8 + R_INVK2: f(IC<2>{}, IC<R_INVK2>{}); return true;
+            default: return false;
+        }
+    }
+}
+
+// f(IC<PY>) for a y-pass term with ky power PY = 1 or 2 (FP32 up to N = 256);
+// false otherwise.
+template <typename T, int N, typename F> __device__ __forceinline__ bool ydispatch(const Term& tm, F&& f) {
+    if constexpr (sizeof(T) != 4 || N > 256) {
+        return false;
+    } else {
+        if (tm.py == 1) { f(IC<1>{}); return true; }
+        if (tm.py == 2) { f(IC<2>{}); return true; }
+        return false;
+    }
+}
+
 #ifndef BRIDGE_YPASS_MINB
 #define BRIDGE_YPASS_MINB 3   // FP32; the FP64 y passes (one CTA per SM by shared memory) are unbounded
 #endif
@@ -211,7 +269,22 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YP
                 for (int j = 0; j < TL::J; ++j)
 #pragma unroll
                     for (int i = 0; i < TL::N2; ++i) acc[j][i] = cadd(acc[j][i], cmul(c, X[j][i]));
-            } else {
+            } else if (XM || !ydispatch<T, N>(tm, [&](auto pyc) {
+                           // ky^PY per element times one complex factor (cre + i cim) kz^pz
+                           constexpr int PY = decltype(pyc)::value;
+                           Term t0 = tm;
+                           t0.py = 0;
+                           const V c = ymult<T>(t0, 0, kz, N, kp);
+#pragma unroll
+                           for (int j = 0; j < TL::J; ++j) {
+                               const int k1 = TL::b_k1(t, j);
+                               sfor<0, TL::N2>([&](auto ic) {
+                                   constexpr int i = decltype(ic)::value;
+                                   const T r = xfac<T, N, PY, R_ONE, TL::N1 * bitrev(i, TL::N2)>(k1, 0, kp);
+                                   acc[j][i] = cadd(acc[j][i], cmul(cmake<V>(c.x * r, c.y * r), X[j][i]));
+                               });
+                           }
+                       })) {
 #pragma unroll
                 for (int j = 0; j < TL::J; ++j) {
                     const int k1 = TL::b_k1(t, j);
@@ -269,7 +342,22 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YP
                 for (int j = 0; j < TL::J; ++j)
 #pragma unroll
                     for (int k2 = 0; k2 < TL::N2; ++k2) Y[j][k2] = cmul(c, X[j][k2]);
-            } else {
+            } else if (XM || !ydispatch<T, N>(tm, [&](auto pyc) {
+                           // ky^PY per element times one complex factor (cre + i cim) kz^pz
+                           constexpr int PY = decltype(pyc)::value;
+                           Term t0 = tm;
+                           t0.py = 0;
+                           const V c = ymult<T>(t0, 0, kz, N, kp);
+#pragma unroll
+                           for (int j = 0; j < TL::J; ++j) {
+                               const int k1 = TL::b_k1(t, j);
+                               sfor<0, TL::N2>([&](auto ic) {
+                                   constexpr int k2 = decltype(ic)::value;
+                                   const T r = xfac<T, N, PY, R_ONE, TL::N1 * k2>(k1, 0, kp);
+                                   Y[j][k2] = cmul(cmake<V>(c.x * r, c.y * r), X[j][k2]);
+                               });
+                           }
+                       })) {
 #pragma unroll
                 for (int j = 0; j < TL::J; ++j) {
                     const int k1 = TL::b_k1(t, j);
@@ -389,13 +477,27 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_n
         if (m + 1 < P.n_merge) TL::stage(src_of(m + 1), buf, t);
         V X[TL::J][TL::N2];
         TL::fwdB(sm, t, X);
+        const bool spec = xdispatch<T, N>(tm, [&](auto pxc, auto rcc) {
+            constexpr int PX = decltype(pxc)::value, RC = decltype(rcc)::value;
 #pragma unroll
-        for (int j = 0; j < TL::J; ++j) {
-            const int k1 = TL::b_k1(t, j);
+            for (int j = 0; j < TL::J; ++j) {
+                const int k1 = TL::b_k1(t, j);
+                sfor<0, TL::N2>([&](auto ic) {
+                    constexpr int i = decltype(ic)::value;
+                    const T r = xfac<T, N, PX, RC, TL::N1 * bitrev(i, TL::N2)>(k1, m2yz, kp);
+                    Q[j][i] = cadd(Q[j][i], cmul(cmake<V>(xt.cr * r, xt.ci * r), X[j][i]));
+                });
+            }
+        });
+        if (!spec) {
 #pragma unroll
-            for (int i = 0; i < TL::N2; ++i) {
-                const int ix = k1 + TL::N1 * bitrev(i, TL::N2);
-                Q[j][i] = cadd(Q[j][i], cmul(xmult<T>(xt, signed_freq(ix, N), ix, m2yz, N, kp, skx), X[j][i]));
+            for (int j = 0; j < TL::J; ++j) {
+                const int k1 = TL::b_k1(t, j);
+#pragma unroll
+                for (int i = 0; i < TL::N2; ++i) {
+                    const int ix = k1 + TL::N1 * bitrev(i, TL::N2);
+                    Q[j][i] = cadd(Q[j][i], cmul(xmult<T>(xt, signed_freq(ix, N), ix, m2yz, N, kp, skx), X[j][i]));
+                }
             }
         }
     }
@@ -403,13 +505,27 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_n
         const Term tm = P.expand[m];
         const XTerm<T> xt = xterm<T>(tm, my, mz, N, kp);
         V Y[TL::J][TL::N2];   // natural k2 order
+        const bool spec = xdispatch<T, N>(tm, [&](auto pxc, auto rcc) {
+            constexpr int PX = decltype(pxc)::value, RC = decltype(rcc)::value;
 #pragma unroll
-        for (int j = 0; j < TL::J; ++j) {
-            const int k1 = TL::b_k1(t, j);
+            for (int j = 0; j < TL::J; ++j) {
+                const int k1 = TL::b_k1(t, j);
+                sfor<0, TL::N2>([&](auto ic) {
+                    constexpr int k2 = decltype(ic)::value;
+                    const T r = xfac<T, N, PX, RC, TL::N1 * k2>(k1, m2yz, kp);
+                    Y[j][k2] = cmul(cmake<V>(xt.cr * r, xt.ci * r), Q[j][bitrev(k2, TL::N2)]);
+                });
+            }
+        });
+        if (!spec) {
 #pragma unroll
-            for (int k2 = 0; k2 < TL::N2; ++k2) {
-                const int ix = k1 + TL::N1 * k2;
-                Y[j][k2] = cmul(xmult<T>(xt, signed_freq(ix, N), ix, m2yz, N, kp, skx), Q[j][bitrev(k2, TL::N2)]);
+            for (int j = 0; j < TL::J; ++j) {
+                const int k1 = TL::b_k1(t, j);
+#pragma unroll
+                for (int k2 = 0; k2 < TL::N2; ++k2) {
+                    const int ix = k1 + TL::N1 * k2;
+                    Y[j][k2] = cmul(xmult<T>(xt, signed_freq(ix, N), ix, m2yz, N, kp, skx), Q[j][bitrev(k2, TL::N2)]);
+                }
             }
         }
         __syncthreads();
