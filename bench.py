@@ -81,8 +81,8 @@ def csrc_hash() -> str:
 def recorded_traffic(kernel: str, alg_bytes_per_launch: float):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the current sources.
 
-    The summary line reads: traffic <kernel> <csrc hash> <dram/algorithmic ratio>; the ratio
-    (measured on a smaller mesh) scales to the timed launch."""
+    The summary line reads: traffic <kernel> <csrc hash> <dram/algorithmic ratio>; the ratio,
+    measured by ncu on the same workload, times the algorithmic bytes of the timed launch."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.md")
     if not os.path.exists(path):
         return None

@@ -172,8 +172,10 @@ template <typename T, int N, bool XM> struct Tile {
 // use: kx^PX times 1 (RC = R_ONE) or 1/k^2 (RC = R_INVK2); HI is the
 // compile-time part N1 * k2 of the element's x index k1 + HI, so the signed
 // frequency and the Nyquist test reduce to one add and one compare.
+// RC = R_SQRTP reads the radial table at m^2; the blend codes take the x factor
+// skx[k1 + HI] times the per-thread (y, z) factor kyz (see XTerm).
 template <typename T, int N, int PX, int RC, int HI>
-__device__ __forceinline__ T xfac(int k1, int m2yz, const KParams& kp) {
+__device__ __forceinline__ T xfac(int k1, int m2yz, const KParams& kp, const T* skx = nullptr, T kyz = T(0)) {
     const int mx = HI < N / 2 ? k1 + HI : k1 + HI - N;
     T r = T(1);
     if constexpr (PX > 0) {
@@ -184,6 +186,12 @@ __device__ __forceinline__ T xfac(int k1, int m2yz, const KParams& kp) {
     if constexpr (RC == R_INVK2) {
         const int m2 = mx * mx + m2yz;
         r *= m2 > 0 ? T(__fdividef(float(kp.inv_kf2), float(m2))) : T(0);
+    } else if constexpr (RC == R_SQRTP) {
+        r *= __ldg(reinterpret_cast<const T*>(kp.rtab) + (R_SQRTP - 1) * kp.rlen + mx * mx + m2yz);
+    } else if constexpr (RC == R_KBLEND) {
+        r *= skx[k1 + HI] * kyz;
+    } else if constexpr (RC == R_1MKBLEND) {
+        r *= T(1) - skx[k1 + HI] * kyz;
     }
     return r;
 }
@@ -209,6 +217,9 @@ template <typename T, int N, typename F> __device__ __forceinline__ bool xdispat
             case 0 * 8 + R_INVK2: f(IC<0>{}, IC<R_INVK2>{}); return true;
             case 1 * 8 + R_INVK2: f(IC<1>{}, IC<R_INVK2>{}); return true;
             case 2 * 8 + R_INVK2: f(IC<2>{}, IC<R_INVK2>{}); return true;
+            case 0 * 8 + R_SQRTP: f(IC<0>{}, IC<R_SQRTP>{}); return true;
+            case 0 * 8 + R_KBLEND: f(IC<0>{}, IC<R_KBLEND>{}); return true;
+            case 0 * 8 + R_1MKBLEND: f(IC<0>{}, IC<R_1MKBLEND>{}); return true;
             default: return false;
         }
     }
@@ -484,7 +495,7 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_n
                 const int k1 = TL::b_k1(t, j);
                 sfor<0, TL::N2>([&](auto ic) {
                     constexpr int i = decltype(ic)::value;
-                    const T r = xfac<T, N, PX, RC, TL::N1 * bitrev(i, TL::N2)>(k1, m2yz, kp);
+                    const T r = xfac<T, N, PX, RC, TL::N1 * bitrev(i, TL::N2)>(k1, m2yz, kp, skx, xt.kyz);
                     Q[j][i] = cadd(Q[j][i], cmul(cmake<V>(xt.cr * r, xt.ci * r), X[j][i]));
                 });
             }
@@ -512,7 +523,7 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_n
                 const int k1 = TL::b_k1(t, j);
                 sfor<0, TL::N2>([&](auto ic) {
                     constexpr int k2 = decltype(ic)::value;
-                    const T r = xfac<T, N, PX, RC, TL::N1 * k2>(k1, m2yz, kp);
+                    const T r = xfac<T, N, PX, RC, TL::N1 * k2>(k1, m2yz, kp, skx, xt.kyz);
                     Y[j][k2] = cmul(cmake<V>(xt.cr * r, xt.ci * r), Q[j][bitrev(k2, TL::N2)]);
                 });
             }
@@ -541,8 +552,14 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_n
 // ---------------------------------------------------------------------------
 template <typename T, int N> using ZPass = ZCfg<T, N, 256 / (8 * Split<N>::N2)>;
 
+#ifndef BRIDGE_ZFWD_MINB
+#define BRIDGE_ZFWD_MINB 5   // FP32 up to N = 256: 48 registers, no spills, 0.351 -> 0.337 ms at 256^3 (the inverse pass loses at 5; 512 would spill)
+#endif
+#ifndef BRIDGE_ZINV_MINB
+#define BRIDGE_ZINV_MINB 0   // 0: register count left to the compiler
+#endif
 template <typename T, int N>
-__global__ void __launch_bounds__(ZPass<T, N>::NT) k_z_fwd(const ZProgram P) {
+__global__ void __launch_bounds__(ZPass<T, N>::NT, (sizeof(T) == 4 && N <= 256) ? BRIDGE_ZFWD_MINB : 0) k_z_fwd(const ZProgram P) {
     using ZT = ZPass<T, N>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -557,7 +574,7 @@ __global__ void __launch_bounds__(ZPass<T, N>::NT) k_z_fwd(const ZProgram P) {
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(ZPass<T, N>::NT) k_z_inv(const ZProgram P) {
+__global__ void __launch_bounds__(ZPass<T, N>::NT, BRIDGE_ZINV_MINB) k_z_inv(const ZProgram P) {
     using ZT = ZPass<T, N>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];

@@ -282,8 +282,14 @@ __device__ __forceinline__ void web_forward(const Fields16& th, size_t j, T rho_
     web_eval<T, NR>(a6, h6, rho_mass, B, wp, S);
 }
 
+#ifndef BRIDGE_PASSA_MINB
+#define BRIDGE_PASSA_MINB 0   // 0: register count left to the compiler
+#endif
+#ifndef BRIDGE_PASSB_MINB
+#define BRIDGE_PASSB_MINB 0
+#endif
 template <typename T, int NR>
-__global__ void __launch_bounds__(kPwThreads) k_pass_a(long long nvox, Fields16 th, const T* rho, T* lnf_out,
+__global__ void __launch_bounds__(kPwThreads, BRIDGE_PASSA_MINB) k_pass_a(long long nvox, Fields16 th, const T* rho, T* lnf_out,
                                                       T* beta_out, const BiasT<T>* bias, WebParams wp, double* partial) {
     __shared__ BiasT<T> B;
     const int chain = blockIdx.y;
@@ -319,7 +325,7 @@ template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = double4_32a; };
 
 template <typename T>
-__global__ void __launch_bounds__(kPwThreads) k_pass_b(long long nvox, const T* lnf, const T* beta_i,
+__global__ void __launch_bounds__(kPwThreads, BRIDGE_PASSB_MINB) k_pass_b(long long nvox, const T* lnf, const T* beta_i,
                                                       const uint16_t* c16, const T* nu, const ChainScalars* sc,
                                                       double* partial) {
     using V4 = typename Vec4<T>::type;
@@ -356,10 +362,12 @@ __global__ void __launch_bounds__(kPwThreads) k_pass_b(long long nvox, const T* 
 // requested (BIASG), the partial sums of d/d alpha_r and d/d beta_r.
 // ---------------------------------------------------------------------------
 #ifndef BRIDGE_WEBADJ_MINB
-#define BRIDGE_WEBADJ_MINB 3
+#define BRIDGE_WEBADJ_MINB 4   // FP32 without bias gradients: 64 registers, no spills, 0.74 -> 0.66 ms at 256^3
 #endif
+// FP64 and the bias-gradient variant spill more at 64 registers and keep 80 (3 blocks per SM).
+template <typename T, bool BIASG> constexpr int webadj_minb() { return sizeof(T) == 4 && !BIASG ? BRIDGE_WEBADJ_MINB : 3; }
 template <typename T, int NR, bool BIASG>
-__global__ void __launch_bounds__(kPwThreads, BRIDGE_WEBADJ_MINB) k_web_adj(long long nvox, Fields16 th, const T* rho,
+__global__ void __launch_bounds__(kPwThreads, (webadj_minb<T, BIASG>())) k_web_adj(long long nvox, Fields16 th, const T* rho,
                                                           const uint16_t* c16, const BiasT<T>* bias, WebParams wp,
                                                           const ChainScalars* sc, Fields16 out, double* partial) {
     __shared__ BiasT<T> B;
