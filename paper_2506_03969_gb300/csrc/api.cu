@@ -62,6 +62,7 @@ struct bridge_ctx {
     BiasD* biasd = nullptr;
     void* biast = nullptr;
     int* errflag = nullptr;
+    int* tickets = nullptr;     // [B] counters of the fused partial-sum reductions (zero between launches)
     void* grad_tmp = nullptr;   // gradient scratch for leapfrog
     void* node_scratch = nullptr;  // per-CTA slabs of the fused nodes
     size_t node_cap = 0;           // bytes of node_scratch
@@ -137,6 +138,7 @@ cudaEvent_t prof_event(bridge_ctx* ctx) {
     }
     return ctx->prof_pool[ctx->prof_used++];
 }
+inline RedArgs red_args(bridge_ctx* c) { return RedArgs{c->tickets, c->sc, c->biasd, c->nr}; }
 template <typename T> double rby(const bridge_ctx* c) { return double(c->nvox) * c->B * sizeof(T); }
 template <typename T> double sby(const bridge_ctx* c) { return double(c->nspec) * c->B * 2 * sizeof(T); }
 inline double c16b(const bridge_ctx* c) { return double(c->nvox) * c->B * 2; }
@@ -403,12 +405,10 @@ template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelih
     RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_TH, nth), mreal(ctx, RB_TH, nth)));
     CKL("web_bias", (nth + 3) * rby<T>(ctx), launch_pass_a<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 12), RB<T>(ctx, RB_DELTA), RB<T>(ctx, RB_LNF),
                         RB<T>(ctx, RB_LNF + 1), reinterpret_cast<const BiasT<T>*>(ctx->biast), ctx->wp, ctx->partial,
-                        ctx->stream));
-    CKL("reduce", 0.0, launch_reduce(RED_SUMF, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+                        red_args(ctx), ctx->stream));   // sum f and ln C reduced by the last block
     if (likelihood) {
         CKL("nb_lik", 3 * rby<T>(ctx) + c16b(ctx), launch_pass_b<T>(ctx->n, ctx->B, RB<T>(ctx, RB_LNF), RB<T>(ctx, RB_LNF + 1), ctx->c16, nu, ctx->sc,
-                            ctx->partial, ctx->stream));
-        CKL("reduce", 0.0, launch_reduce(RED_LIK, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+                            ctx->partial, red_args(ctx), ctx->stream));   // log posterior reduced by the last block
     }
     return BRIDGE_OK;
 }
@@ -521,9 +521,17 @@ template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad, boo
         CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
     RUN(y_identity<T>(ctx, SP_SCR, 1, false));
-    // inverse z and the white-noise prior: g_nu = (likelihood part) - nu
-    RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_SCR, 1), mreal(ctx, RB_SCR, 1)));
-    CKL("prior_grad", 3 * rby<T>(ctx), launch_sub<T>(ctx->nvox * ctx->B, RB<T>(ctx, RB_SCR), nu, grad, ctx->stream));
+    // inverse z with the white-noise prior in its stores: g_nu = (likelihood part) - nu
+    {
+        ZProgram p{};
+        p.n_fields = 1;
+        p.in[0] = ctx->spec[SP_SCR];
+        p.out[0] = grad;
+        p.sub[0] = nu;
+        p.in_cs = ctx->nspec;
+        p.out_cs = ctx->nvox;
+        CKL("z_inv", 2 * rby<T>(ctx) + sby<T>(ctx), launch_z_inv<T>(ctx->n, ctx->B, p, ctx->stream));
+    }
     return BRIDGE_OK;
 }
 
@@ -562,8 +570,9 @@ template <typename T> int upload_bias(bridge_ctx* ctx, const bridge_bias* bias) 
 template <typename T> int prep_counts(bridge_ctx* ctx, const int32_t* counts) {
     if (!counts) return fail(ctx, BRIDGE_EINVAL, "counts is NULL");
     CK(cudaMemsetAsync(ctx->errflag, 0, sizeof(int), ctx->stream));
-    CKL("counts_prep", 3 * c16b(ctx), launch_counts_prep<T>(ctx->n, ctx->B, counts, ctx->c16, ctx->partial, ctx->errflag, ctx->stream));
-    CKL("reduce", 0.0, launch_reduce(RED_NTR, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
+    // N_tr is reduced by the kernel's last block (no separate reduction launch)
+    CKL("counts_prep", 3 * c16b(ctx), launch_counts_prep<T>(ctx->n, ctx->B, counts, ctx->c16, ctx->partial, ctx->errflag,
+                                                             red_args(ctx), ctx->stream));
     return BRIDGE_OK;
 }
 
@@ -1022,6 +1031,8 @@ int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
                                                       std::to_string(pl.node_bytes) + " or grid " + std::to_string(grid));
     }
     if (cudaMalloc(&ctx->errflag, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&ctx->tickets, sizeof(int) * ctx->B) != cudaSuccess ||
+        cudaMemset(ctx->tickets, 0, sizeof(int) * ctx->B) != cudaSuccess ||
         cudaMallocHost(&ctx->sc_host, sizeof(ChainScalars) * ctx->B) != cudaSuccess ||
         cudaMallocHost(&ctx->biasd_host, sizeof(BiasD) * ctx->B) != cudaSuccess ||
         cudaMallocHost(&ctx->biast_host, sizeof(BiasT<double>) * ctx->B) != cudaSuccess ||
@@ -1038,6 +1049,7 @@ void bridge_destroy(bridge_ctx* ctx) {
     if (ctx->stream || ctx->ws) cudaStreamSynchronize(ctx->stream);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->errflag) cudaFree(ctx->errflag);
+    if (ctx->tickets) cudaFree(ctx->tickets);
     if (ctx->h_nu) cudaFree(ctx->h_nu);
     if (ctx->h_counts) cudaFree(ctx->h_counts);
     if (ctx->h_grad) cudaFree(ctx->h_grad);

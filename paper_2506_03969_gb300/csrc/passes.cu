@@ -573,7 +573,14 @@ __global__ void __launch_bounds__(ZPass<T, N>::NT, (sizeof(T) == 4 && N <= 256) 
                   threadIdx.x);
 }
 
-template <typename T, int N>
+// Stores out[p] = v - sub[p] (the subtrahend read through the read-only path).
+template <typename T> struct SubLineIO {
+    const T* out;
+    const T* sub;
+    template <typename U> __device__ __forceinline__ void st(U* p, U v) const { *p = v - __ldg(sub + (p - out)); }
+};
+
+template <typename T, int N, bool SUB>
 __global__ void __launch_bounds__(ZPass<T, N>::NT, BRIDGE_ZINV_MINB) k_z_inv(const ZProgram P) {
     using ZT = ZPass<T, N>;
     using V = cplx_t<T>;
@@ -584,8 +591,13 @@ __global__ void __launch_bounds__(ZPass<T, N>::NT, BRIDGE_ZINV_MINB) k_z_inv(con
     ZT::tile_xy(blockIdx.x, x0, y0);
     T* rout = reinterpret_cast<T*>(P.out[f]) + chain * P.out_cs;
     auto line = [&](int c) { return rout + (size_t(x0 + 2 * (c % 8)) * N + y0 + c / 8) * N; };
-    ztile_inv<ZT>(reinterpret_cast<const V*>(P.in[f]) + chain * P.in_cs, line, (long long)N * N, x0, y0, sm,
-                  threadIdx.x);
+    const V* spec = reinterpret_cast<const V*>(P.in[f]) + chain * P.in_cs;
+    if constexpr (SUB) {
+        const SubLineIO<T> io{rout, reinterpret_cast<const T*>(P.sub[f]) + chain * P.out_cs};
+        ztile_inv<ZT, decltype(line), false, SubLineIO<T>>(spec, line, (long long)N * N, x0, y0, sm, threadIdx.x, io);
+    } else {
+        ztile_inv<ZT>(spec, line, (long long)N * N, x0, y0, sm, threadIdx.x);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -627,13 +639,21 @@ template <typename T, int N> static cudaError_t z_fwd_n(int batch, const ZProgra
     k_z_fwd<T, N><<<dim3(ZT::TILES, p.n_fields, batch), ZT::NT, sm, s>>>(p);
     return cudaGetLastError();
 }
-template <typename T, int N> static cudaError_t z_inv_n(int batch, const ZProgram& p, cudaStream_t s) {
+template <typename T, int N, bool SUB> static cudaError_t z_inv_nk(int batch, const ZProgram& p, cudaStream_t s) {
     using ZT = ZPass<T, N>;
     const size_t sm = size_t(ZT::SM_ELEMS) * sizeof(cplx_t<T>);
-    cudaError_t e = set_smem(k_z_inv<T, N>, sm);
+    cudaError_t e = set_smem(k_z_inv<T, N, SUB>, sm);
     if (e != cudaSuccess) return e;
-    k_z_inv<T, N><<<dim3(ZT::TILES, p.n_fields, batch), ZT::NT, sm, s>>>(p);
+    k_z_inv<T, N, SUB><<<dim3(ZT::TILES, p.n_fields, batch), ZT::NT, sm, s>>>(p);
     return cudaGetLastError();
+}
+template <typename T, int N> static cudaError_t z_inv_n(int batch, const ZProgram& p, cudaStream_t s) {
+    if (p.sub[0]) {
+        for (int f = 0; f < p.n_fields; ++f)
+            if (!p.sub[f]) return cudaErrorInvalidValue;
+        return z_inv_nk<T, N, true>(batch, p, s);
+    }
+    return z_inv_nk<T, N, false>(batch, p, s);
 }
 template <typename T, int N, bool XM, bool FWD>
 static cudaError_t col_n(int batch, const PassProgram& p, const KParams& kp, cudaStream_t s) {

@@ -54,6 +54,9 @@ struct ZProgram {
     const void* in[kMaxFields];
     void* out[kMaxFields];
     long long in_cs, out_cs;
+    // inverse pass only: when sub[0] is set, out[f] = IDFT(in[f]) - sub[f] (sub: real
+    // fields with the layout and chain stride of out; may be out itself)
+    const void* sub[kMaxFields];
 };
 
 template <typename T> cudaError_t launch_z_fwd(int n, int batch, const ZProgram& p, cudaStream_t s);

@@ -22,6 +22,26 @@ __device__ __forceinline__ void write_partials(const double (&acc)[K], double* p
     }
 }
 
+__device__ void reduce_body(int what, int chain, int nblk, int K, const double* partial, ChainScalars* sc,
+                            const BiasD* bias, int n_regions);
+
+// Partial sums of this block, then the last block of the chain to finish (a
+// ticket counter) reduces all of them with reduce_body and resets the counter.
+template <int K>
+__device__ __forceinline__ void finish_partials(const double (&acc)[K], double* partial, int what, const RedArgs& ra) {
+    write_partials<K>(acc, partial);
+    __shared__ int last;
+    __threadfence();   // this block's partials are visible before its ticket is taken
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ra.tickets + blockIdx.y, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        reduce_body(what, blockIdx.y, gridDim.x, K, partial, ra.sc, ra.bias, ra.n_regions);
+        if (threadIdx.x == 0) ra.tickets[blockIdx.y] = 0;
+    }
+}
+
 #define PW_LOOP(i, nvox) for (long long i = (long long)blockIdx.x * kPwThreads + threadIdx.x; i < (nvox); \
                               i += (long long)gridDim.x * kPwThreads)
 
@@ -29,7 +49,8 @@ __device__ __forceinline__ void write_partials(const double (&acc)[K], double* p
 // counts: int32 -> uint16 with range check; N_tr partial sums
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kPwThreads) k_counts_prep(long long nvox, const int32_t* __restrict__ counts,
-                                                           uint16_t* __restrict__ c16, double* partial, int* err) {
+                                                           uint16_t* __restrict__ c16, double* partial, int* err,
+                                                           RedArgs ra) {
     const size_t off = (size_t)blockIdx.y * nvox;
     double acc[1] = {0.0};
     long long s = 0;
@@ -49,7 +70,7 @@ __global__ void __launch_bounds__(kPwThreads) k_counts_prep(long long nvox, cons
     }
     if (bad) atomicOr(err, 1);
     acc[0] = (double)s;
-    write_partials<1>(acc, partial);
+    finish_partials<1>(acc, partial, RED_NTR, ra);
 }
 
 // ---------------------------------------------------------------------------
@@ -290,7 +311,8 @@ __device__ __forceinline__ void web_forward(const Fields16& th, size_t j, T rho_
 #endif
 template <typename T, int NR>
 __global__ void __launch_bounds__(kPwThreads, BRIDGE_PASSA_MINB) k_pass_a(long long nvox, Fields16 th, const T* rho, T* lnf_out,
-                                                      T* beta_out, const BiasT<T>* bias, WebParams wp, double* partial) {
+                                                      T* beta_out, const BiasT<T>* bias, WebParams wp, double* partial,
+                                                      RedArgs ra) {
     __shared__ BiasT<T> B;
     const int chain = blockIdx.y;
     if (threadIdx.x == 0) B = bias[chain];
@@ -314,7 +336,7 @@ __global__ void __launch_bounds__(kPwThreads, BRIDGE_PASSA_MINB) k_pass_a(long l
         if (++cnt == 16) { accd += (double)accf; accf = T(0); cnt = 0; }
     }
     acc[0] = accd + (double)accf;
-    write_partials<1>(acc, partial);
+    finish_partials<1>(acc, partial, RED_SUMF, ra);
 }
 
 // NB likelihood (pass B): ln nbar = ln f + ln C; partial sums of log P,
@@ -327,7 +349,7 @@ template <> struct Vec4<double> { using type = double4_32a; };
 template <typename T>
 __global__ void __launch_bounds__(kPwThreads, BRIDGE_PASSB_MINB) k_pass_b(long long nvox, const T* lnf, const T* beta_i,
                                                       const uint16_t* c16, const T* nu, const ChainScalars* sc,
-                                                      double* partial) {
+                                                      double* partial, RedArgs ra) {
     using V4 = typename Vec4<T>::type;
     const int chain = blockIdx.y;
     const size_t off = (size_t)chain * nvox;
@@ -354,7 +376,7 @@ __global__ void __launch_bounds__(kPwThreads, BRIDGE_PASSB_MINB) k_pass_b(long l
         if (++cnt == 4) { acc[0] += a0; acc[1] += a1; acc[2] += a2; a0 = a1 = a2 = T(0); cnt = 0; }
     }
     acc[0] += a0; acc[1] += a1; acc[2] += a2;
-    write_partials<3>(acc, partial);
+    finish_partials<3>(acc, partial, RED_LIK, ra);
 }
 
 // ---------------------------------------------------------------------------
@@ -423,11 +445,6 @@ template <typename T> __global__ void k_shift(long long count, const T* in, T* o
         out[i] = in[i] + c;
 }
 
-template <typename T> __global__ void k_sub(long long count, const T* r, const T* nu, T* out) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
-        out[i] = r[i] - nu[i];
-}
-
 // Leapfrog (Sect. 2.2): p += ck g; nu += cd p; partial sums of p^2 after the update.
 template <typename T>
 __global__ void __launch_bounds__(kPwThreads) k_kick_drift(long long nvox, T* p, T* nu, const T* g, T ck, T cd,
@@ -480,10 +497,13 @@ __device__ double lognormal_dlogpdf(double b, double mu, double sigma) {
     return -1.0 / b - (lb - mu) / (sigma * sigma * b);
 }
 
-__global__ void __launch_bounds__(1024) k_reduce(int what, int nblk, int K, const double* partial, ChainScalars* sc,
-                                                 const BiasD* bias, int n_regions) {
+// Final reduction of one chain's partial sums (K components per block, nblk
+// blocks) in a fixed order, and the scalars derived from them.  Called by every
+// thread of one block of at least 32 K threads; partials are read past L1 (they
+// may have been written by other blocks of the same launch).
+__device__ void reduce_body(int what, int chain, int nblk, int K, const double* partial, ChainScalars* sc,
+                            const BiasD* bias, int n_regions) {
     __shared__ double tot[32];
-    const int chain = blockIdx.x;
     ChainScalars& S = sc[chain];
     const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (k < K) {
@@ -494,12 +514,12 @@ __global__ void __launch_bounds__(1024) k_reduce(int what, int nblk, int K, cons
         int b = lane;
 #pragma unroll 4
         for (; b + 96 < nblk; b += 128) {
-            v0 += p[(size_t)b * K];
-            v1 += p[(size_t)(b + 32) * K];
-            v2 += p[(size_t)(b + 64) * K];
-            v3 += p[(size_t)(b + 96) * K];
+            v0 += __ldcg(p + (size_t)b * K);
+            v1 += __ldcg(p + (size_t)(b + 32) * K);
+            v2 += __ldcg(p + (size_t)(b + 64) * K);
+            v3 += __ldcg(p + (size_t)(b + 96) * K);
         }
-        for (; b < nblk; b += 32) v0 += p[(size_t)b * K];
+        for (; b < nblk; b += 32) v0 += __ldcg(p + (size_t)b * K);
         double v = (v0 + v1) + (v2 + v3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -544,6 +564,11 @@ __global__ void __launch_bounds__(1024) k_reduce(int what, int nblk, int K, cons
     }
 }
 
+__global__ void __launch_bounds__(1024) k_reduce(int what, int nblk, int K, const double* partial, ChainScalars* sc,
+                                                 const BiasD* bias, int n_regions) {
+    reduce_body(what, blockIdx.x, nblk, K, partial, sc, bias, n_regions);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -551,8 +576,8 @@ static inline long long nvox_of(int n) { return (long long)n * n * n; }
 
 template <typename T>
 cudaError_t launch_counts_prep(int n, int batch, const int32_t* counts, uint16_t* c16, double* partial, int* err,
-                               cudaStream_t s) {
-    k_counts_prep<<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), counts, c16, partial, err);
+                               const RedArgs& ra, cudaStream_t s) {
+    k_counts_prep<<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), counts, c16, partial, err, ra);
     return cudaGetLastError();
 }
 template <typename T>
@@ -583,17 +608,18 @@ cudaError_t launch_cic_scatter(int n, int batch, const Fields16& psi3, T* delta,
 }
 template <typename T>
 cudaError_t launch_pass_a(int n, int batch, const Fields16& th, const T* delta, T* lnf, T* beta_i,
-                          const BiasT<T>* bias, const WebParams& wp, double* partial, cudaStream_t s) {
+                          const BiasT<T>* bias, const WebParams& wp, double* partial, const RedArgs& ra,
+                          cudaStream_t s) {
     if (wp.n_regions == 16)
-        k_pass_a<T, 16><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), th, delta, lnf, beta_i, bias, wp, partial);
+        k_pass_a<T, 16><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), th, delta, lnf, beta_i, bias, wp, partial, ra);
     else
-        k_pass_a<T, 4><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), th, delta, lnf, beta_i, bias, wp, partial);
+        k_pass_a<T, 4><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), th, delta, lnf, beta_i, bias, wp, partial, ra);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_pass_b(int n, int batch, const T* lnf, const T* beta_i, const uint16_t* c16, const T* nu,
-                          const ChainScalars* sc, double* partial, cudaStream_t s) {
-    k_pass_b<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), lnf, beta_i, c16, nu, sc, partial);
+                          const ChainScalars* sc, double* partial, const RedArgs& ra, cudaStream_t s) {
+    k_pass_b<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), lnf, beta_i, c16, nu, sc, partial, ra);
     return cudaGetLastError();
 }
 template <typename T>
@@ -629,11 +655,6 @@ template <typename T> cudaError_t launch_shift(long long count, const T* in, T* 
     k_shift<T><<<(unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b)), 256, 0, s>>>(count, in, out, c);
     return cudaGetLastError();
 }
-template <typename T> cudaError_t launch_sub(long long count, const T* r, const T* nu, T* out, cudaStream_t s) {
-    long long b = (count + 1023) / 1024;
-    k_sub<T><<<(unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b)), 256, 0, s>>>(count, r, nu, out);
-    return cudaGetLastError();
-}
 template <typename T>
 cudaError_t launch_kick_drift(int n, int batch, T* p, T* nu, const T* g, double ck, double cd, double* partial,
                               cudaStream_t s) {
@@ -659,21 +680,21 @@ cudaError_t launch_reduce(int what, int nblk, int batch, const double* partial, 
 }
 
 #define PW_INST(T)                                                                                                   \
-    template cudaError_t launch_counts_prep<T>(int, int, const int32_t*, uint16_t*, double*, int*, cudaStream_t);   \
+    template cudaError_t launch_counts_prep<T>(int, int, const int32_t*, uint16_t*, double*, int*, const RedArgs&,   \
+                                               cudaStream_t);                                                       \
     template cudaError_t launch_alpt_src<T>(int, int, const Fields16&, T*, T*, double, double, cudaStream_t);        \
     template cudaError_t launch_fill<T>(long long, T*, T, cudaStream_t);                                            \
     template cudaError_t launch_cic_scatter<T>(int, int, const Fields16&, T*, cudaStream_t);                        \
     template cudaError_t launch_pass_a<T>(int, int, const Fields16&, const T*, T*, T*, const BiasT<T>*,             \
-                                          const WebParams&, double*, cudaStream_t);                                 \
+                                          const WebParams&, double*, const RedArgs&, cudaStream_t);                 \
     template cudaError_t launch_pass_b<T>(int, int, const T*, const T*, const uint16_t*, const T*,                  \
-                                          const ChainScalars*, double*, cudaStream_t);                              \
+                                          const ChainScalars*, double*, const RedArgs&, cudaStream_t);              \
     template cudaError_t launch_web_adjoint<T>(int, int, const Fields16&, const T*, const uint16_t*,                \
                                                const BiasT<T>*, const WebParams&, const ChainScalars*,              \
                                                const Fields16&, double*, bool, cudaStream_t, int);                  \
     template cudaError_t launch_cic_gather<T>(int, int, const T*, const Fields16&, const Fields16&, cudaStream_t);  \
     template cudaError_t launch_alpt_adjoint<T>(int, int, const T*, const T*, const Fields16&, const Fields16&,     \
                                                 double, double, cudaStream_t);                                      \
-    template cudaError_t launch_sub<T>(long long, const T*, const T*, T*, cudaStream_t);                            \
     template cudaError_t launch_shift<T>(long long, const T*, T*, T, cudaStream_t);                                 \
     template cudaError_t launch_kick_drift<T>(int, int, T*, T*, const T*, double, double, double*, cudaStream_t);   \
     template cudaError_t launch_lnnbar<T>(long long, int, const T*, const ChainScalars*, T*, cudaStream_t);         \

@@ -42,11 +42,20 @@ struct BiasD {        // double copy of a chain's table and prior (device)
     double mu_alpha, sigma_alpha, mu_beta, sigma_beta;
 };
 
+// Reduction done by the last block of the kernel that writes the partial sums
+// (a per-chain ticket counter, zero between launches, picks that block).
+struct RedArgs {
+    int* tickets;          // [batch], zero-initialised; each fused launch leaves it at zero
+    ChainScalars* sc;
+    const BiasD* bias;
+    int n_regions;
+};
+
 struct Fields16 { void* p[16]; };
 
 template <typename T>
 cudaError_t launch_counts_prep(int n, int batch, const int32_t* counts, uint16_t* c16, double* partial, int* err,
-                               cudaStream_t s);
+                               const RedArgs& ra, cudaStream_t s);
 template <typename T>
 cudaError_t launch_alpt_src(int n, int batch, const Fields16& in7, T* a_out, T* b_out, double growth, double d2,
                             cudaStream_t s);
@@ -55,10 +64,10 @@ template <typename T>
 cudaError_t launch_cic_scatter(int n, int batch, const Fields16& psi3, T* delta, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pass_a(int n, int batch, const Fields16& th, const T* delta, T* lnf, T* beta_i,
-                          const BiasT<T>* bias, const WebParams& wp, double* partial, cudaStream_t s);
+                          const BiasT<T>* bias, const WebParams& wp, double* partial, const RedArgs& ra, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pass_b(int n, int batch, const T* lnf, const T* beta_i, const uint16_t* c16, const T* nu,
-                          const ChainScalars* sc, double* partial, cudaStream_t s);
+                          const ChainScalars* sc, double* partial, const RedArgs& ra, cudaStream_t s);
 template <typename T>
 cudaError_t launch_web_adjoint(int n, int batch, const Fields16& th, const T* delta, const uint16_t* c16,
                                const BiasT<T>* bias, const WebParams& wp, const ChainScalars* sc,
@@ -70,8 +79,6 @@ cudaError_t launch_cic_gather(int n, int batch, const T* gdelta, const Fields16&
 template <typename T>
 cudaError_t launch_alpt_adjoint(int n, int batch, const T* ga, const T* gb, const Fields16& in7,
                                 const Fields16& out7, double growth, double d2, cudaStream_t s);
-template <typename T>
-cudaError_t launch_sub(long long count, const T* r, const T* nu, T* out, cudaStream_t s);
 template <typename T> cudaError_t launch_shift(long long count, const T* in, T* out, T c, cudaStream_t s);
 template <typename T>
 cudaError_t launch_kick_drift(int n, int batch, T* p, T* nu, const T* g, double ck, double cd, double* partial,
@@ -86,5 +93,6 @@ cudaError_t launch_eigs(int n, int batch, const Fields16& t6, const Fields16& ou
 cudaError_t launch_reduce(int what, int nblk, int batch, const double* partial, ChainScalars* sc, const BiasD* bias,
                           int n_regions, cudaStream_t s);
 enum { RED_NTR = 0, RED_SUMF = 1, RED_LIK = 2, RED_BIASGRAD = 3, RED_P2 = 4 };
+
 
 }  // namespace bridge
