@@ -194,6 +194,10 @@ __device__ __forceinline__ void cic_flush4(double* g, const CicWin<double>& W, i
     }
 }
 
+#ifndef BRIDGE_CIC_BZ
+#define BRIDGE_CIC_BZ 16   // particle block depth along z: 16 gives 16 x 16 x 24-cell windows (48 KB, four CTAs
+                           // per SM), 0.33 -> 0.22 ms at 256^3 against 32 (80 KB, two CTAs per SM)
+#endif
 template <typename T, int BZ>
 __global__ void __launch_bounds__(kPwThreads) k_cic_scatter(int N, long long nvox, Fields16 psi3, T* rho) {
     using CB = CicBlock<T>;
@@ -595,7 +599,7 @@ template <typename T>
 cudaError_t launch_cic_scatter(int n, int batch, const Fields16& psi3, T* delta, cudaStream_t s) {
     using CB = CicBlock<T>;
     if (n < 16) return cudaErrorInvalidValue;
-    // BZ = 32 (one warp = one z run of 32 particles), 16 on the smallest mesh
+    // BZ = BRIDGE_CIC_BZ (16 or 32 particles along z), 16 on the smallest mesh
     auto run = [&](auto kern, int bz) {
         const size_t sm = size_t(CB::BX + 2 * CB::H) * (CB::BY + 2 * CB::H) * (bz + 2 * CB::H) * 8;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
@@ -604,7 +608,7 @@ cudaError_t launch_cic_scatter(int n, int batch, const Fields16& psi3, T* delta,
         kern<<<dim3(blocks, batch), kPwThreads, sm, s>>>(n, nvox_of(n), psi3, delta);
         return cudaGetLastError();
     };
-    return n >= 32 ? run(k_cic_scatter<T, 32>, 32) : run(k_cic_scatter<T, 16>, 16);
+    return n >= BRIDGE_CIC_BZ ? run(k_cic_scatter<T, BRIDGE_CIC_BZ>, BRIDGE_CIC_BZ) : run(k_cic_scatter<T, 16>, 16);
 }
 template <typename T>
 cudaError_t launch_pass_a(int n, int batch, const Fields16& th, const T* delta, T* lnf, T* beta_i,
