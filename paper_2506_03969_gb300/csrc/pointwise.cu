@@ -73,55 +73,7 @@ __global__ void __launch_bounds__(kPwThreads) k_counts_prep(long long nvox, cons
     finish_partials<1>(acc, partial, RED_NTR, ra);
 }
 
-// ---------------------------------------------------------------------------
-// ALPT sources (Sect. 2.3): a = -D delta0 + D2 S2 (2LPT divergence),
-// b = theta_SC = 3[(1 - 2/3 D delta0)^(1/2) - 1] (D delta0 < 3/2), -3 otherwise.
-// in7 = delta0, phi_xx, phi_xy, phi_xz, phi_yy, phi_yz, phi_zz.
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(kPwThreads) k_alpt_src(long long nvox, Fields16 in7, T* a_out, T* b_out, T D, T D2) {
-    const size_t off = (size_t)blockIdx.y * nvox;
-    const T* d0 = (const T*)in7.p[0] + off;
-    const T* pxx = (const T*)in7.p[1] + off; const T* pxy = (const T*)in7.p[2] + off;
-    const T* pxz = (const T*)in7.p[3] + off; const T* pyy = (const T*)in7.p[4] + off;
-    const T* pyz = (const T*)in7.p[5] + off; const T* pzz = (const T*)in7.p[6] + off;
-    PW_LOOP(i, nvox) {
-        const T xx = pxx[i], xy = pxy[i], xz = pxz[i], yy = pyy[i], yz = pyz[i], zz = pzz[i];
-        const T s2 = xx * yy + xx * zz + yy * zz - xy * xy - xz * xz - yz * yz;
-        const T x = D * d0[i];
-        a_out[off + i] = -x + D2 * s2;
-        T arg = T(1) - T(2.0 / 3.0) * x;
-        arg = arg > T(1e-12) ? arg : T(1e-12);
-        b_out[off + i] = x < T(1.5) ? T(3) * (v_sqrt(arg) - T(1)) : T(-3);
-    }
-}
-
-// ALPT adjoint: given g_a, g_b, returns g_delta0 (direct) and g_phi (stored comps).
-template <typename T>
-__global__ void __launch_bounds__(kPwThreads) k_alpt_adj(long long nvox, const T* ga, const T* gb, Fields16 in7,
-                                                        Fields16 out7, T D, T D2) {
-    const size_t off = (size_t)blockIdx.y * nvox;
-    PW_LOOP(i, nvox) {
-        const size_t j = off + i;
-        const T d0 = ((const T*)in7.p[0])[j];
-        const T xx = ((const T*)in7.p[1])[j], xy = ((const T*)in7.p[2])[j], xz = ((const T*)in7.p[3])[j];
-        const T yy = ((const T*)in7.p[4])[j], yz = ((const T*)in7.p[5])[j], zz = ((const T*)in7.p[6])[j];
-        const T g_a = ga[j], g_b = gb[j];
-        const T x = D * d0;
-        const T arg = T(1) - T(2.0 / 3.0) * x;
-        // d theta_SC / d delta0 = -D / sqrt(1 - 2/3 D delta0) on the uncollapsed, unclamped branch
-        const T dsc = (x < T(1.5) && arg > T(1e-12)) ? -D / v_sqrt(arg) : T(0);
-        const T gs2 = D2 * g_a;
-        ((T*)out7.p[0])[j] = -D * g_a + dsc * g_b;
-        ((T*)out7.p[1])[j] = gs2 * (yy + zz);
-        ((T*)out7.p[2])[j] = gs2 * (T(-2) * xy);
-        ((T*)out7.p[3])[j] = gs2 * (T(-2) * xz);
-        ((T*)out7.p[4])[j] = gs2 * (xx + zz);
-        ((T*)out7.p[5])[j] = gs2 * (T(-2) * yz);
-        ((T*)out7.p[6])[j] = gs2 * (xx + yy);
-    }
-}
-
+// Constant fill (the CIC mass is zeroed before each scatter).
 template <typename T> __global__ void k_fill(long long count, T* p, T v) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
         p[i] = v;
@@ -252,40 +204,6 @@ __global__ void __launch_bounds__(kPwThreads) k_cic_scatter(int N, long long nvo
         const int wy = col % WY, wx = col / WY;
         const int gx = (x0 - H + wx) & msk, gy = (y0 - H + wy) & msk, gz = (z0 - H + 4 * g) & msk;
         cic_flush4(r + ((size_t)gx * N + gy) * N + gz, W, col * WZ + 4 * g);
-    }
-}
-
-// Gather adjoint: g_psi_j = sum_corners g_delta[c] dw_c/dpsi_j (cell units).
-template <typename T>
-__global__ void __launch_bounds__(kPwThreads) k_cic_gather(int N, long long nvox, const T* gdelta, Fields16 psi3, Fields16 out3) {
-    const size_t off = (size_t)blockIdx.y * nvox;
-    const T* g = gdelta + off;
-    const int msk = N - 1;
-    PW_LOOP(q, nvox) {
-        CicCorner<T> c;
-        cic_corner<T>(q, N, ((const T*)psi3.p[0])[off + q], ((const T*)psi3.p[1])[off + q], ((const T*)psi3.p[2])[off + q], c);
-        T gx = 0, gy = 0, gz = 0;
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            const T wx = a ? c.f[0] : T(1) - c.f[0], dwx = a ? T(1) : T(-1);
-            const size_t ix = (size_t)((c.i0[0] + a) & msk) * N;
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const T wy = b ? c.f[1] : T(1) - c.f[1], dwy = b ? T(1) : T(-1);
-                const size_t iy = (ix + (size_t)((c.i0[1] + b) & msk)) * N;
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const T wz = e ? c.f[2] : T(1) - c.f[2], dwz = e ? T(1) : T(-1);
-                    const T gv = g[iy + ((c.i0[2] + e) & msk)];
-                    gx += gv * dwx * wy * wz;
-                    gy += gv * wx * dwy * wz;
-                    gz += gv * wx * wy * dwz;
-                }
-            }
-        }
-        ((T*)out3.p[0])[off + q] = gx;
-        ((T*)out3.p[1])[off + q] = gy;
-        ((T*)out3.p[2])[off + q] = gz;
     }
 }
 
@@ -584,12 +502,6 @@ cudaError_t launch_counts_prep(int n, int batch, const int32_t* counts, uint16_t
     k_counts_prep<<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), counts, c16, partial, err, ra);
     return cudaGetLastError();
 }
-template <typename T>
-cudaError_t launch_alpt_src(int n, int batch, const Fields16& in7, T* a_out, T* b_out, double growth, double d2,
-                            cudaStream_t s) {
-    k_alpt_src<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), in7, a_out, b_out, T(growth), T(d2));
-    return cudaGetLastError();
-}
 template <typename T> cudaError_t launch_fill(long long count, T* p, T v, cudaStream_t s) {
     long long b = (count + 1023) / 1024;
     k_fill<T><<<(unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b)), 256, 0, s>>>(count, p, v);
@@ -642,18 +554,6 @@ cudaError_t launch_web_adjoint(int n, int batch, const Fields16& th, const T* de
     }
     return cudaGetLastError();
 }
-template <typename T>
-cudaError_t launch_cic_gather(int n, int batch, const T* gdelta, const Fields16& psi3, const Fields16& out3,
-                              cudaStream_t s) {
-    k_cic_gather<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(n, nvox_of(n), gdelta, psi3, out3);
-    return cudaGetLastError();
-}
-template <typename T>
-cudaError_t launch_alpt_adjoint(int n, int batch, const T* ga, const T* gb, const Fields16& in7,
-                                const Fields16& out7, double growth, double d2, cudaStream_t s) {
-    k_alpt_adj<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), ga, gb, in7, out7, T(growth), T(d2));
-    return cudaGetLastError();
-}
 template <typename T> cudaError_t launch_shift(long long count, const T* in, T* out, T c, cudaStream_t s) {
     long long b = (count + 1023) / 1024;
     k_shift<T><<<(unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b)), 256, 0, s>>>(count, in, out, c);
@@ -686,7 +586,6 @@ cudaError_t launch_reduce(int what, int nblk, int batch, const double* partial, 
 #define PW_INST(T)                                                                                                   \
     template cudaError_t launch_counts_prep<T>(int, int, const int32_t*, uint16_t*, double*, int*, const RedArgs&,   \
                                                cudaStream_t);                                                       \
-    template cudaError_t launch_alpt_src<T>(int, int, const Fields16&, T*, T*, double, double, cudaStream_t);        \
     template cudaError_t launch_fill<T>(long long, T*, T, cudaStream_t);                                            \
     template cudaError_t launch_cic_scatter<T>(int, int, const Fields16&, T*, cudaStream_t);                        \
     template cudaError_t launch_pass_a<T>(int, int, const Fields16&, const T*, T*, T*, const BiasT<T>*,             \
@@ -696,9 +595,6 @@ cudaError_t launch_reduce(int what, int nblk, int batch, const double* partial, 
     template cudaError_t launch_web_adjoint<T>(int, int, const Fields16&, const T*, const uint16_t*,                \
                                                const BiasT<T>*, const WebParams&, const ChainScalars*,              \
                                                const Fields16&, double*, bool, cudaStream_t, int);                  \
-    template cudaError_t launch_cic_gather<T>(int, int, const T*, const Fields16&, const Fields16&, cudaStream_t);  \
-    template cudaError_t launch_alpt_adjoint<T>(int, int, const T*, const T*, const Fields16&, const Fields16&,     \
-                                                double, double, cudaStream_t);                                      \
     template cudaError_t launch_shift<T>(long long, const T*, T*, T, cudaStream_t);                                 \
     template cudaError_t launch_kick_drift<T>(int, int, T*, T*, const T*, double, double, double*, cudaStream_t);   \
     template cudaError_t launch_lnnbar<T>(long long, int, const T*, const ChainScalars*, T*, cudaStream_t);         \

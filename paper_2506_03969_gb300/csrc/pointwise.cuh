@@ -56,9 +56,6 @@ struct Fields16 { void* p[16]; };
 template <typename T>
 cudaError_t launch_counts_prep(int n, int batch, const int32_t* counts, uint16_t* c16, double* partial, int* err,
                                const RedArgs& ra, cudaStream_t s);
-template <typename T>
-cudaError_t launch_alpt_src(int n, int batch, const Fields16& in7, T* a_out, T* b_out, double growth, double d2,
-                            cudaStream_t s);
 template <typename T> cudaError_t launch_fill(long long count, T* p, T v, cudaStream_t s);
 template <typename T>
 cudaError_t launch_cic_scatter(int n, int batch, const Fields16& psi3, T* delta, cudaStream_t s);
@@ -73,12 +70,6 @@ cudaError_t launch_web_adjoint(int n, int batch, const Fields16& th, const T* de
                                const BiasT<T>* bias, const WebParams& wp, const ChainScalars* sc,
                                const Fields16& out, double* partial, bool bias_grad, cudaStream_t s,
                                int blocks = 0);   // blocks per chain without bias_grad (0: built-in)
-template <typename T>
-cudaError_t launch_cic_gather(int n, int batch, const T* gdelta, const Fields16& psi3, const Fields16& out3,
-                              cudaStream_t s);
-template <typename T>
-cudaError_t launch_alpt_adjoint(int n, int batch, const T* ga, const T* gb, const Fields16& in7,
-                                const Fields16& out7, double growth, double d2, cudaStream_t s);
 template <typename T> cudaError_t launch_shift(long long count, const T* in, T* out, T c, cudaStream_t s);
 template <typename T>
 cudaError_t launch_kick_drift(int n, int batch, T* p, T* nu, const T* g, double ck, double cd, double* partial,
