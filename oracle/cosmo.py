@@ -8,7 +8,8 @@ spherical top hat of radius R = 8 Mpc/h equals sigma8:
     sigma^2(R) = 1/(2 pi^2) * int_0^inf k^2 P(k) W(kR)^2 dk,
     W(x) = 3 (sin x - x cos x) / x^3.
 
-Pins: closed forms for pure power laws n = 0 and n = -2 (tests).
+Pins (tests): sigma^2 closed forms for pure power laws n = -2 and n = -1; the roll-off factor
+exactly 2^-pow at k = kc and the asymptotic slopes ns (k << kc) and ns - 2 pow (k >> kc).
 """
 from __future__ import annotations
 

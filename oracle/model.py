@@ -116,6 +116,22 @@ def delta0_from_nu(nu: torch.Tensor, cfg, g: Optional[Grid] = None) -> torch.Ten
     return g.irfft(torch.sqrt(pk / g.dx ** 3) * g.rfft(nu))
 
 
+def nu_from_delta0(delta0: torch.Tensor, cfg, nu_mean: float = 0.0, g: Optional[Grid] = None) -> torch.Tensor:
+    """Inverse of the white-noise map of App. A on the modes k != 0:
+    DFT(nu)(k) = DFT(delta0)(k) / sqrt(P(k)/dx^3).  P(0) = 0 leaves the k = 0 mode of nu
+    undetermined; it is set so that mean(nu) = nu_mean."""
+    g = g or Grid(cfg.n, cfg.box)
+    amp = amplitude(cfg)
+    pk = torch.tensor(cosmo.power_spectrum(g.kmag.numpy(), amp, cfg.pk_ns, cfg.pk_kc, cfg.pk_pow), dtype=DT)
+    scale = torch.sqrt(pk / g.dx ** 3)
+    inv = torch.zeros_like(scale)
+    nz = scale > 0
+    inv[nz] = 1.0 / scale[nz]
+    nh = g.rfft(delta0) * inv
+    nh[0, 0, 0] = nu_mean * cfg.n ** 3
+    return g.irfft(nh)
+
+
 # ----------------------------------------------------------------------------
 # M_Psi: ALPT (Sect. 2.3) + CIC
 # ----------------------------------------------------------------------------

@@ -70,6 +70,35 @@ def test_amplitude_gives_sigma8():
     assert cosmo.power_spectrum(0.0, A, 0.96, 0.02, 1.5) == 0.0
 
 
+def test_power_spectrum_rolloff_closed_forms():
+    """P(k) = A k^ns / (1 + (k/kc)^2)^pow at pow != 0: at k = kc the roll-off factor is exactly
+    2^-pow; far above kc the logarithmic slope tends to ns - 2 pow, far below it to ns.  A
+    roll-off written as (1 + k/kc)^2 (4^-pow at kc) or with the exponent's sign flipped
+    (2^+pow) fails the first check."""
+    A, ns, kc, pw = 3.7, 0.96, 0.02, 1.5
+    assert abs(float(cosmo.power_spectrum(kc, A, ns, kc, pw)) / (A * kc ** ns * 2.0 ** -pw) - 1) < 1e-14
+    assert abs(float(cosmo.power_spectrum(2 * kc, A, 0.0, kc, 2.0)) - A / 25.0) < 1e-14 * A   # (1 + 4)^-2
+    def slope(k1, k2):
+        p1, p2 = (float(cosmo.power_spectrum(k, A, ns, kc, pw)) for k in (k1, k2))
+        return math.log(p2 / p1) / math.log(k2 / k1)
+    assert abs(slope(1e4 * kc, 2e4 * kc) - (ns - 2 * pw)) < 1e-7
+    assert abs(slope(1e-5 * kc, 2e-5 * kc) - ns) < 1e-8
+
+
+def test_nu_from_delta0_inverts_the_white_noise_map():
+    """The inverse of App. A on k != 0 (Wiener initialisation and test-input construction):
+    round trips through the brute-force-pinned forward map, with the k = 0 mode of nu set by
+    its mean (P(0) = 0 leaves it free)."""
+    cfg = small_cfg(n=16, box=160.0, n_regions=4)
+    nu = torch.tensor(synth.white_noise(16, 21))
+    d0 = model.delta0_from_nu(nu, cfg)
+    back = model.nu_from_delta0(d0, cfg, nu_mean=float(nu.mean()))
+    assert float((back - nu).abs().max()) < 1e-10
+    d = torch.tensor(synth.white_noise(16, 22))
+    d0b = model.delta0_from_nu(model.nu_from_delta0(d, cfg), cfg)
+    assert float((d0b - (d - d.mean())).abs().max()) < 1e-10
+
+
 # ---------------------------------------------------------------------------
 # DFT conventions and spectral operators: brute-force matrix DFT on 4^3
 # ---------------------------------------------------------------------------
@@ -375,6 +404,45 @@ def test_cutoff_special_cases():
     np.testing.assert_allclose(a.numpy(), b.numpy(), rtol=1e-12)
 
 
+def test_first_cutoff_closed_form_away_from_unity():
+    """Eq. local_bias first cut-off at rho = 0.5, eps = 2 (alpha = 0, a = 1): f = exp(-4 u^2).
+    At rho = eps = 1 the forms (u/rho)^eps, u^eps/rho and u/rho^eps coincide; here they give
+    exp(-4 u^2), exp(-2 u^2) and exp(-4 u), so a misplaced exponent fails."""
+    cfg = small_cfg(n=8, box=80.0, n_regions=4)
+    nu = torch.tensor(synth.white_noise(8, 17))
+    fw = model.forward(nu, cfg, model.bias_tables(_uniform_bias(4, alpha=0.0, rho=0.5, eps=2.0)),
+                       n_tracers=64.0, keep=True)
+    u = np.maximum(1.0 + fw["delta"].numpy(), cfg.rho_floor)
+    f = np.exp(-4.0 * u * u)
+    np.testing.assert_allclose(np.exp(fw["ln_nbar"].numpy()), 64.0 * f / f.sum(), rtol=1e-12)
+
+
+def test_parameters_are_interpolated_before_the_bias_law():
+    """Sect. 2.8: each voxel uses b_i = sum_r b^(r) p_i^(r) inside Eq. local_bias (parameters
+    mixed, not the per-region laws).  Two distinct parameter sets -- region 0 (voids) and the
+    other three regions sharing one -- make the mix a single membership p_V = 1 - w1, computed
+    here from the eigenvalues of the oracle's tidal tensor by numpy's eigvalsh at finite
+    sharpness s = 20.  Checked voxel by voxel: rho and eps mixed inside -(u/rho)^eps (alpha = 0,
+    a = 1), and the NB dispersion beta mixed linearly."""
+    cfg = small_cfg(n=8, box=80.0, n_regions=4)
+    nu = torch.tensor(synth.white_noise(8, 12))
+    b = _uniform_bias(4, alpha=0.0)
+    b.rho, b.eps, b.beta = [0.5, 2.0, 2.0, 2.0], [1.0, 3.0, 3.0, 3.0], [5.0, 9.0, 9.0, 9.0]
+    fw = model.forward(nu, cfg, model.bias_tables(b), n_tracers=40.0, keep=True)
+    T = fw["T"].numpy().reshape(6, -1)
+    mats = np.stack([np.array([[t[0], t[1], t[2]], [t[1], t[3], t[4]], [t[2], t[4], t[5]]]) for t in T.T])
+    lam1 = np.linalg.eigvalsh(mats)[:, -1]
+    pv = 1.0 / (1.0 + np.exp(cfg.sharpness * (lam1 - cfg.lambda_th_phi)))
+    assert 20 < np.count_nonzero((pv > 0.1) & (pv < 0.9))      # the mix is exercised
+    u = np.maximum(1.0 + fw["delta"].numpy().ravel(), cfg.rho_floor)
+    rho_i = 0.5 * pv + 2.0 * (1.0 - pv)
+    eps_i = 1.0 * pv + 3.0 * (1.0 - pv)
+    lnf = -(u / rho_i) ** eps_i
+    ln_nbar = math.log(40.0) + lnf - np.log(np.exp(lnf).sum())
+    np.testing.assert_allclose(fw["ln_nbar"].numpy().ravel(), ln_nbar, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(fw["beta"].numpy().ravel(), 5.0 * pv + 9.0 * (1.0 - pv), rtol=1e-12)
+
+
 def test_hard_web_picks_class_parameters():
     """s -> infinity: each voxel uses the parameters of its hard class (row 4*W_phi + W_delta)."""
     cfg = small_cfg(n=8, box=80.0, n_regions=16, sharpness=1e6)
@@ -431,6 +499,22 @@ def test_lognormal_prior_matches_scipy():
     for mu, s in ((0.27, 0.30), (2.12, 0.20)):
         got = model.lognormal_logpdf(torch.tensor(b), mu, s).numpy()
         np.testing.assert_allclose(got, stats.lognorm.logpdf(b, s=s, scale=math.exp(mu)), rtol=1e-12)
+
+
+def test_prior_mask_selects_regions():
+    """Eq. lognormal applies to alpha_r and beta_r of the regions whose bit is set in the prior
+    mask, and to no other entry: bits 1 and 3 give exactly the four scipy log-densities of
+    alpha_1, alpha_3, beta_1, beta_3."""
+    b = synth.bias_phi_web(global_beta=None)
+    b.prior_mask = 0b1010
+    tables = model.bias_tables(b)
+    got = float(model.log_prior_bias(tables, b))
+    a, be = np.array(b.alpha), np.array(b.beta)
+    ref = (stats.lognorm.logpdf(a[[1, 3]], s=b.sigma_alpha, scale=math.exp(b.mu_alpha)).sum()
+           + stats.lognorm.logpdf(be[[1, 3]], s=b.sigma_beta, scale=math.exp(b.mu_beta)).sum())
+    assert abs(got - ref) < 1e-12 * abs(ref)
+    b.prior_mask = 0
+    assert float(model.log_prior_bias(model.bias_tables(b), b)) == 0.0
 
 
 def test_mock_gamma_poisson_moments():
