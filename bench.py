@@ -25,7 +25,6 @@ import hashlib
 import json
 import math
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -79,18 +78,20 @@ def csrc_hash() -> str:
 
 
 def recorded_traffic(kernel: str, alg_bytes_per_launch: float):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current sources.
+    """DRAM bytes per launch from the committed ncu record, if it was taken on the current sources.
 
-    The summary line reads: traffic <kernel> <csrc hash> <dram/algorithmic ratio>; the ratio,
-    measured by ncu on the same workload, times the algorithmic bytes of the timed launch."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    profiles/dram_traffic.json holds, per kernel class, the source hash of the capture and the
+    ratio of DRAM bytes to algorithmic bytes per launch; the ratio times the algorithmic bytes of
+    the timed launch is the traffic.  Records of other sources give None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(path):
         return None
+    with open(path) as f:
+        data = json.load(f)
     cur = csrc_hash()
-    for line in open(path):
-        m = re.match(r"\s*traffic\s+(\S+)\s+(\S+)\s+([0-9.eE+-]+)", line)
-        if m and m.group(1) == kernel and m.group(2) == cur:
-            return float(m.group(3)) * alg_bytes_per_launch
+    for r in data.get("records", []):
+        if r.get("kernel") == kernel and r.get("csrc_hash") == cur:
+            return float(r["dram_over_algorithmic"]) * alg_bytes_per_launch
     return None
 
 
@@ -199,10 +200,16 @@ def run_reference(args):
     total = sum(times)
     scale = (n / 256.0) ** 3
     value = args.steps * scale / total
+    cfg = workload_config(1)
+    cfg.update({"timed_mesh": n, "timed_box_mpc_h": 1000.0 * n / 256.0,
+                "sample": f"each step is one FP64 oracle gradient at {n}^3 (same cell size as 256^3); "
+                          f"value = steps / time x (n/256)^3 = {scale:g}, i.e. 256^3 evaluations per second "
+                          f"if the oracle's cost grows with the voxel count; ms_per_step is the measured "
+                          f"{n}^3 step"})
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps / scale,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(1),
+            "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"each step one FP64 oracle gradient at {n}^3 (same cell size); "
                                        f"throughput scaled to 256^3 by voxel count (x{1/scale:g})"},
@@ -359,7 +366,9 @@ def run_ours(args):
 
 
 def run_extras(pkg, synth, cfg, bias, nu32, counts, args):
-    """Comparators reported beside the headline: FP64 plain path, batched chains, HMC dH."""
+    """Comparators reported beside the headline: FP64 plain path, HMC dH at several step sizes,
+    batched FP32 chains against single FP64 chains at equal dH accuracy, a cuFFT cross-check of
+    the FFT passes, stored vs recomputed ALPT fields, batched and 512^3 throughput."""
     import numpy as np
     import torch
     out = {}
@@ -373,6 +382,9 @@ def run_extras(pkg, synth, cfg, bias, nu32, counts, args):
         torch.cuda.synchronize()
         return (time.perf_counter() - t0) / steps
 
+    def rel(a, b):
+        return float(torch.linalg.vector_norm(a.double() - b.double()) / torch.linalg.vector_norm(b.double()))
+
     # FP64 plain single chain at 256^3
     c64 = pkg.Context(pkg.config_from(cfg, precision=pkg.BRIDGE_FP64, batch=1))
     nu64 = nu32.double()
@@ -381,13 +393,11 @@ def run_extras(pkg, synth, cfg, bias, nu32, counts, args):
     lp64, _, _ = c64.bridge_logpost_grad(nu64, counts, [bias], grad_out=g64, want_bias_grad=False)
     c32 = pkg.Context(pkg.config_from(cfg, batch=1))
     lp32, g32, _ = c32.bridge_logpost_grad(nu32, counts, [bias], want_bias_grad=False)
-    out["fp64_plain_256"] = {"evals_per_s": 1.0 / t,
-                             "fp32_vs_fp64_grad_rel_l2": float(torch.linalg.vector_norm(g32.double() - g64) /
-                                                               torch.linalg.vector_norm(g64)),
+    out["fp64_plain_256"] = {"evals_per_s": 1.0 / t, "fp32_vs_fp64_grad_rel_l2": rel(g32, g64),
                              "fp32_vs_fp64_logpost_rel": abs(lp32[0] - lp64[0]) / abs(lp64[0])}
-    # HMC trajectory at 256^3: 10 leapfrog steps, eps = 0.05, identity mass, FP32 vs FP64 dH.
-    # Data drawn from the model: gamma-Poisson counts (beta = 5) around the FP64 path's nbar at
-    # nu_true (the timing counts only fix N_tr there); the trajectory starts at nu_true.
+
+    # HMC at 256^3: 10 leapfrog steps, identity mass; data drawn from the model (gamma-Poisson,
+    # beta = 5, around the FP64 path's nbar at nu_true); trajectories start at nu_true.
     nu_t = torch.tensor(synth.white_noise(cfg.n, cfg.seed_truth), dtype=torch.float64, device="cuda")
     _, lnnbar = c64.bridge_forward(nu_t, counts, [bias], want_ln_nbar=True)
     gen = torch.Generator(device="cuda")
@@ -395,30 +405,102 @@ def run_extras(pkg, synth, cfg, bias, nu32, counts, args):
     shape = torch.full_like(lnnbar, 5.0)
     rate = torch.exp(lnnbar) * torch._standard_gamma(shape, generator=gen) / 5.0
     counts_m = torch.poisson(rate, generator=gen).clamp_(max=65535).to(torch.int32).contiguous()
+    del shape, rate, lnnbar
     p0 = torch.tensor(synth.momentum(cfg.n, cfg.seed_momentum), dtype=torch.float64, device="cuda")
     hmc = {"data": "gamma-Poisson mock (beta 5) of the model at nu_true, start at nu_true, identity mass",
            "steps": 10}
-    for eps in (0.05, 0.005, 0.0005):
+    eps_star = None
+    for eps in (0.05, 0.005, 5e-4, 1e-4, 5e-5, 2e-5):
         n64, p64 = nu_t.clone(), p0.clone()
-        try:
-            h0a, h1a = c64.bridge_leapfrog(n64, p64, counts_m, [bias], 10, eps)
-            n32, p32 = nu_t.float(), p0.float()
-            t0 = time.perf_counter()
-            h0b, h1b = c32.bridge_leapfrog(n32, p32, counts_m, [bias], 10, eps)
-            torch.cuda.synchronize()
-            tl = time.perf_counter() - t0
-            hmc[f"eps_{eps:g}"] = {
-                "dH_fp64": h1a[0] - h0a[0], "dH_fp32": h1b[0] - h0b[0],
-                "H0_fp64": h0a[0], "H0_fp32_minus_fp64": h0b[0] - h0a[0],
-                "nu_rel_l2_fp32_vs_fp64": float(torch.linalg.vector_norm(n32.double() - n64) /
-                                                torch.linalg.vector_norm(n64)),
-                "p_rel_l2_fp32_vs_fp64": float(torch.linalg.vector_norm(p32.double() - p64) /
-                                               torch.linalg.vector_norm(p64)),
-                "fp32_trajectory_s": tl}
-        except pkg.BridgeError as e:   # a diverged trajectory ends with a non-finite Hamiltonian
-            hmc[f"eps_{eps:g}"] = {"error": str(e)}
+        h0a, h1a = c64.bridge_leapfrog(n64, p64, counts_m, [bias], 10, eps)
+        n32, p32 = nu_t.float(), p0.float()
+        t0 = time.perf_counter()
+        h0b, h1b = c32.bridge_leapfrog(n32, p32, counts_m, [bias], 10, eps)
+        torch.cuda.synchronize()
+        tl = time.perf_counter() - t0
+        d64, d32 = h1a[0] - h0a[0], h1b[0] - h0b[0]
+        rec = {"dH_fp64": d64, "dH_fp32": d32, "abs_dH_fp32_minus_fp64": abs(d32 - d64),
+               "H0_fp64": h0a[0], "H0_fp32_minus_fp64": h0b[0] - h0a[0], "fp32_trajectory_s": tl}
+        if np.isfinite(d64) and np.isfinite(d32):
+            rec["nu_rel_l2_fp32_vs_fp64"] = rel(n32, n64)
+            rec["p_rel_l2_fp32_vs_fp64"] = rel(p32, p64)
+            if eps_star is None and abs(d64) <= 1.0:
+                eps_star = eps
+        else:
+            rec["diverged"] = True
+        hmc[f"eps_{eps:g}"] = rec
+    hmc["eps_dH_order_one"] = eps_star
     out["hmc_256"] = hmc
-    del c64
+
+    # batched FP32 chains against single-chain FP64 at the step size where dH = O(1): four
+    # 256^3 chains (own momenta) advanced together in FP32; each chain again alone in FP64.
+    if eps_star is not None:
+        B = 4
+        p4 = torch.stack([torch.tensor(synth.momentum(cfg.n, cfg.seed_momentum + 10 * b), dtype=torch.float64,
+                                       device="cuda") for b in range(B)])
+        cb4 = pkg.Context(pkg.config_from(cfg, batch=B))
+        nb, pb = nu_t.float().expand(B, -1, -1, -1).contiguous(), p4.float().contiguous()
+        cnt4 = counts_m.expand(B, -1, -1, -1).contiguous()
+        cb4.bridge_leapfrog(nb.clone(), pb.clone(), cnt4, [bias] * B, 10, eps_star)   # graph capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h0b, h1b = cb4.bridge_leapfrog(nb, pb, cnt4, [bias] * B, 10, eps_star)
+        torch.cuda.synchronize()
+        t32 = time.perf_counter() - t0
+        del cb4, cnt4
+        d64s, t64 = [], 0.0
+        for b in range(B):
+            n64, pp64 = nu_t.clone(), p4[b].clone()
+            t0 = time.perf_counter()
+            h0a, h1a = c64.bridge_leapfrog(n64, pp64, counts_m, [bias], 10, eps_star)
+            torch.cuda.synchronize()
+            t64 += time.perf_counter() - t0
+            d64s.append(h1a[0] - h0a[0])
+        d32s = [h1b[b] - h0b[b] for b in range(B)]
+        out["hmc_equal_accuracy_256"] = {
+            "eps": eps_star, "chains": B, "dH_fp64": d64s, "dH_fp32": d32s,
+            "max_abs_dH_fp32_minus_fp64": float(max(abs(a - b) for a, b in zip(d32s, d64s))),
+            "fp32_batched_trajectories_per_s": B / t32, "fp64_single_trajectories_per_s": B / t64,
+            "speedup": (B / t32) / (B / t64),
+            "note": "10 leapfrog steps = 11 gradient evaluations per trajectory; accept/reject uses dH, so equal "
+                    "accuracy means |dH_fp32 - dH_fp64| << 1"}
+    del p0, counts_m, nu_t, c64, nu64, g64
+
+    # FFT cross-check: the library's five FFT pass kernels (r2c + c2r, no operator) against
+    # cuFFT through torch.fft, one 256^3 FP32 field, device-resident
+    x = nu32.reshape(1, -1).contiguous()
+    y = torch.empty_like(x)
+    t_lib = timed(lambda: c32.bridge_fft_roundtrip(x, y), 20)
+    err = rel(y, x)
+    x3 = nu32.reshape(cfg.n, cfg.n, cfg.n)
+    t_cufft = timed(lambda: torch.fft.irfftn(torch.fft.rfftn(x3), s=x3.shape), 20)
+    R = 4.0 * cfg.n ** 3
+    out["fft_crosscheck_256"] = {
+        "library_r2c_c2r_ms": 1e3 * t_lib, "cufft_r2c_c2r_ms": 1e3 * t_cufft, "library_over_cufft": t_lib / t_cufft,
+        "library_roundtrip_rel_l2": err,
+        "library_gbs_at_4R": 4 * R / t_lib / 1e9, "cufft_gbs_at_4R": 4 * R / t_cufft / 1e9,
+        "note": "4R = one real field in and out of each transform; the library's pair is 5 launches (z, y, x, y, z "
+                "passes); cuFFT via torch.fft.rfftn + irfftn includes its own launches and temporaries"}
+    del c32
+
+    # stored vs recomputed ALPT spectra: 256^3 and 512^3
+    rec = {}
+    for tag, cc, b_ in (("256", cfg, bias), ("512", synth.config(4), synth.default_bias(synth.config(4)))):
+        nu_c = nu32 if tag == "256" else torch.tensor(synth.white_noise(cc.n, cc.seed_eval), dtype=torch.float32,
+                                                       device="cuda")
+        cn_c = counts if tag == "256" else torch.tensor(
+            synth.timing_counts(cc.n, cc.seed_counts, cc.mean_tracers, beta=2.0), dtype=torch.int32, device="cuda")
+        gg = torch.empty_like(nu_c)
+        for mode in (False, True):
+            cfg_c = pkg.config_from(cc, batch=1, recompute_alpt=mode)
+            ctx_c = pkg.Context(cfg_c)
+            tt = timed(lambda: ctx_c.bridge_logpost_grad(nu_c, cn_c, [b_], grad_out=gg, want_bias_grad=False), 5)
+            rec[f"{tag}_{'recompute' if mode else 'stored'}"] = {
+                "evals_per_s": 1.0 / tt, "workspace_gb": pkg.lib().bridge_workspace_bytes(cfg_c) / 1e9}
+            del ctx_c
+        del nu_c, cn_c, gg
+    out["alpt_stored_vs_recompute"] = rec
+
     # batched: 16 chains at 128^3 in one launch per pass
     cb = synth.config(3)
     biases = synth.perturbed_biases(synth.default_bias(cb), cb.batch, cb.seed_perturb)

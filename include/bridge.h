@@ -85,6 +85,11 @@ typedef struct {
     int32_t n_regions;       /* 4: Phi-web; 16: Phi x delta web (Sect. 2.7)          */
     double rho_floor;        /* 1 + delta is floored at this value (> 0)             */
     int32_t precision;       /* BRIDGE_FP32, or BRIDGE_FP64 (n <= 256)               */
+    int32_t recompute_alpt;  /* 0: the ALPT spectra (delta0, phi_ij, Psi; Sect. 2.3)
+                                are kept from the forward pass for the adjoint;
+                                1: the adjoint recomputes them from nu (10 fewer
+                                half spectra in the workspace, about 39 R more HBM
+                                traffic per gradient evaluation, R = N^3 floats)   */
 } bridge_config;
 
 /* Bias table of one chain; entries [0, n_regions) are used (Eq. local_bias,
@@ -100,6 +105,17 @@ typedef struct {
     uint32_t prior_mask;               /* bit r: log-normal prior on alpha_r and beta_r */
     double mu_alpha, sigma_alpha;      /* log-normal hyper-parameters          */
     double mu_beta, sigma_beta;
+    /* Free (sampled) bias parameters, whose gradient is returned.  With P free
+     * parameters per kind, bit q of free_mask selects parameter q of the list
+     * alpha_0 .. alpha_{P-1}, beta_0 .. beta_{P-1}.  tie_classes = 0: P =
+     * n_regions, one parameter per table entry.  tie_classes = 1 (16 regions
+     * only): P = 4, and alpha_j (beta_j) shifts the four entries 4j .. 4j+3 of
+     * Phi-web class j together, so its derivative is the sum of theirs --
+     * Sect. 3, Table 2: alpha and beta per Phi-web class, 8 free parameters
+     * with free_mask = 0xFF.  Every chain of a call must use the same
+     * free_mask and tie_classes. */
+    uint32_t free_mask;
+    int32_t tie_classes;
 } bridge_bias;
 
 typedef struct bridge_ctx bridge_ctx;
@@ -142,8 +158,10 @@ int bridge_forward(bridge_ctx* ctx, const void* nu, const int32_t* counts, const
  *   nu, counts, bias   as in bridge_forward
  *   logpost_out        host [B] doubles, may be NULL
  *   grad_nu_out        device [B][N^3] float/double: d log post / d nu; required
- *   grad_bias_out      host [B][2*n_regions] doubles: d/d alpha_r (r < n_regions)
- *                      then d/d beta_r; may be NULL
+ *   grad_bias_out      host [B][popcount(free_mask)] doubles: d log post / d
+ *                      (free bias parameter), in the bit order of
+ *                      bias.free_mask; may be NULL (also not written when
+ *                      free_mask = 0)
  * Synchronises the context stream before returning. */
 int bridge_logpost_grad(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
                         double* logpost_out, void* grad_nu_out, double* grad_bias_out);
@@ -156,6 +174,22 @@ int bridge_logpost_grad_host(bridge_ctx* ctx, const void* nu_host, const int32_t
                              const bridge_bias* bias, double* logpost_out, void* grad_nu_host,
                              double* grad_bias_out);
 
+/* Vector-Jacobian product of the log posterior, the backward pass of reverse-
+ * mode differentiation (Sect. 2.2: the sampler needs the gradient).  Nothing of
+ * an earlier call is reused: the forward model is evaluated again from nu --
+ * the ALPT displacement included -- and then its adjoint, so a forward-only
+ * bridge_forward never pays for the adjoint.
+ *   nu, counts, bias   as in bridge_logpost_grad
+ *   cotangent          host [B] doubles: the upstream derivative c_b of each
+ *                      chain's log posterior (finite); NULL means all ones
+ *   grad_nu_out        device [B][N^3]: c_b d log post_b / d nu_b; required
+ *   grad_bias_out      host [B][popcount(free_mask)]: c_b times the free-
+ *                      parameter gradient; may be NULL
+ * Synchronises the context stream.  Errors as bridge_logpost_grad; EINVAL for
+ * a non-finite cotangent. */
+int bridge_logpost_vjp(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
+                       const double* cotangent, void* grad_nu_out, double* grad_bias_out);
+
 /* HMC leapfrog trajectory (Sect. 2.2), identity mass matrix, U = -log post:
  *   p <- p + eps/2 grad; nu <- nu + eps p; p <- p + eps/2 grad  (n_steps times)
  *   nu, p      device [B][N^3] float/double, updated in place
@@ -163,7 +197,12 @@ int bridge_logpost_grad_host(bridge_ctx* ctx, const void* nu_host, const int32_t
  *   h0_out/h1_out host [B] doubles: H = -log post + 1/2 |p|^2 before/after
  *              (FP64 sums); may be NULL.
  * Performs n_steps + 1 gradient evaluations.  n_steps >= 1, eps finite.
- * Returns ENONFINITE if a Hamiltonian is not finite. */
+ * Chains are independent: the call writes h0 and h1 for every chain.  A chain
+ * whose H0 or H1 is not finite (a diverged trajectory) gets its nu and p back
+ * as they were at the start of the call, and the call returns ENONFINITE after
+ * the whole batch has been integrated; the other chains keep their end points,
+ * so the caller can accept or reject per chain from h0/h1.  On other errors
+ * (EINVAL before any work, ECUDA) the contents of nu and p are unspecified. */
 int bridge_leapfrog(bridge_ctx* ctx, void* nu, void* p, const int32_t* counts, const bridge_bias* bias,
                     int32_t n_steps, double eps, double* h0_out, double* h1_out);
 
@@ -183,6 +222,15 @@ enum {
 };
 int bridge_debug_field(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
                        int32_t which, void* out);
+
+/* The library's 3D real DFT and its inverse, without any operator between them:
+ * out = IDFT(DFT(in)) for every chain, through the same z, y and x pass kernels
+ * that carry every transform of the forward model and its adjoint (App. A
+ * conventions: unnormalised forward DFT, inverse with 1/N^3).  For testing the
+ * transforms and for timing them against a library FFT.
+ *   in, out  device [B][N^3] float/double (per precision); may be the same buffer
+ * Synchronises the context stream.  Errors: EINVAL (NULL, alignment), ECUDA. */
+int bridge_fft_roundtrip(bridge_ctx* ctx, const void* in, void* out);
 
 /* Per-kernel-class timing of later calls on this context: with enable != 0
  * every launch is bracketed by CUDA events recorded on the context stream (a
@@ -253,7 +301,10 @@ int64_t bridge_last_launch_count(const bridge_ctx* ctx);
  *
  * The first call on each device, made with that device current, looks up the
  * array's address (cudaGetSymbolAddress) and uploads the FFT twiddle tables;
- * make that first call outside any stream capture.
+ * make that first call outside any stream capture.  The library remembers
+ * that set-up for the life of the process: after cudaDeviceReset on a device,
+ * whose context then loses the array's contents and the tables, do not call
+ * this entry point on that device again in the same process.
  *
  * Asynchronous: returns once the work is enqueued on `stream`; delta0 is
  * ready, and the scratch free for another stream, when the stream reaches the

@@ -116,6 +116,31 @@ def delta0_from_nu(nu: torch.Tensor, cfg, g: Optional[Grid] = None) -> torch.Ten
     return g.irfft(torch.sqrt(pk / g.dx ** 3) * g.rfft(nu))
 
 
+def delta0_at_cells(nu_np, cfg, cells) -> np.ndarray:
+    """delta0 of App. A at selected cells (flat C-order indices), with the inverse DFT written out
+    cell by cell: delta0(x) = N^-3 sum_k c(kz) Re[delta0_hat(k) exp(2 pi i k.x / N)] over the half
+    spectrum, c = 1 on the kz = 0 and kz = N/2 planes and 2 elsewhere (Hermitian symmetry).
+    For meshes whose full oracle forward model is too large for a test."""
+    n = cfg.n
+    g = Grid(n, cfg.box)
+    amp = amplitude(cfg)
+    pk = torch.tensor(cosmo.power_spectrum(g.kmag.numpy(), amp, cfg.pk_ns, cfg.pk_kc, cfg.pk_pow), dtype=DT)
+    d0h = (torch.sqrt(pk / g.dx ** 3) * g.rfft(torch.tensor(np.asarray(nu_np), dtype=DT))).numpy()
+    c = np.full(n // 2 + 1, 2.0)
+    c[0] = c[n // 2] = 1.0
+    mx = np.arange(n)
+    mz = np.arange(n // 2 + 1)
+    out = []
+    for q in np.asarray(cells).ravel():
+        x, y, z = int(q) // (n * n), (int(q) // n) % n, int(q) % n
+        ez = c * np.exp(2j * math.pi * mz * z / n)
+        ey = np.exp(2j * math.pi * mx * y / n)
+        ex = np.exp(2j * math.pi * mx * x / n)
+        v = ex @ ((d0h @ ez) @ ey)        # sums over kz, then ky, then kx
+        out.append(float(np.real(v)) / n ** 3)
+    return np.array(out)
+
+
 def nu_from_delta0(delta0: torch.Tensor, cfg, nu_mean: float = 0.0, g: Optional[Grid] = None) -> torch.Tensor:
     """Inverse of the white-noise map of App. A on the modes k != 0:
     DFT(nu)(k) = DFT(delta0)(k) / sqrt(P(k)/dx^3).  P(0) = 0 leaves the k = 0 mode of nu

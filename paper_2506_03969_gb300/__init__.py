@@ -7,8 +7,9 @@ is no CPU fallback; if the library is missing or no GB300 is present the calls
 raise.
 
 The C functions keep their names (``bridge_create``, ``bridge_forward``,
-``bridge_logpost_grad``, ``bridge_logpost_grad_host``, ``bridge_leapfrog``,
-``bridge_debug_field``...); ``Context`` wraps them for torch tensors.
+``bridge_logpost_grad``, ``bridge_logpost_vjp``, ``bridge_logpost_grad_host``,
+``bridge_leapfrog``, ``bridge_debug_field``...); ``Context`` wraps them for
+torch tensors.
 """
 from __future__ import annotations
 
@@ -39,7 +40,7 @@ class bridge_config(ctypes.Structure):
                 ("pk_pow", ctypes.c_double), ("growth_d", ctypes.c_double), ("d2_over_d2", ctypes.c_double),
                 ("r_s", ctypes.c_double), ("lambda_th_phi", ctypes.c_double), ("lambda_th_delta", ctypes.c_double),
                 ("sharpness", ctypes.c_double), ("n_regions", ctypes.c_int32), ("rho_floor", ctypes.c_double),
-                ("precision", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("recompute_alpt", ctypes.c_int32)]
 
 
 _D16 = ctypes.c_double * MAX_REGIONS
@@ -53,7 +54,8 @@ class bridge_profile_row(ctypes.Structure):
 class bridge_bias(ctypes.Structure):
     _fields_ = [("a", _D16), ("alpha", _D16), ("rho", _D16), ("eps", _D16), ("rhop", _D16), ("epsp", _D16),
                 ("beta", _D16), ("prior_mask", ctypes.c_uint32), ("mu_alpha", ctypes.c_double),
-                ("sigma_alpha", ctypes.c_double), ("mu_beta", ctypes.c_double), ("sigma_beta", ctypes.c_double)]
+                ("sigma_alpha", ctypes.c_double), ("mu_beta", ctypes.c_double), ("sigma_beta", ctypes.c_double),
+                ("free_mask", ctypes.c_uint32), ("tie_classes", ctypes.c_int32)]
 
 
 _lib = None
@@ -76,6 +78,7 @@ def lib() -> ctypes.CDLL:
     L.bridge_destroy.argtypes = [vp]; L.bridge_destroy.restype = None
     L.bridge_forward.argtypes = [vp, vp, i32p, bp, vp, dp]; L.bridge_forward.restype = ctypes.c_int
     L.bridge_logpost_grad.argtypes = [vp, vp, i32p, bp, dp, vp, dp]; L.bridge_logpost_grad.restype = ctypes.c_int
+    L.bridge_logpost_vjp.argtypes = [vp, vp, i32p, bp, dp, vp, dp]; L.bridge_logpost_vjp.restype = ctypes.c_int
     L.bridge_logpost_grad_host.argtypes = [vp, vp, i32p, bp, dp, vp, dp]
     L.bridge_logpost_grad_host.restype = ctypes.c_int
     L.bridge_leapfrog.argtypes = [vp, vp, vp, i32p, bp, ctypes.c_int32, ctypes.c_double, dp, dp]
@@ -86,6 +89,7 @@ def lib() -> ctypes.CDLL:
     L.bridge_profile_read.argtypes = [vp, ctypes.POINTER(bridge_profile_row), ctypes.c_int]
     L.bridge_profile_read.restype = ctypes.c_int
     L.bridge_autotune.argtypes = [vp, vp, i32p, bp, i32p]; L.bridge_autotune.restype = ctypes.c_int
+    L.bridge_fft_roundtrip.argtypes = [vp, vp, vp]; L.bridge_fft_roundtrip.restype = ctypes.c_int
     L.bridge_delta0_noalloc.argtypes = [cp, vp, vp, vp]; L.bridge_delta0_noalloc.restype = ctypes.c_int
     L.bridge_last_error.argtypes = [vp]; L.bridge_last_error.restype = ctypes.c_char_p
     L.bridge_status_string.argtypes = [ctypes.c_int]; L.bridge_status_string.restype = ctypes.c_char_p
@@ -104,25 +108,32 @@ def make_config(n: int, box: float, batch: int = 1, sigma8: float = 0.8, pk_ns: 
                 pk_pow: float = 1.5, pk_amp: Optional[float] = None, growth_d: float = 1.0,
                 d2_over_d2: float = -3.0 / 7.0, r_s: float = 4.0, lambda_th_phi: float = 0.0,
                 lambda_th_delta: float = 0.0, sharpness: float = 20.0, n_regions: int = 4,
-                rho_floor: float = 1e-6, precision: int = BRIDGE_FP32) -> bridge_config:
+                rho_floor: float = 1e-6, precision: int = BRIDGE_FP32, recompute_alpt: bool = False) -> bridge_config:
     """A bridge_config; the P(k) amplitude is fixed by sigma(8 Mpc/h) = sigma8 unless given."""
     if pk_amp is None:
         pk_amp = bridge_pk_amplitude(sigma8, 8.0, pk_ns, pk_kc, pk_pow)
     return bridge_config(n, batch, box, pk_amp, pk_ns, pk_kc, pk_pow, growth_d, d2_over_d2, r_s, lambda_th_phi,
-                         lambda_th_delta, sharpness, n_regions, rho_floor, precision)
+                         lambda_th_delta, sharpness, n_regions, rho_floor, precision, int(bool(recompute_alpt)))
 
 
-def config_from(cfg, precision: int = BRIDGE_FP32, batch: Optional[int] = None) -> bridge_config:
+def config_from(cfg, precision: int = BRIDGE_FP32, batch: Optional[int] = None,
+                recompute_alpt: bool = False) -> bridge_config:
     """bridge_config from any object with the workload attributes (n, box, sigma8, ...)."""
     return make_config(cfg.n, cfg.box, batch=cfg.batch if batch is None else batch, sigma8=cfg.sigma8,
                        pk_ns=cfg.pk_ns, pk_kc=cfg.pk_kc, pk_pow=cfg.pk_pow, growth_d=cfg.growth_d,
                        d2_over_d2=cfg.d2_over_d2, r_s=cfg.r_s, lambda_th_phi=cfg.lambda_th_phi,
                        lambda_th_delta=cfg.lambda_th_delta, sharpness=cfg.sharpness, n_regions=cfg.n_regions,
-                       rho_floor=cfg.rho_floor, precision=precision)
+                       rho_floor=cfg.rho_floor, precision=precision, recompute_alpt=recompute_alpt)
+
+
+def all_free(n_regions: int) -> int:
+    """free_mask selecting every alpha_r and beta_r entry of an untied table."""
+    return (1 << (2 * n_regions)) - 1
 
 
 def bias_array(biases: Sequence) -> ctypes.Array:
-    """Array of bridge_bias from objects with a, alpha, rho, eps, rhop, epsp, beta lists and prior fields."""
+    """Array of bridge_bias from objects with a, alpha, rho, eps, rhop, epsp, beta lists and prior
+    fields; free_mask / tie_classes default to every alpha_r and beta_r untied."""
     arr = (bridge_bias * len(biases))()
     for i, b in enumerate(biases):
         s = arr[i]
@@ -134,18 +145,15 @@ def bias_array(biases: Sequence) -> ctypes.Array:
         s.prior_mask = int(getattr(b, "prior_mask", 0))
         s.mu_alpha, s.sigma_alpha = float(b.mu_alpha), float(b.sigma_alpha)
         s.mu_beta, s.sigma_beta = float(b.mu_beta), float(b.sigma_beta)
+        fm = getattr(b, "free_mask", None)
+        s.free_mask = all_free(len(list(b.alpha))) if fm is None else int(fm)
+        s.tie_classes = int(getattr(b, "tie_classes", 0))
     return arr
 
 
-def tie_phi_classes(grad_bias: np.ndarray, n_regions: int) -> np.ndarray:
-    """Gradient along the 8 free parameters alpha_j, beta_j of the Phi classes: with
-    16 regions each region (j, k) moves with its class j, so d/d alpha_j = sum_k d/d alpha_jk."""
-    g = np.asarray(grad_bias)
-    if n_regions == 4:
-        return g
-    a = g[..., :16].reshape(*g.shape[:-1], 4, 4).sum(-1)
-    b = g[..., 16:].reshape(*g.shape[:-1], 4, 4).sum(-1)
-    return np.concatenate([a, b], axis=-1)
+def n_free(biases: Sequence) -> int:
+    """Number of free bias parameters per chain (popcount of free_mask)."""
+    return bin(int(bias_array(biases[:1])[0].free_mask)).count("1")
 
 
 # ---------------------------------------------------------------------------
@@ -227,15 +235,35 @@ class Context:
         return np.array(lp[:]), out
 
     def bridge_logpost_grad(self, nu, counts, biases, grad_out=None, want_bias_grad: bool = True):
+        """(log posterior [B], d/d nu, d/d free bias parameters [B][popcount(free_mask)] or None)."""
         torch = self.torch
         self._field(nu, "nu"); self._counts(counts)
         g = grad_out if grad_out is not None else torch.empty_like(nu)
         lp = (ctypes.c_double * self.batch)()
-        gb = (ctypes.c_double * (self.batch * 2 * self.n_regions))() if want_bias_grad else None
+        nf = n_free(biases)
+        gb = (ctypes.c_double * (self.batch * nf))() if want_bias_grad and nf else None
         self._check(lib().bridge_logpost_grad(self.handle, ctypes.c_void_p(_ptr(nu)), ctypes.c_void_p(_ptr(counts)),
                                               bias_array(biases), lp, ctypes.c_void_p(_ptr(g)), gb))
-        gbias = np.array(gb[:]).reshape(self.batch, 2 * self.n_regions) if gb is not None else None
+        gbias = np.array(gb[:]).reshape(self.batch, nf) if gb is not None else None
         return np.array(lp[:]), g, gbias
+
+    def bridge_logpost_vjp(self, nu, counts, biases, cotangent=None, grad_out=None, want_bias_grad: bool = False):
+        """Backward pass: cotangent[b] * d log post_b / d nu (forward model re-evaluated from nu,
+        ALPT included).  Returns (grad, bias gradient or None)."""
+        torch = self.torch
+        self._field(nu, "nu"); self._counts(counts)
+        g = grad_out if grad_out is not None else torch.empty_like(nu)
+        cot = None
+        if cotangent is not None:
+            cv = np.asarray(cotangent, dtype=np.float64).reshape(-1)
+            if cv.size != self.batch:
+                raise ValueError("cotangent must hold one value per chain")
+            cot = (ctypes.c_double * self.batch)(*cv.tolist())
+        nf = n_free(biases)
+        gb = (ctypes.c_double * (self.batch * nf))() if want_bias_grad and nf else None
+        self._check(lib().bridge_logpost_vjp(self.handle, ctypes.c_void_p(_ptr(nu)), ctypes.c_void_p(_ptr(counts)),
+                                             bias_array(biases), cot, ctypes.c_void_p(_ptr(g)), gb))
+        return g, (np.array(gb[:]).reshape(self.batch, nf) if gb is not None else None)
 
     def bridge_logpost_grad_host(self, nu_host, counts_host, biases, grad_host):
         """Host (ideally pinned) torch CPU tensors in and out; copies are part of the call."""
@@ -246,12 +274,16 @@ class Context:
         return np.array(lp[:])
 
     def bridge_leapfrog(self, nu, p, counts, biases, n_steps: int, eps: float):
+        """Leapfrog trajectory in place; returns (H0 [B], H1 [B]).  A chain whose H0 or H1 is not
+        finite comes back with its start state (the library restores it) and its non-finite
+        entries in the returned arrays; other errors raise."""
         self._field(nu, "nu"); self._field(p, "p"); self._counts(counts)
         h0 = (ctypes.c_double * self.batch)()
         h1 = (ctypes.c_double * self.batch)()
-        self._check(lib().bridge_leapfrog(self.handle, ctypes.c_void_p(_ptr(nu)), ctypes.c_void_p(_ptr(p)),
-                                          ctypes.c_void_p(_ptr(counts)), bias_array(biases), int(n_steps), float(eps),
-                                          h0, h1))
+        st = lib().bridge_leapfrog(self.handle, ctypes.c_void_p(_ptr(nu)), ctypes.c_void_p(_ptr(p)),
+                                   ctypes.c_void_p(_ptr(counts)), bias_array(biases), int(n_steps), float(eps), h0, h1)
+        if st != BRIDGE_ENONFINITE:
+            self._check(st)
         return np.array(h0[:]), np.array(h1[:])
 
     def bridge_autotune(self, nu, counts, biases):
@@ -263,6 +295,14 @@ class Context:
         self._check(lib().bridge_autotune(self.handle, ctypes.c_void_p(_ptr(nu)), ctypes.c_void_p(_ptr(counts)),
                                           bias_array(biases), ctypes.cast(ch, ctypes.c_void_p)))
         return [int(v) for v in ch]
+
+    def bridge_fft_roundtrip(self, x, out=None):
+        """IDFT(DFT(x)) through the library's FFT pass kernels (no operator)."""
+        self._field(x, "x")
+        out = out if out is not None else self.torch.empty_like(x)
+        self._field(out, "out")
+        self._check(lib().bridge_fft_roundtrip(self.handle, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(out))))
+        return out
 
     def bridge_debug_field(self, nu, counts, biases, which: int):
         torch = self.torch
@@ -298,23 +338,26 @@ def _make_autograd():
     class LogPosterior(torch.autograd.Function):
         """log posterior(nu) with the hand-written adjoint as backward.
 
-        forward(ctx_obj, nu, counts, biases) -> tensor [B] (float64).  The
-        library evaluates forward and adjoint in one call; the gradient is kept
-        for backward (the ALPT fields are recomputed inside the call, not stored
-        across it)."""
+        forward(ctx_obj, nu, counts, biases) -> tensor [B] (float64) runs the
+        forward model only (bridge_forward).  backward runs bridge_logpost_vjp,
+        which evaluates the forward model again from the saved nu -- the ALPT
+        displacement recomputed, not stored between the two passes -- and then
+        the adjoint, scaled by the incoming gradient of each chain."""
 
         @staticmethod
         def forward(fctx, bctx: Context, nu, counts, biases):
-            lp, g, _ = bctx.bridge_logpost_grad(nu.detach().contiguous(), counts, biases, want_bias_grad=False)
-            fctx.save_for_backward(g)
+            x = nu.detach().contiguous()
+            lp, _ = bctx.bridge_forward(x, counts, biases)
+            fctx.bctx, fctx.biases = bctx, biases
+            fctx.save_for_backward(x, counts)
             return torch.tensor(lp, dtype=torch.float64, device=nu.device)
 
         @staticmethod
         def backward(fctx, grad_out):
-            (g,) = fctx.saved_tensors
-            b = grad_out.numel()
-            scaled = g.reshape(b, -1) * grad_out.to(g.dtype).reshape(b, 1)
-            return None, scaled.reshape(g.shape), None, None
+            x, counts = fctx.saved_tensors
+            cot = grad_out.detach().to(torch.float64).reshape(-1).cpu().numpy()
+            g, _ = fctx.bctx.bridge_logpost_vjp(x, counts, fctx.biases, cotangent=cot)
+            return None, g.reshape(x.shape), None, None
 
     return LogPosterior
 

@@ -18,11 +18,16 @@ using namespace bridge;
 
 namespace {
 
-// Spectral buffers: 19 scratch (peak use: adjoint y merge 13 -> 6) and the
-// spectra kept from the forward pass for the nodes that recompute real fields
-// in the adjoint: linear field and potential Hessian (7), displacement (3),
-// tidal tensor and density Hessian (12).
-enum { SP_SCR = 0, SP_ALPT = 19, SP_PSI = 26, SP_TH = 29, kMaxSpec = 41 };
+// Spectral buffers: 19 scratch slots (peak use: adjoint y merge 13 -> 6).  The
+// tidal tensor and density Hessian spectra (12) exist only inside the forward
+// pass and use scratch slots 7..18.  The ALPT spectra -- linear field and
+// potential Hessian (7), displacement (3) -- feed the adjoint's fused nodes:
+// by default they have slots of their own (19..28) and survive from the
+// forward pass to the adjoint; with recompute_alpt they are recomputed from nu
+// inside the adjoint into scratch slots 7..13 and 14..16, and the workspace
+// holds 19 spectra instead of 29.
+enum { SP_SCR = 0, SP_TH = 7, SP_ALPT_STORED = 19, SP_PSI_STORED = 26, kMaxSpec = 29,
+       SP_ALPT_RECOMP = 7, SP_PSI_RECOMP = 14, kScratchSpec = 19 };
 // Real buffers.
 enum {
     RB_DELTA = 0,   // 1: CIC mass rho = 1 + delta
@@ -32,6 +37,8 @@ enum {
     RB_SCR = 16,    // 13: adjoint fields of the web stage; scratch for inspection fields
     kMaxReal = 29
 };
+// Extra real fields after the named ones: leapfrog gradient, snapshots of nu and p.
+enum { kExtraReal = 3 };
 
 Term mk(int src, int dst, int px, int py, int pz, RCode rc, double cre, double cim = 0.0) {
     Term t;
@@ -49,6 +56,8 @@ struct bridge_ctx {
     std::string err;
     int64_t launches = 0;
     int n = 0, B = 0, nr = 4;
+    int sp_alpt = SP_ALPT_STORED, sp_psi = SP_PSI_STORED;   // ALPT spectrum slots (recompute_alpt moves them)
+    bool recompute = false;
     long long nvox = 0, nspec = 0;
     size_t esz = 4;
     // workspace
@@ -64,6 +73,10 @@ struct bridge_ctx {
     int* errflag = nullptr;
     int* tickets = nullptr;     // [B] counters of the fused partial-sum reductions (zero between launches)
     void* grad_tmp = nullptr;   // gradient scratch for leapfrog
+    void* snap_nu = nullptr;    // leapfrog start state, restored for chains whose Hamiltonian is not finite
+    void* snap_p = nullptr;
+    double* cot = nullptr;      // [B] cotangents of bridge_logpost_vjp (device)
+    double* cot_host = nullptr; // pinned staging of cot
     void* node_scratch = nullptr;  // per-CTA slabs of the fused nodes
     size_t node_cap = 0;           // bytes of node_scratch
     // launch choices (bridge_autotune; 0 = built-in): CTAs per SM of the ALPT,
@@ -162,6 +175,7 @@ int validate(const bridge_config* c, std::string* why) {
     if (!(c->rho_floor > 0) || !(c->rho_floor < 1)) return bad("rho_floor must be in (0, 1)");
     if (c->precision != BRIDGE_FP32 && c->precision != BRIDGE_FP64) return bad("precision must be FP32 or FP64");
     if (c->precision == BRIDGE_FP64 && c->n > 256) return bad("the FP64 path supports n <= 256");
+    if (c->recompute_alpt != 0 && c->recompute_alpt != 1) return bad("recompute_alpt must be 0 or 1");
     return BRIDGE_OK;
 }
 
@@ -179,6 +193,14 @@ int validate_bias(const bridge_ctx* ctx, const bridge_bias* b, std::string* why)
             }
         }
         if (x.prior_mask & ~((ctx->nr == 16) ? 0xFFFFu : 0xFu)) { *why = "prior_mask has bits beyond n_regions"; return BRIDGE_EINVAL; }
+        if (x.tie_classes != 0 && x.tie_classes != 1) { *why = "tie_classes must be 0 or 1"; return BRIDGE_EINVAL; }
+        if (x.tie_classes && ctx->nr != 16) { *why = "tie_classes needs 16 regions"; return BRIDGE_EINVAL; }
+        const int np = x.tie_classes ? 4 : ctx->nr;
+        if (np < 16 && (x.free_mask >> (2 * np)) != 0u) { *why = "free_mask has bits beyond 2 x (free parameters per kind)"; return BRIDGE_EINVAL; }
+        if (x.free_mask != b[0].free_mask || x.tie_classes != b[0].tie_classes) {
+            *why = "free_mask and tie_classes must be the same for every chain of a call";
+            return BRIDGE_EINVAL;
+        }
         if (x.prior_mask) {
             for (int r = 0; r < ctx->nr; ++r)
                 if (((x.prior_mask >> r) & 1u) && !(x.alpha[r] > 0)) { *why = "log-normal prior needs alpha > 0"; return BRIDGE_EINVAL; }
@@ -190,7 +212,7 @@ int validate_bias(const bridge_ctx* ctx, const bridge_bias* b, std::string* why)
 
 struct Plan {
     size_t spec_bytes, real_bytes, c16_bytes, partial_bytes, sc_bytes, biasd_bytes, biast_bytes, node_bytes, rtab_bytes,
-        total;
+        cot_bytes, total;
     int nspec_buf, nreal_buf;
 };
 
@@ -201,7 +223,7 @@ Plan make_plan(const bridge_config* c) {
     const long long n = c->n, B = c->batch;
     const size_t esz = c->precision == BRIDGE_FP64 ? 8 : 4;
     const long long nvox = n * n * n, nspec = (n / 2 + 1) * n * n;
-    p.nspec_buf = kMaxSpec;
+    p.nspec_buf = c->recompute_alpt ? kScratchSpec : kMaxSpec;
     p.nreal_buf = kMaxReal;
     p.spec_bytes = align_up(size_t(nspec) * 2 * esz * B);
     p.real_bytes = align_up(size_t(nvox) * esz * B);
@@ -214,8 +236,9 @@ Plan make_plan(const bridge_config* c) {
     p.biast_bytes = align_up(sizeof(BiasT<double>) * B);
     p.node_bytes = align_up(size_t(BRIDGE_NODE_L2_MB + 8) << 20);   // fused-node slabs (the launcher keeps them below the budget)
     p.rtab_bytes = align_up(size_t(4) * (3 * (n / 2) * (n / 2) + 1) * esz);
-    p.total = p.spec_bytes * p.nspec_buf + p.real_bytes * (p.nreal_buf + 1) + p.c16_bytes + p.partial_bytes +
-              p.sc_bytes + p.biasd_bytes + p.biast_bytes + p.node_bytes + p.rtab_bytes + 256;
+    p.cot_bytes = align_up(sizeof(double) * B);
+    p.total = p.spec_bytes * p.nspec_buf + p.real_bytes * (p.nreal_buf + kExtraReal) + p.c16_bytes + p.partial_bytes +
+              p.sc_bytes + p.biasd_bytes + p.biast_bytes + p.node_bytes + p.rtab_bytes + p.cot_bytes + 256;
     return p;
 }
 
@@ -309,14 +332,12 @@ template <typename T> int node(bridge_ctx* ctx, NodeArgs& na, const char* name, 
 }
 
 // ---------------------------------------------------------------------------
-// Forward model.  Leaves in the workspace: the ALPT, displacement and tensor
-// spectra, rho, ln f and beta_i, and the scalars (ntr, sumf, lnC, loglik, G,
-// logpost).  nu: device [B][N^3].
+// M_delta and the ALPT displacement (App. A, Sect. 2.3): nu -> the spectra of
+// delta0 and phi_ij (slots sp_alpt..+6) and of Psi in cell units (sp_psi..+2),
+// in the [kz][y][x] layout of the z pass.  Uses scratch slots 0..4.
 // ---------------------------------------------------------------------------
-template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelihood) {
+template <typename T> int run_alpt(bridge_ctx* ctx, const T* nu) {
     const double invn3 = 1.0 / double(ctx->nvox);
-    const bool hier = ctx->nr == 16;
-    const int nth = nth_of(ctx);
     // M_delta (App. A) and the linear potential Hessian: nu -> delta0, phi_ij spectra
     RUN(z_fwd<T>(ctx, {nu}, {ctx->spec[SP_SCR]}));
     RUN(y_identity<T>(ctx, SP_SCR, 1, true));
@@ -330,7 +351,7 @@ template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelih
         CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
     {
-        PassProgram p = program(cspec<T>(ctx, SP_SCR + 1, 4), mspec<T>(ctx, SP_ALPT, 7), ctx->nspec);
+        PassProgram p = program(cspec<T>(ctx, SP_SCR + 1, 4), mspec<T>(ctx, ctx->sp_alpt, 7), ctx->nspec);
         add_expand(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));    // delta0
         add_expand(p, mk(1, 1, 0, 0, 0, R_ONE, 1.0));    // phi_xx
         add_expand(p, mk(2, 2, 0, 1, 0, R_ONE, 1.0));    // phi_xy
@@ -344,7 +365,7 @@ template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelih
     {
         NodeArgs na{};
         na.kind = NODE_ALPT_FWD;
-        for (int f = 0; f < 7; ++f) na.spec_in[f] = ctx->spec[SP_ALPT + f];
+        for (int f = 0; f < 7; ++f) na.spec_in[f] = ctx->spec[ctx->sp_alpt + f];
         na.spec_out[0] = ctx->spec[SP_SCR];
         na.spec_out[1] = ctx->spec[SP_SCR + 1];
         RUN(node<T>(ctx, na, "node_alpt", 9 * sby<T>(ctx), nullptr));
@@ -360,15 +381,28 @@ template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelih
         CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
     {
-        PassProgram p = program(cspec<T>(ctx, SP_SCR + 2, 2), mspec<T>(ctx, SP_PSI, 3), ctx->nspec);
+        PassProgram p = program(cspec<T>(ctx, SP_SCR + 2, 2), mspec<T>(ctx, ctx->sp_psi, 3), ctx->nspec);
         add_expand(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));
         add_expand(p, mk(1, 1, 0, 1, 0, R_ONE, 1.0));
         add_expand(p, mk(1, 2, 0, 0, 1, R_ONE, 1.0));
         CKL("y_inv", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_inv<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
+    return BRIDGE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Forward model.  Leaves in the workspace: the ALPT and displacement spectra
+// (unless recompute_alpt), rho, the tensors in real space, ln f and beta_i,
+// and the scalars (ntr, sumf, lnC, loglik, G, logpost).  nu: device [B][N^3].
+// ---------------------------------------------------------------------------
+template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelihood) {
+    const double invn3 = 1.0 / double(ctx->nvox);
+    const bool hier = ctx->nr == 16;
+    const int nth = nth_of(ctx);
+    RUN(run_alpt<T>(ctx, nu));
     // CIC (mass rho accumulated into a zeroed field); the displacement in real
     // space borrows the tensor buffers, which are written only afterwards
-    RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_PSI, 3), mreal(ctx, RB_TH, 3)));
+    RUN(z_inv<T>(ctx, cspec<T>(ctx, ctx->sp_psi, 3), mreal(ctx, RB_TH, 3)));
     CKL("fill", rby<T>(ctx), launch_fill<T>(ctx->nvox * ctx->B, RB<T>(ctx, RB_DELTA), T(0), ctx->stream));
     CKL("cic_scatter", 4 * rby<T>(ctx), launch_cic_scatter<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 3), RB<T>(ctx, RB_DELTA), ctx->stream));
     // tidal tensor and density Hessian spectra (Sect. 2.8, App. B)
@@ -462,12 +496,15 @@ template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad, boo
     }
     RUN(y_identity<T>(ctx, SP_SCR, 1, false));
     RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_SCR, 1), mreal(ctx, RB_GD, 1)));       // g_rho (total)
+    // recompute_alpt: the ALPT and displacement spectra again from nu (every
+    // scratch spectrum is free here; g_rho is a real field)
+    if (ctx->recompute) RUN(run_alpt<T>(ctx, nu));
     // CIC adjoint with the displacement recomputed from its spectra, then r2c
     {
         NodeArgs na{};
         na.kind = NODE_GATHER;
         for (int f = 0; f < 3; ++f) {
-            na.spec_in[f] = ctx->spec[SP_PSI + f];
+            na.spec_in[f] = ctx->spec[ctx->sp_psi + f];
             na.spec_out[f] = ctx->spec[SP_SCR + f];
         }
         na.real_in[0] = ctx->real[RB_GD];
@@ -494,7 +531,7 @@ template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad, boo
     {
         NodeArgs na{};
         na.kind = NODE_ALPT_ADJ;
-        for (int f = 0; f < 7; ++f) na.spec_in[f] = ctx->spec[SP_ALPT + f];
+        for (int f = 0; f < 7; ++f) na.spec_in[f] = ctx->spec[ctx->sp_alpt + f];
         na.spec_in[7] = ctx->spec[SP_SCR + 5];
         na.spec_in[8] = ctx->spec[SP_SCR + 6];
         for (int f = 0; f < 7; ++f) na.spec_out[f] = ctx->spec[SP_SCR + f];
@@ -653,21 +690,61 @@ template <typename T> int eval_graph(bridge_ctx* ctx, const T* nu, const int32_t
     return BRIDGE_OK;
 }
 
+// Gradient with respect to the free bias parameters of chain c (G12 reading):
+// parameter p of alpha_0..alpha_{P-1}, beta_0..beta_{P-1} in bit order of
+// free_mask; with tie_classes, alpha_j / beta_j move the four table entries
+// 4j..4j+3 of Phi class j together, so their derivative is the sum over the four.
+int pack_bias_grad(const bridge_ctx* ctx, const bridge_bias& b, const double* full, double* out) {
+    const int np = b.tie_classes ? 4 : ctx->nr;
+    int k = 0;
+    for (int q = 0; q < 2 * np; ++q) {
+        if (!((b.free_mask >> q) & 1u)) continue;
+        const int kind = q / np, j = q % np;   // kind 0: alpha, 1: beta
+        double v = 0.0;
+        if (b.tie_classes)
+            for (int i = 0; i < 4; ++i) v += full[kind * ctx->nr + 4 * j + i];
+        else
+            v = full[kind * ctx->nr + j];
+        out[k++] = v;
+    }
+    return k;
+}
+
 template <typename T> int do_grad(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
-                                  double* logpost_out, void* grad, double* gbias_out) {
+                                  double* logpost_out, void* grad, double* gbias_out, const double* cot = nullptr) {
     if (!nu || !grad) return fail(ctx, BRIDGE_EINVAL, "nu and grad_nu_out are required");
     if (!counts) return fail(ctx, BRIDGE_EINVAL, "counts is NULL");
     RUN(upload_bias<T>(ctx, bias));
     const T* nuT = reinterpret_cast<const T*>(nu);
     T* gT = reinterpret_cast<T*>(grad);
-    if (ctx->prof) RUN(eval_body<T>(ctx, nuT, counts, gT, gbias_out != nullptr));   // per-launch events need direct launches
-    else RUN(eval_graph<T>(ctx, nuT, counts, gT, gbias_out != nullptr));
+    const bool want_bias = gbias_out != nullptr && bias[0].free_mask != 0u;
+    if (ctx->prof) RUN(eval_body<T>(ctx, nuT, counts, gT, want_bias));   // per-launch events need direct launches
+    else RUN(eval_graph<T>(ctx, nuT, counts, gT, want_bias));
+    bool scale = false;
+    if (cot) {
+        for (int c = 0; c < ctx->B; ++c) {
+            if (!std::isfinite(cot[c])) return fail(ctx, BRIDGE_EINVAL, "cotangent is not finite");
+            ctx->cot_host[c] = cot[c];
+            scale = scale || cot[c] != 1.0;
+        }
+    }
+    if (scale) {
+        CK(cudaMemcpyAsync(ctx->cot, ctx->cot_host, sizeof(double) * ctx->B, cudaMemcpyHostToDevice, ctx->stream));
+        CKL("scale", 2 * rby<T>(ctx), launch_scale_chains<T>(ctx->n, ctx->B, gT, ctx->cot, ctx->stream));
+    }
     RUN(finish(ctx));
     for (int c = 0; c < ctx->B; ++c) {
         if (!std::isfinite(ctx->sc_host[c].logpost)) return fail(ctx, BRIDGE_ENONFINITE, "log posterior is not finite");
         if (logpost_out) logpost_out[c] = ctx->sc_host[c].logpost;
-        if (gbias_out)
-            for (int k = 0; k < 2 * ctx->nr; ++k) gbias_out[c * 2 * ctx->nr + k] = ctx->sc_host[c].gbias[k];
+    }
+    if (want_bias) {
+        const int nf = __builtin_popcount(bias[0].free_mask);
+        for (int c = 0; c < ctx->B; ++c) {
+            double* o = gbias_out + size_t(c) * nf;
+            pack_bias_grad(ctx, bias[c], ctx->sc_host[c].gbias, o);
+            if (cot)
+                for (int k = 0; k < nf; ++k) o[k] *= cot[c];
+        }
     }
     return BRIDGE_OK;
 }
@@ -724,6 +801,10 @@ template <typename T> int do_leapfrog(bridge_ctx* ctx, void* nu_v, void* p_v, co
     T* g = reinterpret_cast<T*>(ctx->grad_tmp);
     RUN(upload_bias<T>(ctx, bias));
     RUN(prep_counts<T>(ctx, counts));
+    // start state, put back for every chain whose Hamiltonian is not finite
+    const size_t fb = size_t(ctx->nvox) * ctx->B * sizeof(T);
+    CK(cudaMemcpyAsync(ctx->snap_nu, nu, fb, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->snap_p, p, fb, cudaMemcpyDeviceToDevice, ctx->stream));
     std::vector<double> u0(ctx->B), k0(ctx->B);
     // initial potential and kinetic energy
     RUN(run_forward<T>(ctx, nu, true));
@@ -745,12 +826,25 @@ template <typename T> int do_leapfrog(bridge_ctx* ctx, void* nu_v, void* p_v, co
     CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, 0.5 * eps, 0.0, ctx->partial, ctx->stream));
     CKL("reduce", 0.0, launch_reduce(RED_P2, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
     RUN(finish(ctx));
+    int bad = 0;
+    const size_t one = size_t(ctx->nvox) * sizeof(T);
     for (int c = 0; c < ctx->B; ++c) {
         const double H0 = u0[c] + k0[c];
         const double H1 = -ctx->sc_host[c].logpost + 0.5 * ctx->sc_host[c].sump2;
-        if (!std::isfinite(H0) || !std::isfinite(H1)) return fail(ctx, BRIDGE_ENONFINITE, "Hamiltonian is not finite");
         if (h0) h0[c] = H0;
         if (h1) h1[c] = H1;
+        if (!std::isfinite(H0) || !std::isfinite(H1)) {
+            ++bad;
+            CK(cudaMemcpyAsync(reinterpret_cast<char*>(nu_v) + c * one, reinterpret_cast<const char*>(ctx->snap_nu) + c * one,
+                               one, cudaMemcpyDeviceToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(reinterpret_cast<char*>(p_v) + c * one, reinterpret_cast<const char*>(ctx->snap_p) + c * one,
+                               one, cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+    }
+    if (bad) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        return fail(ctx, BRIDGE_ENONFINITE, "Hamiltonian is not finite for " + std::to_string(bad) + " of " +
+                                                std::to_string(ctx->B) + " chains (their nu and p are restored)");
     }
     return BRIDGE_OK;
 }
@@ -774,11 +868,13 @@ template <typename T> int do_debug(bridge_ctx* ctx, const void* nu, const int32_
     (void)fb;
     switch (which) {
         case BRIDGE_FIELD_DELTA0:
-            RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_ALPT, 1), mreal(ctx, RB_SCR, 1)));
+            if (ctx->recompute) RUN(run_alpt<T>(ctx, reinterpret_cast<const T*>(nu)));   // slots reused after the ALPT stage
+            RUN(z_inv<T>(ctx, cspec<T>(ctx, ctx->sp_alpt, 1), mreal(ctx, RB_SCR, 1)));
             RUN(copy_fields(RB_SCR, 1));
             break;
         case BRIDGE_FIELD_PSI:
-            RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_PSI, 3), mreal(ctx, RB_SCR, 3)));
+            if (ctx->recompute) RUN(run_alpt<T>(ctx, reinterpret_cast<const T*>(nu)));
+            RUN(z_inv<T>(ctx, cspec<T>(ctx, ctx->sp_psi, 3), mreal(ctx, RB_SCR, 3)));
             RUN(copy_fields(RB_SCR, 3));
             break;
         case BRIDGE_FIELD_DELTA:
@@ -801,6 +897,26 @@ template <typename T> int do_debug(bridge_ctx* ctx, const void* nu, const int32_
         default: return fail(ctx, BRIDGE_EINVAL, "unknown field selector");
     }
     return finish(ctx);
+}
+
+// out = IDFT(DFT(in)) through the five pass kernels with the identity operator:
+// z forward, y forward, x node (forward x DFT, 1/N^3, inverse x DFT), y
+// inverse, z inverse -- the transforms of every other program without an
+// operator, for testing them and timing them against a library FFT.
+template <typename T> int do_fft_roundtrip(bridge_ctx* ctx, const void* in, void* out) {
+    if (!in || !out) return fail(ctx, BRIDGE_EINVAL, "in and out are required");
+    RUN(z_fwd<T>(ctx, {in}, {ctx->spec[SP_SCR]}));
+    RUN(y_identity<T>(ctx, SP_SCR, 1, true));
+    {
+        PassProgram p = program(cspec<T>(ctx, SP_SCR, 1), mspec<T>(ctx, SP_SCR + 1, 1), ctx->nspec);
+        add_merge(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0 / double(ctx->nvox)));
+        add_expand(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));
+        CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+    }
+    RUN(y_identity<T>(ctx, SP_SCR + 1, 1, false));
+    RUN(z_inv<T>(ctx, {ctx->spec[SP_SCR + 1]}, {out}));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return BRIDGE_OK;
 }
 
 // Simpson in ln k of k^3 P(k) W(kR)^2 / (2 pi^2).
@@ -970,6 +1086,9 @@ int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
     ctx->nvox = (long long)cfg->n * cfg->n * cfg->n;
     ctx->nspec = (long long)(cfg->n / 2 + 1) * cfg->n * cfg->n;
     ctx->esz = cfg->precision == BRIDGE_FP64 ? 8 : 4;
+    ctx->recompute = cfg->recompute_alpt != 0;
+    ctx->sp_alpt = ctx->recompute ? SP_ALPT_RECOMP : SP_ALPT_STORED;
+    ctx->sp_psi = ctx->recompute ? SP_PSI_RECOMP : SP_PSI_STORED;
     ctx->kp.kf = 2.0 * kPi / cfg->box;
     ctx->kp.inv_kf2 = 1.0 / (ctx->kp.kf * ctx->kp.kf);
     ctx->kp.dx = cfg->box / cfg->n;
@@ -998,6 +1117,8 @@ int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
     for (int i = 0; i < pl.nspec_buf; ++i) { ctx->spec[i] = w; w += pl.spec_bytes; }
     for (int i = 0; i < pl.nreal_buf; ++i) { ctx->real[i] = w; w += pl.real_bytes; }
     ctx->grad_tmp = w; w += pl.real_bytes;
+    ctx->snap_nu = w; w += pl.real_bytes;
+    ctx->snap_p = w; w += pl.real_bytes;
     ctx->c16 = reinterpret_cast<uint16_t*>(w); w += pl.c16_bytes;
     ctx->partial = reinterpret_cast<double*>(w); w += pl.partial_bytes;
     ctx->sc = reinterpret_cast<ChainScalars*>(w); w += pl.sc_bytes;
@@ -1006,6 +1127,7 @@ int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
     ctx->node_scratch = w; w += pl.node_bytes;
     ctx->node_cap = pl.node_bytes;
     ctx->rtab = w; w += pl.rtab_bytes;
+    ctx->cot = reinterpret_cast<double*>(w); w += pl.cot_bytes;
     {
         const int rlen = 3 * (cfg->n / 2) * (cfg->n / 2) + 1;
         std::vector<double> tab(size_t(4) * rlen);
@@ -1036,7 +1158,8 @@ int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
         cudaMallocHost(&ctx->sc_host, sizeof(ChainScalars) * ctx->B) != cudaSuccess ||
         cudaMallocHost(&ctx->biasd_host, sizeof(BiasD) * ctx->B) != cudaSuccess ||
         cudaMallocHost(&ctx->biast_host, sizeof(BiasT<double>) * ctx->B) != cudaSuccess ||
-        cudaMallocHost(&ctx->errflag_host, sizeof(int)) != cudaSuccess) {
+        cudaMallocHost(&ctx->errflag_host, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&ctx->cot_host, sizeof(double) * ctx->B) != cudaSuccess) {
         cudaGetLastError();
         return create_fail(ctx, BRIDGE_ENOMEM, "small device or pinned host buffers");
     }
@@ -1057,6 +1180,7 @@ void bridge_destroy(bridge_ctx* ctx) {
     if (ctx->biasd_host) cudaFreeHost(ctx->biasd_host);
     if (ctx->biast_host) cudaFreeHost(ctx->biast_host);
     if (ctx->errflag_host) cudaFreeHost(ctx->errflag_host);
+    if (ctx->cot_host) cudaFreeHost(ctx->cot_host);
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->eexec) cudaGraphExecDestroy(ctx->eexec);
@@ -1106,6 +1230,15 @@ int bridge_logpost_grad_host(bridge_ctx* ctx, const void* nu_host, const int32_t
     return BRIDGE_OK;
 }
 
+int bridge_logpost_vjp(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
+                       const double* cotangent, void* grad_nu_out, double* grad_bias_out) {
+    if (!ctx) return BRIDGE_EINVAL;
+    ctx->launches = 0;
+    ctx->err.clear();
+    if (!aligned16({nu, counts, grad_nu_out})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
+    return DISPATCH(ctx, do_grad, nu, counts, bias, nullptr, grad_nu_out, grad_bias_out, cotangent);
+}
+
 int bridge_leapfrog(bridge_ctx* ctx, void* nu, void* p, const int32_t* counts, const bridge_bias* bias, int32_t n_steps,
                     double eps, double* h0_out, double* h1_out) {
     if (!ctx) return BRIDGE_EINVAL;
@@ -1122,6 +1255,14 @@ int bridge_debug_field(bridge_ctx* ctx, const void* nu, const int32_t* counts, c
     ctx->err.clear();
     if (!aligned16({nu, counts, out})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
     return DISPATCH(ctx, do_debug, nu, counts, bias, which, out);
+}
+
+int bridge_fft_roundtrip(bridge_ctx* ctx, const void* in, void* out) {
+    if (!ctx) return BRIDGE_EINVAL;
+    ctx->launches = 0;
+    ctx->err.clear();
+    if (!aligned16({in, out})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
+    return DISPATCH(ctx, do_fft_roundtrip, in, out);
 }
 
 int bridge_autotune(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,

@@ -52,8 +52,12 @@ class Bias:
 
     Eq. local_bias parameters a (amplitude), alpha, rho, eps (first cut-off),
     rhop, epsp (second cut-off) and the NB dispersion beta (Sect. 2.6), plus the
-    log-normal prior hyper-parameters (Eq. lognormal) and the set of regions the
-    prior applies to.
+    log-normal prior hyper-parameters (Eq. lognormal), the set of regions the
+    prior applies to, and the free (sampled) parameters: bit q of ``free_mask``
+    selects parameter q of alpha_0..alpha_{P-1}, beta_0..beta_{P-1}, with P =
+    n_regions, or P = 4 Phi-web classes when ``tie_classes`` is set (16-region
+    tables, whose four delta-web entries per Phi class then move together;
+    ``None`` means every entry, untied).
     """
     a: List[float]
     alpha: List[float]
@@ -67,6 +71,8 @@ class Bias:
     sigma_alpha: float = PRIOR_SIGMA_ALPHA
     mu_beta: float = PRIOR_MU_BETA
     sigma_beta: float = PRIOR_SIGMA_BETA
+    free_mask: Optional[int] = None
+    tie_classes: int = 0
 
     @property
     def n_regions(self) -> int:
@@ -120,16 +126,18 @@ def bias_phi_web(alpha=TABLE2_TEST1_ALPHA, beta=None, global_beta: Optional[floa
     if beta is None:
         beta = [global_beta] * 4 if global_beta is not None else list(TABLE2_TEST1_BETA)
     return Bias(a=[1.0] * 4, alpha=list(alpha), rho=[d[3] for d in diag], eps=[d[2] for d in diag],
-                rhop=[0.0] * 4, epsp=[1.0] * 4, beta=list(beta), prior_mask=0xF)
+                rhop=[0.0] * 4, epsp=[1.0] * 4, beta=list(beta), prior_mask=0xF, free_mask=0xFF)
 
 
 def bias_hierarchical(global_beta: Optional[float] = None) -> Bias:
     """16-region (Phi x delta web) table from Table 3 (TEST3); rho' = 0, eps' = 1
-    as in Sect. 3 so the second cut-off factor is one."""
+    as in Sect. 3 so the second cut-off factor is one.  Free parameters: alpha_j
+    and beta_j of the four Phi-web classes, each shared by its four delta-web
+    sub-classes (8 free parameters, Table 2)."""
     t = TABLE3_TEST3
     beta = [r[1] for r in t] if global_beta is None else [global_beta] * 16
     return Bias(a=[1.0] * 16, alpha=[r[0] for r in t], rho=[r[3] for r in t], eps=[r[2] for r in t],
-                rhop=[0.0] * 16, epsp=[1.0] * 16, beta=beta, prior_mask=0xFFFF)
+                rhop=[0.0] * 16, epsp=[1.0] * 16, beta=beta, prior_mask=0xFFFF, free_mask=0xFF, tie_classes=1)
 
 
 def config(i: int) -> Config:

@@ -47,7 +47,8 @@ def test_validate_config(pkg):
     assert pkg.lib().bridge_validate_config(ctypes.byref(good)) == pkg.BRIDGE_OK
     assert pkg.lib().bridge_workspace_bytes(ctypes.byref(good)) > 0
     for field, value in (("n", 48), ("n", 8), ("n", 1024), ("batch", 0), ("box", -1.0), ("n_regions", 5),
-                         ("sharpness", 0.0), ("rho_floor", 0.0), ("precision", 7), ("r_s", float("nan"))):
+                         ("sharpness", 0.0), ("rho_floor", 0.0), ("precision", 7), ("r_s", float("nan")),
+                         ("recompute_alpt", 2)):
         bad = pkg.make_config(32, 300.0, pk_amp=1.0)
         setattr(bad, field, value)
         assert pkg.lib().bridge_validate_config(ctypes.byref(bad)) == pkg.BRIDGE_EINVAL, field
@@ -68,6 +69,11 @@ def test_workspace_scales_with_mesh_and_batch(pkg):
     # 512^3 FP32 fits comfortably in a GB300's HBM
     d = pkg.lib().bridge_workspace_bytes(ctypes.byref(pkg.make_config(512, 2000.0, pk_amp=1.0, n_regions=16)))
     assert d < 60e9
+    # recomputing the ALPT spectra in the adjoint drops ten half spectra from the workspace
+    r = pkg.lib().bridge_workspace_bytes(ctypes.byref(pkg.make_config(512, 2000.0, pk_amp=1.0, n_regions=16,
+                                                                        recompute_alpt=True)))
+    spec = 8 * (512 // 2 + 1) * 512 * 512
+    assert abs((d - r) - 10 * spec) < 4096
 
 
 def test_pk_amplitude_matches_oracle_quadrature(pkg):
@@ -90,9 +96,13 @@ def test_bias_marshalling(pkg):
     arr = pkg.bias_array([b, b])
     assert arr[1].alpha[15] == b.alpha[15] and arr[0].rho[3] == b.rho[3]
     assert arr[0].prior_mask == 0xFFFF
-    g = np.arange(32.0)
-    tied = pkg.tie_phi_classes(g, 16)
-    np.testing.assert_allclose(tied[:4], [0 + 1 + 2 + 3, 4 + 5 + 6 + 7, 8 + 9 + 10 + 11, 12 + 13 + 14 + 15])
+    # Table 2 reading: alpha_j, beta_j of the four Phi classes, tied over their delta sub-classes
+    assert arr[0].free_mask == 0xFF and arr[0].tie_classes == 1 and pkg.n_free([b]) == 8
+    u = synth.bias_phi_web()
+    u.free_mask = None
+    assert pkg.bias_array([u])[0].free_mask == 0xFF and pkg.bias_array([u])[0].tie_classes == 0
+    u.free_mask = 0b1010
+    assert pkg.n_free([u]) == 2
 
 
 def test_create_without_device_fails_cleanly(pkg):

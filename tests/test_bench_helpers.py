@@ -4,6 +4,7 @@ roofline.traffic comes from a recorded ncu ratio that is valid only for the CUDA
 measured on: the record names the source hash, and any source change must make the bench report
 null instead of a stale figure.
 """
+import json
 import os
 
 import pytest
@@ -18,12 +19,12 @@ def _tree(tmp_path, sources, record):
         (csrc / name).write_text(text)
     prof = tmp_path / "profiles"
     prof.mkdir()
-    (prof / "dram_traffic.md").write_text(record)
+    (prof / "dram_traffic.json").write_text(record)
     return tmp_path
 
 
 def test_source_hash_is_stable_and_tracks_every_file(tmp_path, monkeypatch):
-    root = _tree(tmp_path, {"a.cu": "x", "b.cuh": "y"}, "")
+    root = _tree(tmp_path, {"a.cu": "x", "b.cuh": "y"}, "{}")
     monkeypatch.setattr(bench, "ROOT", str(root))
     h1 = bench.csrc_hash()
     assert len(h1) == 12 and all(c in "0123456789abcdef" for c in h1)
@@ -37,11 +38,12 @@ def test_source_hash_is_stable_and_tracks_every_file(tmp_path, monkeypatch):
 
 
 def test_recorded_traffic_only_for_the_recorded_sources(tmp_path, monkeypatch):
-    root = _tree(tmp_path, {"k.cu": "kernel"}, "")
+    root = _tree(tmp_path, {"k.cu": "kernel"}, "{}")
     monkeypatch.setattr(bench, "ROOT", str(root))
     h = bench.csrc_hash()
-    (root / "profiles" / "dram_traffic.md").write_text(
-        f"# notes\n\ntraffic x_node {h} 0.882\ntraffic web_bias_adj deadbeef0000 0.976\n")
+    (root / "profiles" / "dram_traffic.json").write_text(json.dumps({"records": [
+        {"kernel": "x_node", "csrc_hash": h, "dram_over_algorithmic": 0.882},
+        {"kernel": "web_bias_adj", "csrc_hash": "deadbeef0000", "dram_over_algorithmic": 0.976}]}))
     assert bench.recorded_traffic("x_node", 1000.0) == pytest.approx(882.0)
     assert bench.recorded_traffic("web_bias_adj", 1000.0) is None     # recorded on other sources
     assert bench.recorded_traffic("y_inv", 1000.0) is None            # never recorded
@@ -50,19 +52,18 @@ def test_recorded_traffic_only_for_the_recorded_sources(tmp_path, monkeypatch):
 
 
 def test_recorded_traffic_without_a_record(tmp_path, monkeypatch):
-    root = _tree(tmp_path, {"k.cu": "kernel"}, "")
-    os.remove(root / "profiles" / "dram_traffic.md")
+    root = _tree(tmp_path, {"k.cu": "kernel"}, "{}")
+    os.remove(root / "profiles" / "dram_traffic.json")
     monkeypatch.setattr(bench, "ROOT", str(root))
     assert bench.recorded_traffic("x_node", 1.0) is None
 
 
 def test_committed_record_parses():
-    """Every traffic line of the committed record has the form the bench reads."""
+    """Every record of the committed file has the fields the bench reads."""
     import re
-    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "profiles", "dram_traffic.md")
-    lines = [l for l in open(path) if l.startswith("traffic ")]
-    assert lines
-    for l in lines:
-        m = re.match(r"traffic\s+(\S+)\s+([0-9a-f]{12})\s+([0-9.]+)\s*$", l)
-        assert m, l
-        assert 0.5 < float(m.group(3)) < 1.5
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "profiles", "dram_traffic.json")
+    recs = json.load(open(path))["records"]
+    assert recs
+    for r in recs:
+        assert re.fullmatch(r"[0-9a-f]{12}", r["csrc_hash"]) and r["kernel"]
+        assert 0.5 < float(r["dram_over_algorithmic"]) < 1.5

@@ -85,6 +85,17 @@ def test_power_spectrum_rolloff_closed_forms():
     assert abs(slope(1e-5 * kc, 2e-5 * kc) - ns) < 1e-8
 
 
+def test_delta0_at_cells_matches_the_full_inverse_transform():
+    """The inverse DFT written out cell by cell equals the library inverse FFT of the same
+    spectrum (itself pinned by the brute-force DFT above), including cells on the Nyquist
+    planes of every axis."""
+    cfg = small_cfg(n=16, box=160.0, n_regions=4)
+    nu = synth.white_noise(16, 23)
+    full = model.delta0_from_nu(torch.tensor(nu), cfg).numpy().ravel()
+    cells = np.array([0, 5, 8 * 256 + 8 * 16 + 8, 15 * 256 + 3 * 16 + 8, 4095])
+    np.testing.assert_allclose(model.delta0_at_cells(nu, cfg, cells), full[cells], rtol=1e-11, atol=1e-13)
+
+
 def test_nu_from_delta0_inverts_the_white_noise_map():
     """The inverse of App. A on k != 0 (Wiener initialisation and test-input construction):
     round trips through the brute-force-pinned forward map, with the k = 0 mode of nu set by

@@ -9,6 +9,10 @@ anything is launched.  The file name sorts last, so the GPU test also runs after
 the rest of the suite.
 """
 import ctypes
+import os
+import subprocess
+import sys
+import textwrap
 
 import numpy as np
 import pytest
@@ -83,3 +87,35 @@ def test_matches_context_delta0_two_calls(n, batch, precision):
             err = rel_l2(out[b], ref[b])
             assert err <= TOL[precision], f"chain {b}: rel L2 {err:.3e}"
     assert rel_l2(outs[0], outs[1]) > 0.5   # the two calls saw different noise
+
+
+@pytest.mark.gpu
+def test_first_call_in_a_fresh_process_before_any_context():
+    """The one-time set-up of the first call (scratch address, twiddle tables) is what the call
+    itself does, not something an earlier context left behind: a new process calls
+    bridge_delta0_noalloc before any context exists, twice, and only then creates a context
+    whose delta0 it is compared with."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = textwrap.dedent("""
+        import sys, numpy as np, torch
+        sys.path.insert(0, %r)
+        import synth, paper_2506_03969_gb300 as pkg
+        c = synth.config(0)
+        cfg = pkg.config_from(c, batch=2)
+        nu = torch.tensor(synth.white_noise(32, 4404, 2), dtype=torch.float32, device="cuda").reshape(2, -1).contiguous()
+        out = torch.empty_like(nu)
+        pkg.bridge_delta0_noalloc(cfg, nu, out)
+        first = out.clone()
+        pkg.bridge_delta0_noalloc(cfg, nu, out)
+        torch.cuda.synchronize()
+        counts = torch.ones_like(nu, dtype=torch.int32)
+        ctx = pkg.Context(cfg)
+        ref = ctx.bridge_debug_field(nu, counts, [synth.default_bias(c)] * 2, pkg.FIELD_DELTA0).reshape(2, -1)
+        for o in (first, out):
+            e = float(torch.linalg.vector_norm(o.double() - ref.double()) / torch.linalg.vector_norm(ref.double()))
+            print("rel", e)
+            assert e <= 1e-6, e
+    """) % root
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600)
+    print(r.stdout, r.stderr[-2000:])
+    assert r.returncode == 0
