@@ -90,6 +90,11 @@ typedef struct {
                                 1: the adjoint recomputes them from nu (10 fewer
                                 half spectra in the workspace, about 39 R more HBM
                                 traffic per gradient evaluation, R = N^3 floats)   */
+    double rsd_f;            /* redshift space (Sect. 2.9, b_v = 1): plane-parallel line
+                                of sight along z with the linear velocity v/(aH) =
+                                f Psi_1, i.e. Psi_z += f Psi_1,z (Psi_1 the Zel'dovich
+                                displacement) before the mass assignment; 0 = real
+                                space; finite                                        */
 } bridge_config;
 
 /* Bias table of one chain; entries [0, n_regions) are used (Eq. local_bias,

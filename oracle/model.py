@@ -18,6 +18,9 @@ its reason in the design notes):
     lap phi2 = S2 = sum_{i<j}(phi1_ii phi1_jj - phi1_ij^2), D2 = (D2/D^2) D^2.
     Spherical collapse: Psi_SC curl-free with divergence
     3[(1 - 2/3 D delta0)^(1/2) - 1] for D delta0 < 3/2, else -3.
+  * Redshift space (Sect. 2.9), plane-parallel along z with b_v = 1 and the
+    linear velocity v/(aH) = f Psi_1 (config rsd_f = f; 0 = real space):
+    Psi_z += f Psi_1,z before the mass assignment.
   * CIC: the particle of cell q sits at q + Psi/dx (cell units); trilinear
     weights, periodic; delta = rho - 1 (one particle per cell).
   * Phi-web: tidal tensor T_jk = d_j d_k Phi with lap Phi = delta (Sect. 2.8);
@@ -187,6 +190,12 @@ def alpt_displacement(delta0: torch.Tensor, cfg, g: Optional[Grid] = None, parts
         lpt = -D * gj * phi1_h + D2 * gj * phi2_h
         sc = gj * phisc_h
         psi.append(g.irfft(kern * lpt + (1.0 - kern) * sc) / g.dx)
+    f_rsd = getattr(cfg, "rsd_f", 0.0)
+    if f_rsd:
+        # redshift space (Sect. 2.9, Eq. of delta(s)) with b_v = 1, plane-parallel line of sight
+        # along z and the linear-theory velocity v / (aH) = f Psi_1: s_z = r_z + f Psi_1,z, where
+        # Psi_1 = -D grad phi1 is the first-order (Zel'dovich) displacement
+        psi[2] = psi[2] + f_rsd * g.irfft(-D * g.grad_mult(2) * phi1_h) / g.dx
     psi = torch.stack(psi)
     if parts:
         return psi, dict(phi=phi, s2=s2, theta_sc=tsc)

@@ -26,8 +26,10 @@ namespace {
 // forward pass to the adjoint; with recompute_alpt they are recomputed from nu
 // inside the adjoint into scratch slots 7..13 and 14..16, and the workspace
 // holds 19 spectra instead of 29.
+// The adjoint keeps g_Psi_z (the gather node's third output) in scratch slot 17
+// until the delta0 adjoint, which the redshift-space term feeds.
 enum { SP_SCR = 0, SP_TH = 7, SP_ALPT_STORED = 19, SP_PSI_STORED = 26, kMaxSpec = 29,
-       SP_ALPT_RECOMP = 7, SP_PSI_RECOMP = 14, kScratchSpec = 19 };
+       SP_ALPT_RECOMP = 7, SP_PSI_RECOMP = 14, SP_GPSIZ = 17, kScratchSpec = 19 };
 // Real buffers.
 enum {
     RB_DELTA = 0,   // 1: CIC mass rho = 1 + delta
@@ -176,6 +178,7 @@ int validate(const bridge_config* c, std::string* why) {
     if (c->precision != BRIDGE_FP32 && c->precision != BRIDGE_FP64) return bad("precision must be FP32 or FP64");
     if (c->precision == BRIDGE_FP64 && c->n > 256) return bad("the FP64 path supports n <= 256");
     if (c->recompute_alpt != 0 && c->recompute_alpt != 1) return bad("recompute_alpt must be 0 or 1");
+    if (!std::isfinite(c->rsd_f)) return bad("rsd_f must be finite");
     return BRIDGE_OK;
 }
 
@@ -381,10 +384,18 @@ template <typename T> int run_alpt(bridge_ctx* ctx, const T* nu) {
         CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
     {
-        PassProgram p = program(cspec<T>(ctx, SP_SCR + 2, 2), mspec<T>(ctx, ctx->sp_psi, 3), ctx->nspec);
+        // redshift space (Sect. 2.9), plane-parallel along z with the linear velocity
+        // v/(aH) = f Psi_1: Psi_z += f Psi_1,z = (i f D / dx) kz V0, V0 = delta0_hat / k^2 (the
+        // first x node's output, still in slot 4), summed into Psi_z before its inverse y DFT
+        const bool rsd = ctx->cfg.rsd_f != 0.0;
+        PassProgram p = program(cspec<T>(ctx, SP_SCR + 2, rsd ? 3 : 2), mspec<T>(ctx, ctx->sp_psi, 3), ctx->nspec);
         add_expand(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));
         add_expand(p, mk(1, 1, 0, 1, 0, R_ONE, 1.0));
         add_expand(p, mk(1, 2, 0, 0, 1, R_ONE, 1.0));
+        if (rsd) {
+            add_expand(p, mk(2, 2, 0, 0, 1, R_ONE, 0.0, ctx->cfg.rsd_f * ctx->cfg.growth_d / ctx->kp.dx));
+            p.accumulate = 1;
+        }
         CKL("y_inv", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_inv<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
     return BRIDGE_OK;
@@ -505,13 +516,14 @@ template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad, boo
         na.kind = NODE_GATHER;
         for (int f = 0; f < 3; ++f) {
             na.spec_in[f] = ctx->spec[ctx->sp_psi + f];
-            na.spec_out[f] = ctx->spec[SP_SCR + f];
+            na.spec_out[f] = ctx->spec[f < 2 ? SP_SCR + f : SP_GPSIZ];
         }
         na.real_in[0] = ctx->real[RB_GD];
         RUN(node<T>(ctx, na, "node_cic_gather", 6 * sby<T>(ctx) + rby<T>(ctx), nullptr));
     }
     {
-        PassProgram p = program(cspec<T>(ctx, SP_SCR, 3), mspec<T>(ctx, SP_SCR + 3, 2), ctx->nspec);
+        PassProgram p = program({ctx->spec[SP_SCR], ctx->spec[SP_SCR + 1], ctx->spec[SP_GPSIZ]},
+                                mspec<T>(ctx, SP_SCR + 3, 2), ctx->nspec);
         add_merge(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));
         add_merge(p, mk(1, 1, 0, 1, 0, R_ONE, 1.0));
         add_merge(p, mk(2, 1, 0, 0, 1, R_ONE, 1.0));
@@ -538,7 +550,12 @@ template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad, boo
         RUN(node<T>(ctx, na, "node_alpt_adj", 16 * sby<T>(ctx), nullptr));
     }
     {
-        PassProgram p = program(cspec<T>(ctx, SP_SCR, 7), mspec<T>(ctx, SP_SCR + 7, 4), ctx->nspec);
+        const bool rsd = ctx->cfg.rsd_f != 0.0;
+        std::vector<const void*> in = cspec<T>(ctx, SP_SCR, 7);
+        if (rsd) in.push_back(ctx->spec[SP_GPSIZ]);
+        PassProgram p = program(in, mspec<T>(ctx, SP_SCR + 7, 4), ctx->nspec);
+        // transpose of the redshift-space term: V0' += conj(i f D / dx) kz g_Psi_z
+        if (rsd) add_merge(p, mk(7, 3, 0, 0, 1, R_ONE, 0.0, -ctx->cfg.rsd_f * ctx->cfg.growth_d / ctx->kp.dx));
         add_merge(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));   // W0' <- g_delta0
         add_merge(p, mk(1, 1, 0, 0, 0, R_ONE, 1.0));   // V2' <- g_phi_xx
         add_merge(p, mk(2, 2, 0, 1, 0, R_ONE, 1.0));   // V1' <- ky g_phi_xy + kz g_phi_xz

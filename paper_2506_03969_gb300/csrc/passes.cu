@@ -389,6 +389,52 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YP
     }
 }
 
+// Inverse column pass whose outputs may be fed by several terms (y pass only):
+// out[d] = IDFT(sum over the terms of d of mult * in[src]), the sum formed before
+// the inverse DFT (linear); each term reads its source tile.  A kernel of its
+// own, so that the one-term-per-output pass above keeps its register budget.
+template <typename T, int N>
+__global__ void __launch_bounds__(Tile<T, N, false>::NT, 1) k_col_inv_acc(const PassProgram P, const KParams kp) {
+    using TL = Tile<T, N, false>;
+    using V = cplx_t<T>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* sm = reinterpret_cast<V*>(smraw);
+    const int t = threadIdx.x, chain = blockIdx.y;
+    int kz, c0;
+    TL::tile_pos(blockIdx.x, kz, c0);
+    const size_t base = TL::tile_base(kz, c0);
+    const int g = TL::b_g(t);
+    for (int d = 0; d < P.n_out; ++d) {
+        V Y[TL::J][TL::N2];
+#pragma unroll
+        for (int j = 0; j < TL::J; ++j)
+#pragma unroll
+            for (int k2 = 0; k2 < TL::N2; ++k2) Y[j][k2] = cmake<V>(T(0), T(0));
+        bool any = false;
+        for (int m = 0; m < P.n_expand; ++m) {
+            const Term tm = P.expand[m];
+            if (tm.dst != d) continue;
+            any = true;
+            const V* src = reinterpret_cast<const V*>(P.in[tm.src]) + chain * P.in_cs + base;
+#pragma unroll
+            for (int j = 0; j < TL::J; ++j) {
+                const int k1 = TL::b_k1(t, j);
+#pragma unroll
+                for (int k2 = 0; k2 < TL::N2; ++k2) {
+                    int mx, my, mz;
+                    TL::freqs(k1 + TL::N1 * k2, g, kz, c0, mx, my, mz);
+                    Y[j][k2] = cadd(Y[j][k2], cmul(ymult<T>(tm, my, mz, N, kp), src[TL::goff(k1 + TL::N1 * k2, g)]));
+                }
+            }
+        }
+        if (!any) continue;
+        __syncthreads();
+        TL::invB(Y, sm, t);
+        __syncthreads();
+        TL::invA(sm, reinterpret_cast<V*>(P.out[d]) + chain * P.out_cs + base, t);
+    }
+}
+
 // x node: Q = sum_merge mult * DFTx(in[src]);  out[dst] = IDFTx(mult * Q).
 // Within a tile every thread has one (ky, kz), so each term's ky/kz powers and
 // complex coefficient fold into one per-thread constant; per element only the
@@ -659,7 +705,7 @@ template <typename T, int N, bool XM, bool FWD>
 static cudaError_t col_n(int batch, const PassProgram& p, const KParams& kp, cudaStream_t s) {
     using TL = Tile<T, N, XM>;
     const size_t sm = size_t(TL::SM_ELEMS + (FWD ? TL::STAGE_ELEMS : 0)) * sizeof(cplx_t<T>);
-    auto kern = FWD ? k_col_fwd<T, N, XM> : k_col_inv<T, N, XM>;
+    auto kern = FWD ? k_col_fwd<T, N, XM> : (!XM && p.accumulate ? k_col_inv_acc<T, N> : k_col_inv<T, N, XM>);
     cudaError_t e = set_smem(kern, sm);
     if (e != cudaSuccess) return e;
     if (FWD) {

@@ -25,6 +25,7 @@ constexpr int kMaxFields = 16;
 // `expand` terms map Q into outputs (src ignored).
 struct PassProgram {
     int n_in, n_out, n_merge, n_expand;
+    int accumulate;   // y inverse pass: 1 when several expand terms share an output (summed before the inverse DFT)
     const void* in[kMaxFields];
     void* out[kMaxFields];
     long long in_cs, out_cs;

@@ -113,6 +113,7 @@ class Config:
     seed_momentum: int = 5001
     seed_perturb: int = 6001
     nb_beta: Optional[float] = None  # global beta override (configs that fix one beta)
+    rsd_f: float = 0.0               # redshift-space displacement along z with linear velocity f (0: real space)
 
     @property
     def dx(self) -> float:

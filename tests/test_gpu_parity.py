@@ -351,12 +351,14 @@ def test_autotune_keeps_results_and_later_calls_work(name, precision):
     ctx.close()
 
 
-def test_recompute_alpt_matches_stored():
+@pytest.mark.parametrize("rsd_f", [0.0, 0.8])
+def test_recompute_alpt_matches_stored(rsd_f):
     """recompute_alpt (the adjoint recomputes the ALPT spectra from nu) gives the same fields and
-    gradient as the default path that keeps them, and both match the oracle."""
+    gradient as the default path that keeps them, and both match the oracle, in real and in
+    redshift space."""
     n, box, nr, seed = CASES["64_hier"]
-    cfg, bias, nu, counts, _ = make_case(n, box, nr, seed, point="eval")
-    f, lp_o, g_o, gb_o, _ = oracle_ref("64_hier", cfg, bias, nu, counts)
+    cfg, bias, nu, counts, _ = make_case(n, box, nr, seed, point="eval", rsd_f=rsd_f)
+    f, lp_o, g_o, gb_o, _ = oracle_ref(f"64_hier_rsd{rsd_f}", cfg, bias, nu, counts, conditioning=False)
     out = {}
     for rec in (False, True):
         ctx, nu_d, c_d = run_gpu(cfg, bias, nu, counts, pkg.BRIDGE_FP32, recompute_alpt=rec)
@@ -368,6 +370,37 @@ def test_recompute_alpt_matches_stored():
         ctx.close()
     assert rel_l2(out[True][1], out[False][1]) <= 1e-5
     assert np.max(np.abs(out[True][2] - out[False][2])) <= 1e-5 * np.max(np.abs(out[False][2]))
+
+
+@pytest.mark.parametrize("n,precision", [(32, "fp32"), (32, "fp64"), (64, "fp32"), (64, "fp64")])
+def test_redshift_space_against_oracle(n, precision):
+    """Sect. 2.9, plane-parallel along z with the linear velocity (f = 0.8, the large-field
+    workload's value): counts drawn from the redshift-space model; every field (the displacement
+    includes f Psi_1,z), the log posterior and the gradient (through the transposed RSD term)
+    against the oracle at the fixed bounds."""
+    box, nr = {32: (300.0, 4), 64: (500.0, 16)}[n]
+    cfg, bias, nu, counts, _ = make_case(n, box, nr, 1900 + n, point="eval", rsd_f=0.8)
+    ctx, nu_d, c_d, _, _ = _full_check(f"rsd_{n}", cfg, bias, nu, counts, precision)
+    real = synth.Config("real", n, box, n_regions=nr)
+    psi_real = model.alpt_displacement(model.delta0_from_nu(torch.tensor(nu), real), real).numpy()
+    psi = ctx.bridge_debug_field(nu_d, c_d, [bias], pkg.FIELD_PSI).double().cpu().numpy().reshape(psi_real.shape)
+    moved = rel_l2(psi[2], psi_real[2])
+    print(f"RSD moves Psi_z by {moved:.2e} (relative); Psi_x unchanged to {rel_l2(psi[0], psi_real[0]):.1e}")
+    assert moved > 0.1 and rel_l2(psi[0], psi_real[0]) <= bounds(precision)[0]
+    ctx.close()
+
+
+def test_redshift_space_256():
+    """The 256^3 workload in redshift space (f = 0.8), FP32, at the data-consistent point:
+    fields, log posterior and gradient at the fixed bounds."""
+    cfg = synth.config(2)
+    cfg.rsd_f = 0.8
+    bias = synth.default_bias(cfg)
+    nu_t = synth.white_noise(cfg.n, cfg.seed_truth)
+    counts = mock.mock_counts(nu_t, cfg, bias, cfg.seed_counts)
+    nu, counts, _, _ = pp.condition(nu_t, counts, cfg, bias)
+    ctx = _full_check("256_rsd", cfg, bias, nu, counts, "fp32", conditioning=False)[0]
+    ctx.close()
 
 
 def test_free_mask_and_tied_classes():

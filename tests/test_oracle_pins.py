@@ -226,6 +226,53 @@ def test_2lpt_two_orthogonal_waves():
     np.testing.assert_allclose(psi[2], 0.0, atol=1e-12)
 
 
+def test_rsd_plane_parallel_closed_forms():
+    """Sect. 2.9 with b_v = 1, line of sight z, linear velocity v/(aH) = f Psi_1.  Two orthogonal
+    waves along x and z (r_s = 0, pure 2LPT): the z displacement becomes (1 + f) times its
+    Zel'dovich part plus the unchanged second-order part (so using the whole 2LPT Psi_z instead
+    of Psi_1,z fails), and the x displacement does not change; a wave along x alone is not moved
+    at all."""
+    f = 0.8
+    cfg = small_cfg(n=16, box=100.0, r_s=0.0, growth_d=1.0, rsd_f=f)
+    n, dx = cfg.n, cfg.box / cfg.n
+    X, Y, Z = _mesh(n)
+    k1, k3 = 2 * math.pi * 2 / cfg.box, 2 * math.pi * 3 / cfg.box
+    A1, A3 = 0.3, 0.2
+    x, z = X * dx, Z * dx
+    d0 = A1 * np.cos(k1 * x) + A3 * np.cos(k3 * z)
+    psi = model.alpt_displacement(torch.tensor(d0), cfg).numpy() * dx
+    D2 = -3.0 / 7.0
+    ex = -A1 * np.sin(k1 * x) / k1 + D2 * A1 * A3 * k1 * np.sin(k1 * x) * np.cos(k3 * z) / (k1 ** 2 + k3 ** 2)
+    ez = -(1 + f) * A3 * np.sin(k3 * z) / k3 + D2 * A1 * A3 * k3 * np.cos(k1 * x) * np.sin(k3 * z) / (k1 ** 2 + k3 ** 2)
+    np.testing.assert_allclose(psi[0], ex, atol=1e-12)
+    np.testing.assert_allclose(psi[1], 0.0, atol=1e-12)
+    np.testing.assert_allclose(psi[2], ez, atol=1e-12)
+    dx_only = A1 * np.cos(k1 * x)
+    off = small_cfg(n=16, box=100.0, r_s=0.0, growth_d=1.0)
+    np.testing.assert_allclose(model.alpt_displacement(torch.tensor(dx_only), cfg).numpy(),
+                               model.alpt_displacement(torch.tensor(dx_only), off).numpy(), atol=1e-14)
+
+
+def test_rsd_only_moves_the_line_of_sight_component():
+    """A random field with the ALPT blend on: RSD leaves Psi_x, Psi_y unchanged and adds to Psi_z a
+    term linear in f (Psi_z(2f) - Psi_z(0) = 2 (Psi_z(f) - Psi_z(0))), which is curl-free with
+    divergence -f D d^2 phi1 / dz^2 in k space (brute force on the spectrum)."""
+    base = small_cfg(n=16, box=160.0, growth_d=1.0)
+    d0 = model.delta0_from_nu(torch.tensor(synth.white_noise(16, 31)), base)
+    p0 = model.alpt_displacement(d0, base).numpy()
+    p1 = model.alpt_displacement(d0, small_cfg(n=16, box=160.0, growth_d=1.0, rsd_f=0.5)).numpy()
+    p2 = model.alpt_displacement(d0, small_cfg(n=16, box=160.0, growth_d=1.0, rsd_f=1.0)).numpy()
+    np.testing.assert_allclose(p1[:2], p0[:2], atol=1e-14)
+    np.testing.assert_allclose(p2[2] - p0[2], 2 * (p1[2] - p0[2]), atol=1e-12)
+    # the added z displacement: -f D d/dz of phi1 with lap phi1 = delta0 -> in k space
+    # i kz (f D) delta0_hat / k^2 (cell units), Nyquist plane of kz zeroed
+    g = model.Grid(16, 160.0)
+    add_h = torch.fft.rfftn(torch.tensor(p2[2] - p0[2])) * g.dx
+    d0h = torch.fft.rfftn(d0)
+    expect = 1j * g.k_odd[2] * 1.0 * d0h * g.inv_k2
+    assert float((add_h - expect).abs().max()) < 1e-10 * float(expect.abs().max())
+
+
 def test_spherical_collapse_pointwise():
     x = torch.tensor([0.0, 1e-4, -1e-4, 0.3, 1.5, 2.0, -1.5], dtype=torch.float64)
     t = model.theta_sc(x, 1.0).numpy()
