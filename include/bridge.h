@@ -84,7 +84,7 @@ typedef struct {
     double sharpness;        /* sigmoid steepness s (Eq. sigmoid)                    */
     int32_t n_regions;       /* 4: Phi-web; 16: Phi x delta web (Sect. 2.7)          */
     double rho_floor;        /* 1 + delta is floored at this value (> 0)             */
-    int32_t precision;       /* BRIDGE_FP32, or BRIDGE_FP64 (n <= 256)               */
+    int32_t precision;       /* BRIDGE_FP32, or BRIDGE_FP64 (the comparator path)    */
     int32_t recompute_alpt;  /* 0: the ALPT spectra (delta0, phi_ij, Psi; Sect. 2.3)
                                 are kept from the forward pass for the adjoint;
                                 1: the adjoint recomputes them from nu (10 fewer
@@ -227,6 +227,20 @@ enum {
 };
 int bridge_debug_field(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
                        int32_t which, void* out);
+
+/* Starting point of a chain (Sect. 2.2): the observed tracer density contrast
+ * delta*_tr = n* N^3 / N_tr - 1 Wiener-filtered (Zaroubi et al. 1995) back to an
+ * approximate linear field delta0^(0) and mapped to white noise nu^(0) by the
+ * inverse of App. A.  Signal: the evolved linear field D delta0 with the known
+ * power D^2 P(k); noise: Poisson shot noise of power L^3 / N_tr; no peculiar
+ * motions.  Per mode k != 0 (the k = 0 mode, and so the mean of nu^(0), is 0):
+ *   nu^(0)_hat = D sqrt(P dx^3) / (D^2 P + L^3 / N_tr) DFT(delta*_tr).
+ *   counts   device [B][N^3] int32 tracer counts in [0, 65535]; every chain needs
+ *            at least one tracer (EINVAL otherwise)
+ *   nu_out   device [B][N^3] float/double: nu^(0)
+ * Synchronises the context stream (several times: the filter depends on each
+ * chain's N_tr).  Errors: EINVAL, ECUDA. */
+int bridge_wiener_init(bridge_ctx* ctx, const int32_t* counts, void* nu_out);
 
 /* The library's 3D real DFT and its inverse, without any operator between them:
  * out = IDFT(DFT(in)) for every chain, through the same z, y and x pass kernels

@@ -160,6 +160,27 @@ def nu_from_delta0(delta0: torch.Tensor, cfg, nu_mean: float = 0.0, g: Optional[
     return g.irfft(nh)
 
 
+def wiener_init(counts_np, cfg) -> np.ndarray:
+    """Starting point of a chain (Sect. 2.2): the observed tracer contrast
+    delta*_tr = n* N^3 / N_tr - 1 Wiener-filtered (Zaroubi et al. 1995) back to a linear
+    field and mapped to white noise.  Signal: the evolved linear field D delta0 with power
+    D^2 P(k) (the spectrum assumed known); noise: white Poisson shot noise of power
+    P_N = L^3 / N_tr; no peculiar motions.  Per mode k != 0:
+        delta0^(0)_hat = D P / (D^2 P + P_N) DFT(delta*_tr),
+    and nu^(0) is the inverse of App. A applied to delta0^(0) (mean zero)."""
+    g = Grid(cfg.n, cfg.box)
+    n = torch.tensor(np.asarray(counts_np), dtype=DT)
+    ntr = float(n.sum())
+    d = n * (cfg.n ** 3 / ntr) - 1.0
+    amp = amplitude(cfg)
+    pk = torch.tensor(cosmo.power_spectrum(g.kmag.numpy(), amp, cfg.pk_ns, cfg.pk_kc, cfg.pk_pow), dtype=DT)
+    D = cfg.growth_d
+    pn = cfg.box ** 3 / ntr
+    filt = D * pk / (D * D * pk + pn)
+    d0 = g.irfft(filt * g.rfft(d))
+    return nu_from_delta0(d0, cfg, nu_mean=0.0, g=g).numpy()
+
+
 # ----------------------------------------------------------------------------
 # M_Psi: ALPT (Sect. 2.3) + CIC
 # ----------------------------------------------------------------------------

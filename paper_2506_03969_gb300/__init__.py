@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
     L.bridge_profile_read.restype = ctypes.c_int
     L.bridge_autotune.argtypes = [vp, vp, i32p, bp, i32p]; L.bridge_autotune.restype = ctypes.c_int
     L.bridge_fft_roundtrip.argtypes = [vp, vp, vp]; L.bridge_fft_roundtrip.restype = ctypes.c_int
+    L.bridge_wiener_init.argtypes = [vp, i32p, vp]; L.bridge_wiener_init.restype = ctypes.c_int
     L.bridge_delta0_noalloc.argtypes = [cp, vp, vp, vp]; L.bridge_delta0_noalloc.restype = ctypes.c_int
     L.bridge_last_error.argtypes = [vp]; L.bridge_last_error.restype = ctypes.c_char_p
     L.bridge_status_string.argtypes = [ctypes.c_int]; L.bridge_status_string.restype = ctypes.c_char_p
@@ -298,6 +299,14 @@ class Context:
         self._check(lib().bridge_autotune(self.handle, ctypes.c_void_p(_ptr(nu)), ctypes.c_void_p(_ptr(counts)),
                                           bias_array(biases), ctypes.cast(ch, ctypes.c_void_p)))
         return [int(v) for v in ch]
+
+    def bridge_wiener_init(self, counts, out=None):
+        """Chain starting point nu^(0): the tracer contrast Wiener-filtered to white noise."""
+        self._counts(counts)
+        out = out if out is not None else self.torch.empty(counts.shape, dtype=self.dtype, device=counts.device)
+        self._field(out, "out")
+        self._check(lib().bridge_wiener_init(self.handle, ctypes.c_void_p(_ptr(counts)), ctypes.c_void_p(_ptr(out))))
+        return out
 
     def bridge_fft_roundtrip(self, x, out=None):
         """IDFT(DFT(x)) through the library's FFT pass kernels (no operator)."""

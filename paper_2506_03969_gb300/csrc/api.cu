@@ -176,7 +176,6 @@ int validate(const bridge_config* c, std::string* why) {
     if (c->n_regions != 4 && c->n_regions != 16) return bad("n_regions must be 4 or 16");
     if (!(c->rho_floor > 0) || !(c->rho_floor < 1)) return bad("rho_floor must be in (0, 1)");
     if (c->precision != BRIDGE_FP32 && c->precision != BRIDGE_FP64) return bad("precision must be FP32 or FP64");
-    if (c->precision == BRIDGE_FP64 && c->n > 256) return bad("the FP64 path supports n <= 256");
     if (c->recompute_alpt != 0 && c->recompute_alpt != 1) return bad("recompute_alpt must be 0 or 1");
     if (!std::isfinite(c->rsd_f)) return bad("rsd_f must be finite");
     return BRIDGE_OK;
@@ -238,7 +237,7 @@ Plan make_plan(const bridge_config* c) {
     p.biasd_bytes = align_up(sizeof(BiasD) * B);
     p.biast_bytes = align_up(sizeof(BiasT<double>) * B);
     p.node_bytes = align_up(size_t(BRIDGE_NODE_L2_MB + 8) << 20);   // fused-node slabs (the launcher keeps them below the budget)
-    p.rtab_bytes = align_up(size_t(4) * (3 * (n / 2) * (n / 2) + 1) * esz);
+    p.rtab_bytes = align_up(size_t(kRadialTables) * (3 * (n / 2) * (n / 2) + 1) * esz);
     p.cot_bytes = align_up(sizeof(double) * B);
     p.total = p.spec_bytes * p.nspec_buf + p.real_bytes * (p.nreal_buf + kExtraReal) + p.c16_bytes + p.partial_bytes +
               p.sc_bytes + p.biasd_bytes + p.biast_bytes + p.node_bytes + p.rtab_bytes + p.cot_bytes + 256;
@@ -916,6 +915,48 @@ template <typename T> int do_debug(bridge_ctx* ctx, const void* nu, const int32_
     return finish(ctx);
 }
 
+// Chain initialisation (Sect. 2.2): the tracer contrast delta*_tr = n* N^3 / N_tr - 1
+// Wiener-filtered to the linear field and mapped to white noise, per mode k != 0
+//   nu0_hat = D s dx^3 / (D^2 s^2 dx^3 + P_N) DFT(delta*_tr),  s = sqrt(P / dx^3),
+// P_N = L^3 / N_tr (Poisson shot noise); the factor is written per chain into the
+// fifth radial table and applied by the x node.
+template <typename T> int do_wiener_init(bridge_ctx* ctx, const int32_t* counts, void* nu_out) {
+    if (!counts || !nu_out) return fail(ctx, BRIDGE_EINVAL, "counts and nu_out are required");
+    RUN(prep_counts<T>(ctx, counts));
+    CKL("delta_tr", rby<T>(ctx) + c16b(ctx), launch_delta_tr<T>(ctx->n, ctx->B, ctx->c16, ctx->sc, RB<T>(ctx, RB_SCR), ctx->stream));
+    RUN(z_fwd<T>(ctx, creal(ctx, RB_SCR, 1), mspec<T>(ctx, SP_SCR, 1)));
+    RUN(y_identity<T>(ctx, SP_SCR, 1, true));
+    RUN(finish(ctx));   // N_tr of every chain on the host
+    const int rlen = ctx->kp.rlen;
+    std::vector<double> tab(size_t(4) * rlen);
+    radial_tables_host(ctx->n, ctx->kp, tab.data());
+    const double* sq = tab.data() + (R_SQRTP - 1) * rlen;
+    const double D = ctx->cfg.growth_d, dx3 = ctx->kp.dx * ctx->kp.dx * ctx->kp.dx;
+    std::vector<T> w(rlen);
+    T* wdev = reinterpret_cast<T*>(ctx->rtab) + size_t(R_WIENER - 1) * rlen;
+    for (int c = 0; c < ctx->B; ++c) {
+        const double ntr = ctx->sc_host[c].ntr;
+        if (!(ntr > 0)) return fail(ctx, BRIDGE_EINVAL, "chain " + std::to_string(c) + " has no tracers");
+        const double pn = ctx->cfg.box * ctx->cfg.box * ctx->cfg.box / ntr;
+        for (int m2 = 0; m2 < rlen; ++m2) {
+            const double sv = sq[m2];
+            w[m2] = T(D * sv * dx3 / (D * D * sv * sv * dx3 + pn));
+        }
+        CK(cudaMemcpyAsync(wdev, w.data(), sizeof(T) * rlen, cudaMemcpyHostToDevice, ctx->stream));
+        PassProgram p = program({reinterpret_cast<char*>(ctx->spec[SP_SCR]) + size_t(c) * ctx->nspec * 2 * sizeof(T)},
+                                {reinterpret_cast<char*>(ctx->spec[SP_SCR + 1]) + size_t(c) * ctx->nspec * 2 * sizeof(T)},
+                                ctx->nspec);
+        add_merge(p, mk(0, 0, 0, 0, 0, R_WIENER, 1.0 / double(ctx->nvox)));
+        add_expand(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));
+        CKL("x_node", 2 * sby<T>(ctx) / ctx->B, launch_x_node<T>(ctx->n, 1, p, ctx->kp, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));   // the host table is refilled for the next chain
+    }
+    RUN(y_identity<T>(ctx, SP_SCR + 1, 1, false));
+    RUN(z_inv<T>(ctx, {ctx->spec[SP_SCR + 1]}, {nu_out}));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return BRIDGE_OK;
+}
+
 // out = IDFT(DFT(in)) through the five pass kernels with the identity operator:
 // z forward, y forward, x node (forward x DFT, 1/N^3, inverse x DFT), y
 // inverse, z inverse -- the transforms of every other program without an
@@ -1272,6 +1313,14 @@ int bridge_debug_field(bridge_ctx* ctx, const void* nu, const int32_t* counts, c
     ctx->err.clear();
     if (!aligned16({nu, counts, out})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
     return DISPATCH(ctx, do_debug, nu, counts, bias, which, out);
+}
+
+int bridge_wiener_init(bridge_ctx* ctx, const int32_t* counts, void* nu_out) {
+    if (!ctx) return BRIDGE_EINVAL;
+    ctx->launches = 0;
+    ctx->err.clear();
+    if (!aligned16({counts, nu_out})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
+    return DISPATCH(ctx, do_wiener_init, counts, nu_out);
 }
 
 int bridge_fft_roundtrip(bridge_ctx* ctx, const void* in, void* out) {

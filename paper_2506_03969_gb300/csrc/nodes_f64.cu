@@ -18,6 +18,7 @@ template <> cudaError_t launch_node<double>(int n, int batch, const NodeArgs& a,
         case 64: return node_dispatch<double, 64>(batch, sms, a, s, grid_used);
         case 128: return node_dispatch<double, 128>(batch, sms, a, s, grid_used);
         case 256: return node_dispatch<double, 256>(batch, sms, a, s, grid_used);
+        case 512: return node_dispatch<double, 512>(batch, sms, a, s, grid_used);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -30,6 +31,7 @@ template <> int node_max_grid<double>(int n, int batch) {
         case 64: return node_grid_max<double, 64>(batch, sms);
         case 128: return node_grid_max<double, 128>(batch, sms);
         case 256: return node_grid_max<double, 256>(batch, sms);
+        case 512: return node_grid_max<double, 512>(batch, sms);
         default: return 0;
     }
 }
@@ -42,6 +44,7 @@ template <> size_t node_scratch_bytes<double>(int n, int batch) {
         case 64: return node_scratch_max<double, 64>(batch, sms);
         case 128: return node_scratch_max<double, 128>(batch, sms);
         case 256: return node_scratch_max<double, 256>(batch, sms);
+        case 512: return node_scratch_max<double, 512>(batch, sms);
         default: return 0;
     }
 }

@@ -72,7 +72,9 @@ __device__ __forceinline__ cplx_t<T> ymult(const Term& tm, int my, int mz, int n
 template <typename T, int N, bool XM> struct Tile {
     using V = cplx_t<T>;
     static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, J = N1 / N2;
-    static constexpr int GY0 = (int)(128 / sizeof(V)) > 256 / N2 ? (int)(128 / sizeof(V)) : 256 / N2;
+    // FP64 at N = 512: 8 columns, so that the forward pass's tile and its staged copy fit in shared memory
+    static constexpr int GY0 = (sizeof(V) == 16 && N >= 512) ? 8
+                               : ((int)(128 / sizeof(V)) > 256 / N2 ? (int)(128 / sizeof(V)) : 256 / N2);
     static constexpr int GX0 = (sizeof(V) == 8 ? 256 : 128) / N2;
     static constexpr int G0 = XM ? GX0 : GY0;
     static constexpr int G = G0 < N ? G0 : N;
@@ -654,7 +656,7 @@ template <typename K> static cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaSuccess;
 }
 
-// Mesh sizes compiled in (FP64 stops at 256: the FP64 path is the comparator).
+// Mesh sizes compiled in.
 #ifndef BRIDGE_ONLY_N
 #define BRIDGE_N_SWITCH(n, T, CALL)                                   \
     switch (n) {                                                      \
@@ -663,10 +665,7 @@ template <typename K> static cudaError_t set_smem(K kernel, size_t bytes) {
         case 64: { constexpr int NN = 64; CALL; }                     \
         case 128: { constexpr int NN = 128; CALL; }                   \
         case 256: { constexpr int NN = 256; CALL; }                   \
-        case 512: {                                                   \
-            if constexpr (sizeof(T) == 4) { constexpr int NN = 512; CALL; } \
-            else return cudaErrorInvalidValue;                        \
-        }                                                             \
+        case 512: { constexpr int NN = 512; CALL; }                   \
         default: return cudaErrorInvalidValue;                        \
     }
 #else

@@ -7,7 +7,10 @@
 namespace bridge {
 
 // Multiplier radial factors R(|k|) used by pass terms.
-enum RCode : int8_t { R_ONE = 0, R_INVK2 = 1, R_SQRTP = 2, R_KBLEND = 3, R_1MKBLEND = 4 };
+// R_WIENER: the Wiener-filter factor of the chain initialisation, written into
+// the fifth radial table per call (it depends on the chain's tracer count).
+enum RCode : int8_t { R_ONE = 0, R_INVK2 = 1, R_SQRTP = 2, R_KBLEND = 3, R_1MKBLEND = 4, R_WIENER = 5 };
+constexpr int kRadialTables = 5;
 
 // One linear term of a pass program:
 //   out[dst] (+)= (cre + i cim) * kx^px * ky^py * kz^pz * R(|k|) * in[src]
@@ -41,7 +44,7 @@ struct KParams {
     double pk_amp, pk_ns, pk_kc, pk_pow;
     double r_s;
     // Radial factors tabulated by the integer m^2 = mx^2 + my^2 + mz^2 (k^2 = kf^2 m^2),
-    // computed on the host in FP64: table c-1 holds R_c for c = R_INVK2 .. R_1MKBLEND.
+    // computed on the host in FP64: table c-1 holds R_c for c = R_INVK2 .. R_WIENER.
     const void* rtab;
     int rlen;         // entries per table: 3 (N/2)^2 + 1
 };

@@ -387,6 +387,13 @@ __global__ void __launch_bounds__(kPwThreads) k_kick_drift(long long nvox, T* p,
     write_partials<1>(acc, partial);
 }
 
+// Tracer density contrast n* N^3 / N_tr - 1 of each chain (Sect. 2.2 initialisation).
+template <typename T> __global__ void k_delta_tr(long long nvox, const uint16_t* c16, const ChainScalars* sc, T* out) {
+    const size_t off = (size_t)blockIdx.y * nvox;
+    const T scale = T(double(nvox) / sc[blockIdx.y].ntr);
+    PW_LOOP(i, nvox) out[off + i] = T(c16[off + i]) * scale - T(1);
+}
+
 // g[chain] *= scale[chain] (the cotangent of a vector-Jacobian product).
 template <typename T> __global__ void k_scale_chains(long long nvox, T* g, const double* scale) {
     const size_t off = (size_t)blockIdx.y * nvox;
@@ -572,6 +579,11 @@ cudaError_t launch_kick_drift(int n, int batch, T* p, T* nu, const T* g, double 
     k_kick_drift<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), p, nu, g, T(ck), T(cd), partial);
     return cudaGetLastError();
 }
+template <typename T> cudaError_t launch_delta_tr(int n, int batch, const uint16_t* c16, const ChainScalars* sc, T* out,
+                                                  cudaStream_t s) {
+    k_delta_tr<T><<<dim3(pw_blocks_wide(n), batch), kPwThreads, 0, s>>>(nvox_of(n), c16, sc, out);
+    return cudaGetLastError();
+}
 template <typename T> cudaError_t launch_scale_chains(int n, int batch, T* g, const double* scale, cudaStream_t s) {
     k_scale_chains<T><<<dim3(pw_blocks_wide(n), batch), kPwThreads, 0, s>>>(nvox_of(n), g, scale);
     return cudaGetLastError();
@@ -609,6 +621,7 @@ cudaError_t launch_reduce(int what, int nblk, int batch, const double* partial, 
     template cudaError_t launch_shift<T>(long long, const T*, T*, T, cudaStream_t);                                 \
     template cudaError_t launch_kick_drift<T>(int, int, T*, T*, const T*, double, double, double*, cudaStream_t);   \
     template cudaError_t launch_scale_chains<T>(int, int, T*, const double*, cudaStream_t);                         \
+    template cudaError_t launch_delta_tr<T>(int, int, const uint16_t*, const ChainScalars*, T*, cudaStream_t);       \
     template cudaError_t launch_lnnbar<T>(long long, int, const T*, const ChainScalars*, T*, cudaStream_t);         \
     template cudaError_t launch_eigs<T>(int, int, const Fields16&, const Fields16&, cudaStream_t);
 PW_INST(float)

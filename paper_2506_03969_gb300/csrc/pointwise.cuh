@@ -74,6 +74,8 @@ template <typename T> cudaError_t launch_shift(long long count, const T* in, T* 
 template <typename T>
 cudaError_t launch_kick_drift(int n, int batch, T* p, T* nu, const T* g, double ck, double cd, double* partial,
                               cudaStream_t s);
+template <typename T>
+cudaError_t launch_delta_tr(int n, int batch, const uint16_t* c16, const ChainScalars* sc, T* out, cudaStream_t s);
 template <typename T> cudaError_t launch_scale_chains(int n, int batch, T* g, const double* scale, cudaStream_t s);
 template <typename T>
 cudaError_t launch_lnnbar(long long nvox, int batch, const T* lnf, const ChainScalars* sc, T* out, cudaStream_t s);

@@ -35,11 +35,72 @@ __device__ __forceinline__ double v_fmax(double a, double b) { return fmax(a, b)
 
 // Eigen-decomposition data of a symmetric 3x3 tensor A: m = tr(A)/3, B = A - m I,
 // eigenvalues mu1 >= mu2 >= mu3 of B (lambda_n = m + mu_n), by the trigonometric
-// solution of the characteristic cubic (Smith 1961), App. B ordering.
+// solution of the characteristic cubic (Smith 1961), App. B ordering.  Where two
+// eigenvalues nearly coincide (|r| within kEigPairBand of 1, r = det B / (2 p^3)),
+// the cubic fixes the pair only to about sqrt(epsilon) of the scale; there the
+// isolated eigenvalue is kept and the pair is taken from the 2x2 block of B in
+// the plane orthogonal to its eigenvector (eig_pair).
+constexpr double kEigPairBand = 1e-3;
 template <typename T> struct Eig3 {
     T m;
     T mu[3];
 };
+
+template <typename T> __device__ __forceinline__ T dot3(const T u[3], const T v[3]) {
+    return u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+}
+template <typename T> __device__ __forceinline__ void cross3(const T u[3], const T v[3], T w[3]) {
+    w[0] = u[1] * v[2] - u[2] * v[1];
+    w[1] = u[2] * v[0] - u[0] * v[2];
+    w[2] = u[0] * v[1] - u[1] * v[0];
+}
+// B v for the symmetric B stored as xx, xy, xz, yy, yz, zz
+template <typename T> __device__ __forceinline__ void symv(const T b[6], const T v[3], T w[3]) {
+    w[0] = b[0] * v[0] + b[1] * v[1] + b[2] * v[2];
+    w[1] = b[1] * v[0] + b[3] * v[1] + b[4] * v[2];
+    w[2] = b[2] * v[0] + b[4] * v[1] + b[5] * v[2];
+}
+
+// The two eigenvalues of traceless B other than an isolated one, iso, by
+// deflation: v = the eigenvector of iso (the largest cross product of two rows
+// of B - iso I), an orthonormal pair u, w spanning its complement, and the 2x2
+// block [u.Bu, u.Bw; w.Bu, w.Bw] with trace -iso, whose eigenvalues are
+// -iso/2 +- sqrt(h^2 + q^2) with h = (u.Bu - w.Bw)/2, q = u.Bw.  The gap of
+// the pair comes out as a square root of a sum of squares, accurate however
+// small it is, whereas from the invariants of the characteristic cubic it is
+// lost to cancellation (an error of order sqrt(epsilon) times the scale).
+template <typename T> __device__ __forceinline__ void eig_pair(const T b[6], T iso, T& hi, T& lo) {
+    const T r0[3] = {b[0] - iso, b[1], b[2]}, r1[3] = {b[1], b[3] - iso, b[4]}, r2[3] = {b[2], b[4], b[5] - iso};
+    T c01[3], c02[3], c12[3];
+    cross3(r0, r1, c01);
+    cross3(r0, r2, c02);
+    cross3(r1, r2, c12);
+    const T n01 = dot3(c01, c01), n02 = dot3(c02, c02), n12 = dot3(c12, c12);
+    T v[3];
+    T nv = n01;
+    v[0] = c01[0]; v[1] = c01[1]; v[2] = c01[2];
+    if (n02 > nv) { nv = n02; v[0] = c02[0]; v[1] = c02[1]; v[2] = c02[2]; }
+    if (n12 > nv) { nv = n12; v[0] = c12[0]; v[1] = c12[1]; v[2] = c12[2]; }
+    if (!(nv > T(0))) { hi = lo = T(-0.5) * iso; return; }
+    const T iv = T(1) / v_sqrt(nv);
+    v[0] *= iv; v[1] *= iv; v[2] *= iv;
+    // u: v crossed with the coordinate axis least aligned with v
+    const T ax = v[0] < T(0) ? -v[0] : v[0], ay = v[1] < T(0) ? -v[1] : v[1], az = v[2] < T(0) ? -v[2] : v[2];
+    T u[3];
+    if (ax <= ay && ax <= az) { u[0] = T(0); u[1] = v[2]; u[2] = -v[1]; }
+    else if (ay <= az) { u[0] = -v[2]; u[1] = T(0); u[2] = v[0]; }
+    else { u[0] = v[1]; u[1] = -v[0]; u[2] = T(0); }
+    const T iu = T(1) / v_sqrt(dot3(u, u));
+    u[0] *= iu; u[1] *= iu; u[2] *= iu;
+    T w[3], bu[3], bw[3];
+    cross3(v, u, w);
+    symv(b, u, bu);
+    symv(b, w, bw);
+    const T h = T(0.5) * (dot3(u, bu) - dot3(w, bw)), q = dot3(u, bw);
+    const T g = v_sqrt(h * h + q * q);
+    hi = T(-0.5) * iso + g;
+    lo = T(-0.5) * iso - g;
+}
 
 template <typename T> __device__ __forceinline__ void eig3(const T a[6], Eig3<T>& e) {
     e.m = (a[0] + a[3] + a[5]) * T(1.0 / 3.0);
@@ -59,6 +120,20 @@ template <typename T> __device__ __forceinline__ void eig3(const T a[6], Eig3<T>
     // cos(phi + 2pi/3) = -c/2 - (sqrt3/2) s
     const T mu1 = T(2) * p * c;
     const T mu3 = T(2) * p * (T(-0.5) * c - T(0.86602540378443864676) * s);
+    if (r > T(1) - T(kEigPairBand)) {
+        // mu2 close to mu3: mu1 is isolated and accurate; the pair by deflation
+        T hi, lo;
+        eig_pair<T>(b, mu1, hi, lo);
+        e.mu[0] = mu1; e.mu[1] = hi; e.mu[2] = lo;
+        return;
+    }
+    if (r < T(-1) + T(kEigPairBand)) {
+        // mu2 close to mu1: mu3 is isolated
+        T hi, lo;
+        eig_pair<T>(b, mu3, hi, lo);
+        e.mu[0] = hi; e.mu[1] = lo; e.mu[2] = mu3;
+        return;
+    }
     T mu2 = -mu1 - mu3;
     mu2 = mu2 > mu1 ? mu1 : (mu2 < mu3 ? mu3 : mu2);
     e.mu[0] = mu1; e.mu[1] = mu2; e.mu[2] = mu3;

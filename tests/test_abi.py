@@ -54,7 +54,7 @@ def test_validate_config(pkg):
         assert pkg.lib().bridge_validate_config(ctypes.byref(bad)) == pkg.BRIDGE_EINVAL, field
         assert pkg.lib().bridge_workspace_bytes(ctypes.byref(bad)) == 0
     big64 = pkg.make_config(512, 2000.0, pk_amp=1.0, precision=pkg.BRIDGE_FP64)
-    assert pkg.lib().bridge_validate_config(ctypes.byref(big64)) == pkg.BRIDGE_EINVAL
+    assert pkg.lib().bridge_validate_config(ctypes.byref(big64)) == pkg.BRIDGE_OK
     assert pkg.lib().bridge_validate_config(None) == pkg.BRIDGE_EINVAL
 
 

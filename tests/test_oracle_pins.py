@@ -85,6 +85,33 @@ def test_power_spectrum_rolloff_closed_forms():
     assert abs(slope(1e-5 * kc, 2e-5 * kc) - ns) < 1e-8
 
 
+def test_wiener_init_matches_dense_real_space_filter():
+    """Sect. 2.2 initialisation against the textbook Wiener filter written with dense matrices
+    in real space on a 4^3 mesh: signal covariance S of D delta0 (columns of the brute-force-
+    pinned white-noise map applied to unit vectors, S = D^2 A A^T), noise N = (N^3 / N_tr) I
+    (Poisson variance of n* N^3 / N_tr per cell), estimate s = S (S + N)^-1 delta*_tr; then
+    delta0 = s / D and nu = A^+ delta0 (least-squares solve).  Independent of the Fourier-space
+    form of the filter and of its shot-noise power L^3 / N_tr."""
+    n = 4
+    cfg = small_cfg(n=n, box=60.0, n_regions=4, growth_d=0.8)
+    counts = np.random.default_rng(41).poisson(3.0, (n, n, n)).astype(np.int32)
+    got = model.wiener_init(counts, cfg).ravel()
+    m = n ** 3
+    A = np.zeros((m, m))
+    for i in range(m):
+        e = np.zeros(m)
+        e[i] = 1.0
+        A[:, i] = model.delta0_from_nu(torch.tensor(e.reshape(n, n, n)), cfg).numpy().ravel()
+    D = cfg.growth_d
+    S = D * D * A @ A.T
+    ntr = counts.sum()
+    d = counts.ravel() * (m / ntr) - 1.0
+    s = S @ np.linalg.solve(S + (m / ntr) * np.eye(m), d)
+    nu = np.linalg.lstsq(A, s / D, rcond=1e-12)[0]
+    np.testing.assert_allclose(got, nu - nu.mean(), rtol=1e-8, atol=1e-10)
+    assert abs(got.mean()) < 1e-12
+
+
 def test_delta0_at_cells_matches_the_full_inverse_transform():
     """The inverse DFT written out cell by cell equals the library inverse FFT of the same
     spectrum (itself pinned by the brute-force DFT above), including cells on the Nyquist
