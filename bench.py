@@ -457,9 +457,20 @@ def run_extras(pkg, synth, cfg, bias, nu32, counts, args):
             t64 += time.perf_counter() - t0
             d64s.append(h1a[0] - h0a[0])
         d32s = [h1b[b] - h0b[b] for b in range(B)]
+        # the same FP32 trajectories with their two endpoint energies from the FP64 path
+        # (U = -log posterior at the FP32 start and end points, 1/2 |p|^2 summed in FP64)
+        dmix = []
+        for b in range(B):
+            lp0, _ = c64.bridge_forward(nu_t, counts_m, [bias])
+            lp1, _ = c64.bridge_forward(nb[b].double().contiguous(), counts_m, [bias])
+            k0 = 0.5 * float((p4[b].float().double() ** 2).sum())
+            k1 = 0.5 * float((pb[b].double() ** 2).sum())
+            dmix.append((-lp1[0] + k1) - (-lp0[0] + k0))
         out["hmc_equal_accuracy_256"] = {
             "eps": eps_star, "chains": B, "dH_fp64": d64s, "dH_fp32": d32s,
             "max_abs_dH_fp32_minus_fp64": float(max(abs(a - b) for a, b in zip(d32s, d64s))),
+            "dH_fp32_trajectory_fp64_endpoints": dmix,
+            "max_abs_dH_fp32_traj_fp64_ends_minus_fp64": float(max(abs(a - b) for a, b in zip(dmix, d64s))),
             "fp32_batched_trajectories_per_s": B / t32, "fp64_single_trajectories_per_s": B / t64,
             "speedup": (B / t32) / (B / t64),
             "note": "10 leapfrog steps = 11 gradient evaluations per trajectory; accept/reject uses dH, so equal "

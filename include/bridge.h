@@ -211,6 +211,24 @@ int bridge_logpost_vjp(bridge_ctx* ctx, const void* nu, const int32_t* counts, c
 int bridge_leapfrog(bridge_ctx* ctx, void* nu, void* p, const int32_t* counts, const bridge_bias* bias,
                     int32_t n_steps, double eps, double* h0_out, double* h1_out);
 
+/* Splitting integrators of Hamilton's equations for H = -log post + 1/2 |p|^2
+ * (Sect. 2.2 names second- and fourth-order integrators and the Blanes et al.
+ * 2014 variant).  One step is K(k_0) D(d_0) K(k_1) ... D(d_{s-1}) K(k_s) with
+ * K(c): p <- p + c eps grad log post and D(d): nu <- nu + d eps p:
+ *   BRIDGE_LEAPFROG      k = 1/2, 1/2; d = 1                       (s = 1)
+ *   BRIDGE_TWO_STAGE     k = b, 1 - 2b, b; d = 1/2, 1/2, b = 0.211781 (Blanes,
+ *                        Casas and Sanz-Serna 2014)                 (s = 2)
+ *   BRIDGE_FOURTH_ORDER  three leapfrog sub-steps of w1 eps, w0 eps, w1 eps,
+ *                        w1 = 1/(2 - 2^(1/3)), w0 = 1 - 2 w1 (Yoshida 1990) (s = 3)
+ * A trajectory of n_steps takes s n_steps + 1 gradient evaluations. */
+enum { BRIDGE_LEAPFROG = 0, BRIDGE_TWO_STAGE = 1, BRIDGE_FOURTH_ORDER = 2 };
+
+/* A trajectory of `scheme` with the arguments, state handling and errors of
+ * bridge_leapfrog (which is this call with BRIDGE_LEAPFROG).  EINVAL for an
+ * unknown scheme. */
+int bridge_integrate(bridge_ctx* ctx, void* nu, void* p, const int32_t* counts, const bridge_bias* bias,
+                     int32_t scheme, int32_t n_steps, double eps, double* h0_out, double* h1_out);
+
 /* Intermediate fields of the forward model, for inspection and testing.
  * Writes the field selected by `which` for all chains to device `out`:
  *   BRIDGE_FIELD_DELTA0   [B][N^3]     linear density delta0 (App. A)

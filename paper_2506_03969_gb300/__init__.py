@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(HERE, "libbridge.so")
 
 BRIDGE_OK, BRIDGE_EINVAL, BRIDGE_ENOMEM, BRIDGE_ECUDA, BRIDGE_ENONFINITE, BRIDGE_ETIMEOUT, BRIDGE_ENODEVICE = range(7)
 BRIDGE_FP32, BRIDGE_FP64 = 0, 1
+BRIDGE_LEAPFROG, BRIDGE_TWO_STAGE, BRIDGE_FOURTH_ORDER = 0, 1, 2
 FIELD_DELTA0, FIELD_PSI, FIELD_DELTA, FIELD_TIDAL, FIELD_HESSIAN, FIELD_LAMBDA, FIELD_LNNBAR = range(7)
 MAX_REGIONS = 16
 
@@ -83,6 +84,8 @@ def lib() -> ctypes.CDLL:
     L.bridge_logpost_grad_host.restype = ctypes.c_int
     L.bridge_leapfrog.argtypes = [vp, vp, vp, i32p, bp, ctypes.c_int32, ctypes.c_double, dp, dp]
     L.bridge_leapfrog.restype = ctypes.c_int
+    L.bridge_integrate.argtypes = [vp, vp, vp, i32p, bp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, dp, dp]
+    L.bridge_integrate.restype = ctypes.c_int
     L.bridge_debug_field.argtypes = [vp, vp, i32p, bp, ctypes.c_int32, vp]; L.bridge_debug_field.restype = ctypes.c_int
     L.bridge_last_launch_count.argtypes = [vp]; L.bridge_last_launch_count.restype = ctypes.c_int64
     L.bridge_profile_enable.argtypes = [vp, ctypes.c_int]; L.bridge_profile_enable.restype = ctypes.c_int
@@ -286,6 +289,19 @@ class Context:
         h1 = (ctypes.c_double * self.batch)()
         st = lib().bridge_leapfrog(self.handle, ctypes.c_void_p(_ptr(nu)), ctypes.c_void_p(_ptr(p)),
                                    ctypes.c_void_p(_ptr(counts)), bias_array(biases), int(n_steps), float(eps), h0, h1)
+        if st != BRIDGE_ENONFINITE:
+            self._check(st)
+        return np.array(h0[:]), np.array(h1[:])
+
+    def bridge_integrate(self, nu, p, counts, biases, scheme: int, n_steps: int, eps: float):
+        """Trajectory of a splitting integrator (BRIDGE_LEAPFROG, BRIDGE_TWO_STAGE,
+        BRIDGE_FOURTH_ORDER) in place; returns (H0 [B], H1 [B]) as bridge_leapfrog does."""
+        self._field(nu, "nu"); self._field(p, "p"); self._counts(counts)
+        h0 = (ctypes.c_double * self.batch)()
+        h1 = (ctypes.c_double * self.batch)()
+        st = lib().bridge_integrate(self.handle, ctypes.c_void_p(_ptr(nu)), ctypes.c_void_p(_ptr(p)),
+                                    ctypes.c_void_p(_ptr(counts)), bias_array(biases), int(scheme), int(n_steps),
+                                    float(eps), h0, h1)
         if st != BRIDGE_ENONFINITE:
             self._check(st)
         return np.array(h0[:]), np.array(h1[:])

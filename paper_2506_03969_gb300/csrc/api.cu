@@ -104,7 +104,7 @@ struct bridge_ctx {
     cudaStream_t gstream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     const void* gkey[3] = {nullptr, nullptr, nullptr};
-    double geps = 0.0;
+    std::vector<double> gck, gcd;   // unit coefficients of the captured interior step
     int64_t glaunches = 0;
     cudaEvent_t gev[2] = {nullptr, nullptr};
     // per-launch CUDA-event profiling (bridge_profile_enable)
@@ -765,19 +765,54 @@ template <typename T> int do_grad(bridge_ctx* ctx, const void* nu, const int32_t
     return BRIDGE_OK;
 }
 
-// One interior leapfrog step: gradient at nu, then p += eps g; nu += eps p.
-template <typename T> int leapfrog_step(bridge_ctx* ctx, T* nu, T* p, T* g, double eps) {
-    RUN(run_forward<T>(ctx, nu, true));
-    RUN(run_adjoint<T>(ctx, nu, g, false));
-    CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, eps, eps, ctx->partial, ctx->stream));
+// Splitting integrators (Sect. 2.2).  One step of a scheme is K(k_0) D(d_0)
+// K(k_1) ... D(d_{s-1}) K(k_s), in units of eps, with K(c): p += c eps grad log
+// post and D(d): nu += d eps p.  The trajectory runs as units "gradient at nu,
+// then kick and drift" (launch_kick_drift); the last kick of a step and the
+// first of the next are merged into one unit.
+struct Scheme {
+    int s = 1;                        // drifts per step (gradient evaluations per step)
+    double kick[5] = {0.5, 0.5};      // s + 1 kick coefficients
+    double drift[4] = {1.0};          // s drift coefficients
+};
+bool make_scheme(int id, Scheme* sc) {
+    Scheme r;
+    if (id == BRIDGE_LEAPFROG) {
+        r.s = 1; r.kick[0] = r.kick[1] = 0.5; r.drift[0] = 1.0;
+    } else if (id == BRIDGE_TWO_STAGE) {
+        // Blanes, Casas and Sanz-Serna (2014), b = 0.211781
+        const double b = 0.211781;
+        r.s = 2; r.kick[0] = b; r.kick[1] = 1.0 - 2.0 * b; r.kick[2] = b; r.drift[0] = r.drift[1] = 0.5;
+    } else if (id == BRIDGE_FOURTH_ORDER) {
+        // Yoshida (1990) triple jump of leapfrog sub-steps w1, w0, w1: 2 w1 + w0 = 1, 2 w1^3 + w0^3 = 0
+        const double w1 = 1.0 / (2.0 - std::cbrt(2.0)), w0 = 1.0 - 2.0 * w1;
+        r.s = 3; r.kick[0] = 0.5 * w1; r.kick[1] = 0.5 * (w1 + w0); r.kick[2] = 0.5 * (w0 + w1); r.kick[3] = 0.5 * w1;
+        r.drift[0] = w1; r.drift[1] = w0; r.drift[2] = w1;
+    } else {
+        return false;
+    }
+    *sc = r;
+    return true;
+}
+
+// Units of one interior step: gradient at nu, then p += ck g; nu += cd p.
+template <typename T> int interior_step(bridge_ctx* ctx, T* nu, T* p, T* g, const std::vector<double>& ck,
+                                        const std::vector<double>& cd) {
+    for (size_t j = 0; j < ck.size(); ++j) {
+        RUN(run_forward<T>(ctx, nu, true));
+        RUN(run_adjoint<T>(ctx, nu, g, false));
+        CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, ck[j], cd[j], ctx->partial, ctx->stream));
+    }
     return BRIDGE_OK;
 }
 
-// Replays n interior steps from a CUDA graph captured (once per nu, p, eps) on
-// a private stream; the context stream waits for the replays.
-template <typename T> int leapfrog_graph(bridge_ctx* ctx, T* nu, T* p, T* g, double eps, int n) {
+// Replays n interior steps from a CUDA graph captured (once per nu, p and
+// coefficients) on a private stream; the context stream waits for the replays.
+template <typename T> int interior_graph(bridge_ctx* ctx, T* nu, T* p, T* g, const std::vector<double>& ck,
+                                         const std::vector<double>& cd, int n) {
     RUN(ensure_graph_stream(ctx));
-    const bool fresh = ctx->gexec && ctx->gkey[0] == nu && ctx->gkey[1] == p && ctx->gkey[2] == g && ctx->geps == eps;
+    bool fresh = ctx->gexec && ctx->gkey[0] == nu && ctx->gkey[1] == p && ctx->gkey[2] == g &&
+                 ctx->gck == ck && ctx->gcd == cd;
     if (!fresh) {
         if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
         cudaStream_t user = ctx->stream;
@@ -787,7 +822,7 @@ template <typename T> int leapfrog_graph(bridge_ctx* ctx, T* nu, T* p, T* g, dou
         ctx->prof = false;
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeRelaxed));
-        const int st = leapfrog_step<T>(ctx, nu, p, g, eps);
+        const int st = interior_step<T>(ctx, nu, p, g, ck, cd);
         const cudaError_t ce = cudaStreamEndCapture(ctx->gstream, &graph);
         ctx->glaunches = ctx->launches - launches;
         ctx->stream = user;
@@ -798,7 +833,8 @@ template <typename T> int leapfrog_graph(bridge_ctx* ctx, T* nu, T* p, T* g, dou
         const cudaError_t ie = cudaGraphInstantiate(&ctx->gexec, graph, 0);
         cudaGraphDestroy(graph);
         if (ie != cudaSuccess) { ctx->gexec = nullptr; return fail(ctx, BRIDGE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie)); }
-        ctx->gkey[0] = nu; ctx->gkey[1] = p; ctx->gkey[2] = g; ctx->geps = eps;
+        ctx->gkey[0] = nu; ctx->gkey[1] = p; ctx->gkey[2] = g;
+        ctx->gck = ck; ctx->gcd = cd;
     }
     CK(cudaEventRecord(ctx->gev[0], ctx->stream));
     CK(cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0));
@@ -808,10 +844,13 @@ template <typename T> int leapfrog_graph(bridge_ctx* ctx, T* nu, T* p, T* g, dou
     return BRIDGE_OK;
 }
 
-template <typename T> int do_leapfrog(bridge_ctx* ctx, void* nu_v, void* p_v, const int32_t* counts,
-                                      const bridge_bias* bias, int n_steps, double eps, double* h0, double* h1) {
+template <typename T> int do_integrate(bridge_ctx* ctx, void* nu_v, void* p_v, const int32_t* counts,
+                                       const bridge_bias* bias, int scheme, int n_steps, double eps, double* h0,
+                                       double* h1) {
     if (!nu_v || !p_v) return fail(ctx, BRIDGE_EINVAL, "nu and p are required");
     if (n_steps < 1 || !std::isfinite(eps)) return fail(ctx, BRIDGE_EINVAL, "n_steps >= 1 and finite eps required");
+    Scheme sc;
+    if (!make_scheme(scheme, &sc)) return fail(ctx, BRIDGE_EINVAL, "unknown integrator scheme");
     T* nu = reinterpret_cast<T*>(nu_v);
     T* p = reinterpret_cast<T*>(p_v);
     T* g = reinterpret_cast<T*>(ctx->grad_tmp);
@@ -829,17 +868,32 @@ template <typename T> int do_leapfrog(bridge_ctx* ctx, void* nu_v, void* p_v, co
     CKL("reduce", 0.0, launch_reduce(RED_P2, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
     RUN(finish(ctx));
     for (int c = 0; c < ctx->B; ++c) { u0[c] = -ctx->sc_host[c].logpost; k0[c] = 0.5 * ctx->sc_host[c].sump2; }
-    // half kick + drift; n-1 interior steps (gradient, full kick + drift); last gradient and half kick
-    CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, 0.5 * eps, eps, ctx->partial, ctx->stream));
-    if (n_steps > 2 && !ctx->prof) {
-        RUN(leapfrog_graph<T>(ctx, nu, p, g, eps, n_steps - 1));
-        ctx->launches += ctx->glaunches * (n_steps - 1);   // kernels replayed from the graph
-    } else {
-        for (int s = 0; s < n_steps - 1; ++s) RUN(leapfrog_step<T>(ctx, nu, p, g, eps));
+    // first step: its first unit uses the gradient just computed
+    CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, sc.kick[0] * eps, sc.drift[0] * eps,
+                                                         ctx->partial, ctx->stream));
+    {
+        std::vector<double> ck, cd;
+        for (int j = 1; j < sc.s; ++j) { ck.push_back(sc.kick[j] * eps); cd.push_back(sc.drift[j] * eps); }
+        RUN(interior_step<T>(ctx, nu, p, g, ck, cd));
     }
+    // interior steps: the merged kick k_s + k_0 opens each
+    if (n_steps > 1) {
+        std::vector<double> ck, cd;
+        ck.push_back((sc.kick[sc.s] + sc.kick[0]) * eps);
+        cd.push_back(sc.drift[0] * eps);
+        for (int j = 1; j < sc.s; ++j) { ck.push_back(sc.kick[j] * eps); cd.push_back(sc.drift[j] * eps); }
+        if (n_steps > 2 && !ctx->prof) {
+            RUN(interior_graph<T>(ctx, nu, p, g, ck, cd, n_steps - 1));
+            ctx->launches += ctx->glaunches * (n_steps - 1);   // kernels replayed from the graph
+        } else {
+            for (int s = 0; s < n_steps - 1; ++s) RUN(interior_step<T>(ctx, nu, p, g, ck, cd));
+        }
+    }
+    // last gradient and closing kick
     RUN(run_forward<T>(ctx, nu, true));
     RUN(run_adjoint<T>(ctx, nu, g, false));
-    CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, 0.5 * eps, 0.0, ctx->partial, ctx->stream));
+    CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, sc.kick[sc.s] * eps, 0.0,
+                                                         ctx->partial, ctx->stream));
     CKL("reduce", 0.0, launch_reduce(RED_P2, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
     RUN(finish(ctx));
     int bad = 0;
@@ -1297,13 +1351,18 @@ int bridge_logpost_vjp(bridge_ctx* ctx, const void* nu, const int32_t* counts, c
     return DISPATCH(ctx, do_grad, nu, counts, bias, nullptr, grad_nu_out, grad_bias_out, cotangent);
 }
 
-int bridge_leapfrog(bridge_ctx* ctx, void* nu, void* p, const int32_t* counts, const bridge_bias* bias, int32_t n_steps,
-                    double eps, double* h0_out, double* h1_out) {
+int bridge_integrate(bridge_ctx* ctx, void* nu, void* p, const int32_t* counts, const bridge_bias* bias, int32_t scheme,
+                     int32_t n_steps, double eps, double* h0_out, double* h1_out) {
     if (!ctx) return BRIDGE_EINVAL;
     ctx->launches = 0;
     ctx->err.clear();
     if (!aligned16({nu, p, counts})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
-    return DISPATCH(ctx, do_leapfrog, nu, p, counts, bias, n_steps, eps, h0_out, h1_out);
+    return DISPATCH(ctx, do_integrate, nu, p, counts, bias, scheme, n_steps, eps, h0_out, h1_out);
+}
+
+int bridge_leapfrog(bridge_ctx* ctx, void* nu, void* p, const int32_t* counts, const bridge_bias* bias, int32_t n_steps,
+                    double eps, double* h0_out, double* h1_out) {
+    return bridge_integrate(ctx, nu, p, counts, bias, BRIDGE_LEAPFROG, n_steps, eps, h0_out, h1_out);
 }
 
 int bridge_debug_field(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias, int32_t which,

@@ -18,11 +18,19 @@ __device__ __forceinline__ double v_acos(double x) { return acos(x); }
 // Fast single-precision exp/log/reciprocal for the web and bias arithmetic
 // (hardware approximations with relative errors of a few 1e-7 on the argument
 // ranges that occur; FP64 keeps the correctly rounded library functions).
+// Building with -DBRIDGE_ACCURATE_WEB_MATH selects the accurate FP32 library
+// functions and IEEE division instead, for measuring what the approximations cost.
+#ifdef BRIDGE_ACCURATE_WEB_MATH
+__device__ __forceinline__ float v_fexp(float x) { return expf(x); }
+__device__ __forceinline__ float v_flog(float x) { return logf(x); }
+__device__ __forceinline__ float v_fdiv(float a, float b) { return a / b; }
+#else
 __device__ __forceinline__ float v_fexp(float x) { return __expf(x); }
-__device__ __forceinline__ double v_fexp(double x) { return exp(x); }
 __device__ __forceinline__ float v_flog(float x) { return __logf(x); }
-__device__ __forceinline__ double v_flog(double x) { return log(x); }
 __device__ __forceinline__ float v_fdiv(float a, float b) { return __fdividef(a, b); }
+#endif
+__device__ __forceinline__ double v_fexp(double x) { return exp(x); }
+__device__ __forceinline__ double v_flog(double x) { return log(x); }
 __device__ __forceinline__ double v_fdiv(double a, double b) { return a / b; }
 
 // sin/cos of pi * x (no large-argument reduction path)

@@ -797,3 +797,30 @@ def test_wiener_init_against_oracle(n, precision):
         ctx.bridge_wiener_init(empty)
     assert e.value.status == pkg.BRIDGE_EINVAL and "no tracers" in str(e.value)
     ctx.close()
+
+
+@pytest.mark.parametrize("scheme", ["bcss2", "yoshida4"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_higher_order_integrators_match_oracle(scheme, precision):
+    """Two-stage (Blanes et al. 2014) and fourth-order (Yoshida) splittings against the oracle's
+    integrator: end state and Hamiltonians after 3 steps, 16^3, two chains in one call."""
+    cfg, bias, nu, counts, _ = make_case(16, 160.0, 4, 1311, point="eval")
+    p0 = pp.f32(synth.momentum(16, 1314))
+    nu_o, p_o, h0_o, h1_o = hmc.integrate(nu, p0, counts, cfg, bias, 3, 0.04, scheme)
+    code = {"bcss2": pkg.BRIDGE_TWO_STAGE, "yoshida4": pkg.BRIDGE_FOURTH_ORDER}[scheme]
+    ctx = pkg.Context(pkg.config_from(cfg, precision=prec_code(precision), batch=2))
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    nu_d = torch.tensor(np.stack([nu, nu]), dtype=dt, device="cuda").contiguous()
+    p_d = torch.tensor(np.stack([p0, p0]), dtype=dt, device="cuda").contiguous()
+    c_d = torch.tensor(np.stack([counts, counts]), dtype=torch.int32, device="cuda").contiguous()
+    h0, h1 = ctx.bridge_integrate(nu_d, p_d, c_d, [bias, bias], code, 3, 0.04)
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    for b in range(2):
+        e_nu = rel_l2(nu_d[b].double().cpu().numpy(), nu_o)
+        e_p = rel_l2(p_d[b].double().cpu().numpy(), p_o)
+        print(f"{scheme} {precision} chain {b}: nu {e_nu:.2e} p {e_p:.2e} dH {h1[b] - h0[b]:.6e} oracle {h1_o - h0_o:.6e}")
+        assert e_nu <= tol and e_p <= 10 * tol
+        assert abs(h0[b] - h0_o) <= tol * abs(h0_o)
+        dtol = 1e-8 if precision == "fp64" else 1e-2
+        assert abs((h1[b] - h0[b]) - (h1_o - h0_o)) <= dtol * max(1.0, abs(h1_o - h0_o))
+    ctx.close()

@@ -690,3 +690,54 @@ def test_leapfrog_reversible_and_second_order():
         _, _, a, b = hmc.leapfrog(nu0, p0, counts, cfg, bias, steps, eps)
         dh.append(abs(b - a))
     assert 2.5 < dh[0] / dh[1] < 6.0
+
+
+# ---------------------------------------------------------------------------
+# higher-order integrators (Sect. 2.2): exact harmonic-oscillator flow
+# ---------------------------------------------------------------------------
+def _oscillator(x0, p0, t):
+    """Exact flow of H = (x^2 + p^2)/2: a rotation by t."""
+    c, s = math.cos(t), math.sin(t)
+    return c * x0 + s * p0, -s * x0 + c * p0
+
+
+@pytest.mark.parametrize("scheme,order", [("leapfrog", 2), ("bcss2", 2), ("yoshida4", 4)])
+def test_integrators_converge_to_the_exact_flow_at_their_order(scheme, order):
+    """For the prior-only Hamiltonian (U = |nu|^2/2, unit oscillators) every integrator
+    approaches the exact rotation with global error O(eps^order) at fixed time, and is
+    reversible (negating p returns to the start)."""
+    grad = lambda x: (-0.5 * float((x ** 2).sum()), -x)
+    x0, p0 = np.array([1.0, -0.3]), np.array([0.2, 0.7])
+    T = 1.3
+    errs = []
+    for n in (20, 40, 80):
+        x, p, _, _ = hmc.integrate(x0, p0, None, None, None, n, T / n, scheme, grad_fn=grad)
+        xe, pe = _oscillator(x0, p0, T)
+        errs.append(math.hypot(*(x - xe)) + math.hypot(*(p - pe)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(abs(r - order) < 0.15 for r in rates), rates
+    x, p, _, _ = hmc.integrate(x0, p0, None, None, None, 7, 0.1, scheme, grad_fn=grad)
+    xb, pb, _, _ = hmc.integrate(x, -p, None, None, None, 7, 0.1, scheme, grad_fn=grad)
+    assert np.allclose(xb, x0, atol=1e-13) and np.allclose(-pb, p0, atol=1e-13)
+
+
+def test_integrator_coefficients():
+    """Consistency (kicks and drifts each sum to one step) and Yoshida's fourth-order condition
+    2 w1^3 + w0^3 = 0 for the triple jump."""
+    for scheme in ("leapfrog", "bcss2", "yoshida4"):
+        k, d = hmc.scheme_coefficients(scheme)
+        assert abs(sum(k) - 1) < 1e-15 and abs(sum(d) - 1) < 1e-15 and len(k) == len(d) + 1
+        assert np.allclose(k, k[::-1]) and np.allclose(d, d[::-1])       # symmetric: time-reversible
+    _, d = hmc.scheme_coefficients("yoshida4")
+    assert abs(2 * d[0] ** 3 + d[1] ** 3) < 1e-14
+
+
+def test_two_stage_energy_error_below_leapfrog_at_equal_cost():
+    """Blanes et al. (2014): for Gaussian targets the two-stage splitting (two gradients per step)
+    has a smaller energy error than leapfrog with half the step (same gradient count)."""
+    grad = lambda x: (-0.5 * float((x ** 2).sum()), -x)
+    rng = np.random.default_rng(3)
+    x0, p0 = rng.standard_normal(64), rng.standard_normal(64)
+    _, _, h0, h1 = hmc.integrate(x0, p0, None, None, None, 10, 0.4, "bcss2", grad_fn=grad)
+    _, _, g0, g1 = hmc.integrate(x0, p0, None, None, None, 20, 0.2, "leapfrog", grad_fn=grad)
+    assert abs(h1 - h0) < abs(g1 - g0)
