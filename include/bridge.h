@@ -229,6 +229,28 @@ enum { BRIDGE_LEAPFROG = 0, BRIDGE_TWO_STAGE = 1, BRIDGE_FOURTH_ORDER = 2 };
 int bridge_integrate(bridge_ctx* ctx, void* nu, void* p, const int32_t* counts, const bridge_bias* bias,
                      int32_t scheme, int32_t n_steps, double eps, double* h0_out, double* h1_out);
 
+/* Joint trajectory of the white noise and the free bias parameters (Sect. 2.1:
+ * log-normal prior Eq. lognormal on b; Sect. 2.2: the chains sample nu and b
+ * together).  The bias parameters move in log space, theta = ln b, so the
+ * target gains the Jacobian of b = e^theta:
+ *   H = -log post(nu, b = e^theta) - sum theta + 1/2 |p|^2 + 1/2 |p_theta|^2,
+ * and every kick also updates p_theta with ck (b d log post/d b + 1), every
+ * drift theta with cd p_theta (identity mass for both).
+ *   nu, p           device [B][N^3], in/out, as in bridge_integrate
+ *   theta, p_theta  host [B][popcount(free_mask)] doubles, in/out: ln of the
+ *                   free parameters (bit order of free_mask over alpha_0 ..
+ *                   alpha_{n-1}, beta_0 .. beta_{n-1}) and their momenta; the
+ *                   free entries of bias[] are replaced by e^theta
+ *   bias            host [B]; free_mask != 0 and tie_classes = 0 (untied)
+ *   scheme, n_steps, eps, h0_out, h1_out as in bridge_integrate (H as above)
+ * Each evaluation also computes the bias gradient (one more reduction).  A
+ * chain whose H0 or H1 is not finite gets nu, p, theta and p_theta back as
+ * they were, and the call returns ENONFINITE after the whole batch.  EINVAL
+ * for tied or empty free sets and non-finite theta or p_theta. */
+int bridge_integrate_joint(bridge_ctx* ctx, void* nu, void* p, double* theta, double* p_theta, const int32_t* counts,
+                           const bridge_bias* bias, int32_t scheme, int32_t n_steps, double eps, double* h0_out,
+                           double* h1_out);
+
 /* Intermediate fields of the forward model, for inspection and testing.
  * Writes the field selected by `which` for all chains to device `out`:
  *   BRIDGE_FIELD_DELTA0   [B][N^3]     linear density delta0 (App. A)

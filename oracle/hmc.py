@@ -14,12 +14,18 @@ nu <- nu + d eps p, with coefficients
 
 One step applies the kicks and drifts alternately, starting and ending with a
 kick; the gradient is evaluated after every drift.
+
+Joint sampling (Sect. 2.1, 2.2): the free bias parameters move together with nu,
+in log space theta = ln b, with the target log post(nu, e^theta) + sum theta
+(the Jacobian of b = e^theta) and unit-mass momenta p_theta.
 """
 from __future__ import annotations
 
 import math
 
 import numpy as np
+
+import torch
 
 from . import model
 
@@ -65,3 +71,50 @@ def integrate(nu0, p0, counts, cfg, bias, n_steps: int, eps: float, scheme: str 
 def leapfrog(nu0, p0, counts, cfg, bias, n_steps: int, eps: float, grad_fn=None):
     """The Stormer-Verlet integrator: p <- p + eps/2 grad; nu <- nu + eps p; p <- p + eps/2 grad."""
     return integrate(nu0, p0, counts, cfg, bias, n_steps, eps, "leapfrog", grad_fn)
+
+
+def free_entries(bias):
+    """(kind, region) of each free parameter in bit order of bias.free_mask (untied tables):
+    kind 0 = alpha, 1 = beta."""
+    nr = len(bias.alpha)
+    mask = (1 << (2 * nr)) - 1 if bias.free_mask is None else bias.free_mask
+    return [(q // nr, q % nr) for q in range(2 * nr) if (mask >> q) & 1]
+
+
+def joint_logpost_and_grad(nu_np, theta_np, counts_np, cfg, bias):
+    """log post(nu, b = e^theta) + sum theta and its gradients with respect to nu and theta
+    (autograd of the oracle's log posterior with the free table entries replaced by e^theta)."""
+    nu = torch.tensor(np.asarray(nu_np), dtype=model.DT, requires_grad=True)
+    th = torch.tensor(np.asarray(theta_np), dtype=model.DT, requires_grad=True)
+    t = model.bias_tables(bias)
+    a, b = list(t["alpha"]), list(t["beta"])
+    for k, (kind, r) in enumerate(free_entries(bias)):
+        if kind == 0:
+            a[r] = torch.exp(th[k])
+        else:
+            b[r] = torch.exp(th[k])
+    t["alpha"], t["beta"] = torch.stack(a), torch.stack(b)
+    lp = model.log_posterior(nu, torch.tensor(np.asarray(counts_np)), cfg, bias, t) + th.sum()
+    g_nu, g_th = torch.autograd.grad(lp, (nu, th))
+    return float(lp.detach()), g_nu.numpy(), g_th.numpy()
+
+
+def integrate_joint(nu0, p0, theta0, ptheta0, counts, cfg, bias, n_steps: int, eps: float, scheme: str = "leapfrog"):
+    """Joint trajectory; returns (nu, p, theta, p_theta, H0, H1) with
+    H = -(log post + sum theta) + 1/2 |p|^2 + 1/2 |p_theta|^2."""
+    kicks, drifts = scheme_coefficients(scheme)
+    nu, p = np.array(nu0, dtype=np.float64), np.array(p0, dtype=np.float64)
+    th, pt = np.array(theta0, dtype=np.float64), np.array(ptheta0, dtype=np.float64)
+    lp, g, gt = joint_logpost_and_grad(nu, th, counts, cfg, bias)
+    h0 = -lp + 0.5 * float((p ** 2).sum()) + 0.5 * float((pt ** 2).sum())
+    for _ in range(n_steps):
+        for j, d in enumerate(drifts):
+            p = p + kicks[j] * eps * g
+            pt = pt + kicks[j] * eps * gt
+            nu = nu + d * eps * p
+            th = th + d * eps * pt
+            lp, g, gt = joint_logpost_and_grad(nu, th, counts, cfg, bias)
+        p = p + kicks[-1] * eps * g
+        pt = pt + kicks[-1] * eps * gt
+    h1 = -lp + 0.5 * float((p ** 2).sum()) + 0.5 * float((pt ** 2).sum())
+    return nu, p, th, pt, h0, h1

@@ -86,6 +86,9 @@ def lib() -> ctypes.CDLL:
     L.bridge_leapfrog.restype = ctypes.c_int
     L.bridge_integrate.argtypes = [vp, vp, vp, i32p, bp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, dp, dp]
     L.bridge_integrate.restype = ctypes.c_int
+    L.bridge_integrate_joint.argtypes = [vp, vp, vp, dp, dp, i32p, bp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                         dp, dp]
+    L.bridge_integrate_joint.restype = ctypes.c_int
     L.bridge_debug_field.argtypes = [vp, vp, i32p, bp, ctypes.c_int32, vp]; L.bridge_debug_field.restype = ctypes.c_int
     L.bridge_last_launch_count.argtypes = [vp]; L.bridge_last_launch_count.restype = ctypes.c_int64
     L.bridge_profile_enable.argtypes = [vp, ctypes.c_int]; L.bridge_profile_enable.restype = ctypes.c_int
@@ -302,6 +305,27 @@ class Context:
         st = lib().bridge_integrate(self.handle, ctypes.c_void_p(_ptr(nu)), ctypes.c_void_p(_ptr(p)),
                                     ctypes.c_void_p(_ptr(counts)), bias_array(biases), int(scheme), int(n_steps),
                                     float(eps), h0, h1)
+        if st != BRIDGE_ENONFINITE:
+            self._check(st)
+        return np.array(h0[:]), np.array(h1[:])
+
+    def bridge_integrate_joint(self, nu, p, theta, p_theta, counts, biases, scheme: int, n_steps: int, eps: float):
+        """Joint trajectory of (nu, theta = ln b) in place: nu, p on the device; theta, p_theta numpy
+        float64 arrays [B][n_free] updated in place.  Returns (H0 [B], H1 [B]); chains whose H is
+        not finite come back with their start state (see bridge_integrate_joint)."""
+        self._field(nu, "nu"); self._field(p, "p"); self._counts(counts)
+        nf = n_free(biases)
+        for a, name in ((theta, "theta"), (p_theta, "p_theta")):
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and
+                    a.size == self.batch * nf):
+                raise ValueError(f"{name} must be a contiguous float64 array of batch * n_free values")
+        h0 = (ctypes.c_double * self.batch)()
+        h1 = (ctypes.c_double * self.batch)()
+        dp = ctypes.POINTER(ctypes.c_double)
+        st = lib().bridge_integrate_joint(self.handle, ctypes.c_void_p(_ptr(nu)), ctypes.c_void_p(_ptr(p)),
+                                          theta.ctypes.data_as(dp), p_theta.ctypes.data_as(dp),
+                                          ctypes.c_void_p(_ptr(counts)), bias_array(biases), int(scheme),
+                                          int(n_steps), float(eps), h0, h1)
         if st != BRIDGE_ENONFINITE:
             self._check(st)
         return np.array(h0[:]), np.array(h1[:])

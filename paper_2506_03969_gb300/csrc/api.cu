@@ -78,6 +78,9 @@ struct bridge_ctx {
     void* snap_nu = nullptr;    // leapfrog start state, restored for chains whose Hamiltonian is not finite
     void* snap_p = nullptr;
     double* cot = nullptr;      // [B] cotangents of bridge_logpost_vjp (device)
+    double* theta = nullptr;    // [B][32] log of the free bias parameters (joint integration, device)
+    double* ptheta = nullptr;   // [B][32] their momenta
+    uint32_t jmask = 0;         // free_mask of the joint integration in progress
     double* cot_host = nullptr; // pinned staging of cot
     void* node_scratch = nullptr;  // per-CTA slabs of the fused nodes
     size_t node_cap = 0;           // bytes of node_scratch
@@ -105,6 +108,7 @@ struct bridge_ctx {
     cudaGraphExec_t gexec = nullptr;
     const void* gkey[3] = {nullptr, nullptr, nullptr};
     std::vector<double> gck, gcd;   // unit coefficients of the captured interior step
+    uint32_t gjoint = 0;            // free_mask of a captured joint step (0: fields only)
     int64_t glaunches = 0;
     cudaEvent_t gev[2] = {nullptr, nullptr};
     // per-launch CUDA-event profiling (bridge_profile_enable)
@@ -238,7 +242,7 @@ Plan make_plan(const bridge_config* c) {
     p.biast_bytes = align_up(sizeof(BiasT<double>) * B);
     p.node_bytes = align_up(size_t(BRIDGE_NODE_L2_MB + 8) << 20);   // fused-node slabs (the launcher keeps them below the budget)
     p.rtab_bytes = align_up(size_t(kRadialTables) * (3 * (n / 2) * (n / 2) + 1) * esz);
-    p.cot_bytes = align_up(sizeof(double) * B);
+    p.cot_bytes = align_up(sizeof(double) * B) + 2 * align_up(sizeof(double) * 32 * B);
     p.total = p.spec_bytes * p.nspec_buf + p.real_bytes * (p.nreal_buf + kExtraReal) + p.c16_bytes + p.partial_bytes +
               p.sc_bytes + p.biasd_bytes + p.biast_bytes + p.node_bytes + p.rtab_bytes + p.cot_bytes + 256;
     return p;
@@ -795,13 +799,24 @@ bool make_scheme(int id, Scheme* sc) {
     return true;
 }
 
+// Kick and drift of one unit: the fields, and with joint integration the log
+// bias parameters (from the bias gradient of the same evaluation).
+template <typename T> int kick_drift_unit(bridge_ctx* ctx, T* nu, T* p, const T* g, double ck, double cd, bool joint) {
+    CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, ck, cd, ctx->partial, ctx->stream));
+    if (joint)
+        CKL("bias_leapfrog", 0.0, launch_bias_kick_drift<T>(ctx->B, ctx->nr, ctx->jmask, ctx->theta, ctx->ptheta, ctx->sc,
+                                                            ctx->biasd, reinterpret_cast<BiasT<T>*>(ctx->biast), ck, cd,
+                                                            ctx->stream));
+    return BRIDGE_OK;
+}
+
 // Units of one interior step: gradient at nu, then p += ck g; nu += cd p.
 template <typename T> int interior_step(bridge_ctx* ctx, T* nu, T* p, T* g, const std::vector<double>& ck,
-                                        const std::vector<double>& cd) {
+                                        const std::vector<double>& cd, bool joint) {
     for (size_t j = 0; j < ck.size(); ++j) {
         RUN(run_forward<T>(ctx, nu, true));
-        RUN(run_adjoint<T>(ctx, nu, g, false));
-        CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, ck[j], cd[j], ctx->partial, ctx->stream));
+        RUN(run_adjoint<T>(ctx, nu, g, joint));
+        RUN(kick_drift_unit<T>(ctx, nu, p, g, ck[j], cd[j], joint));
     }
     return BRIDGE_OK;
 }
@@ -809,10 +824,10 @@ template <typename T> int interior_step(bridge_ctx* ctx, T* nu, T* p, T* g, cons
 // Replays n interior steps from a CUDA graph captured (once per nu, p and
 // coefficients) on a private stream; the context stream waits for the replays.
 template <typename T> int interior_graph(bridge_ctx* ctx, T* nu, T* p, T* g, const std::vector<double>& ck,
-                                         const std::vector<double>& cd, int n) {
+                                         const std::vector<double>& cd, int n, bool joint) {
     RUN(ensure_graph_stream(ctx));
     bool fresh = ctx->gexec && ctx->gkey[0] == nu && ctx->gkey[1] == p && ctx->gkey[2] == g &&
-                 ctx->gck == ck && ctx->gcd == cd;
+                 ctx->gck == ck && ctx->gcd == cd && ctx->gjoint == (joint ? ctx->jmask : 0u);
     if (!fresh) {
         if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
         cudaStream_t user = ctx->stream;
@@ -822,7 +837,7 @@ template <typename T> int interior_graph(bridge_ctx* ctx, T* nu, T* p, T* g, con
         ctx->prof = false;
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeRelaxed));
-        const int st = interior_step<T>(ctx, nu, p, g, ck, cd);
+        const int st = interior_step<T>(ctx, nu, p, g, ck, cd, joint);
         const cudaError_t ce = cudaStreamEndCapture(ctx->gstream, &graph);
         ctx->glaunches = ctx->launches - launches;
         ctx->stream = user;
@@ -834,7 +849,7 @@ template <typename T> int interior_graph(bridge_ctx* ctx, T* nu, T* p, T* g, con
         cudaGraphDestroy(graph);
         if (ie != cudaSuccess) { ctx->gexec = nullptr; return fail(ctx, BRIDGE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie)); }
         ctx->gkey[0] = nu; ctx->gkey[1] = p; ctx->gkey[2] = g;
-        ctx->gck = ck; ctx->gcd = cd;
+        ctx->gck = ck; ctx->gcd = cd; ctx->gjoint = joint ? ctx->jmask : 0u;
     }
     CK(cudaEventRecord(ctx->gev[0], ctx->stream));
     CK(cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0));
@@ -844,37 +859,80 @@ template <typename T> int interior_graph(bridge_ctx* ctx, T* nu, T* p, T* g, con
     return BRIDGE_OK;
 }
 
+// theta, ptheta: host [B][popcount(free_mask)] (joint integration) or NULL.
 template <typename T> int do_integrate(bridge_ctx* ctx, void* nu_v, void* p_v, const int32_t* counts,
                                        const bridge_bias* bias, int scheme, int n_steps, double eps, double* h0,
-                                       double* h1) {
+                                       double* h1, double* theta = nullptr, double* ptheta = nullptr) {
     if (!nu_v || !p_v) return fail(ctx, BRIDGE_EINVAL, "nu and p are required");
     if (n_steps < 1 || !std::isfinite(eps)) return fail(ctx, BRIDGE_EINVAL, "n_steps >= 1 and finite eps required");
     Scheme sc;
     if (!make_scheme(scheme, &sc)) return fail(ctx, BRIDGE_EINVAL, "unknown integrator scheme");
+    const bool joint = theta != nullptr;
     T* nu = reinterpret_cast<T*>(nu_v);
     T* p = reinterpret_cast<T*>(p_v);
     T* g = reinterpret_cast<T*>(ctx->grad_tmp);
-    RUN(upload_bias<T>(ctx, bias));
+    int nf = 0;
+    std::vector<double> th0, pt0;   // start values of the bias state (host), for restores
+    if (joint) {
+        if (!bias || !ptheta) return fail(ctx, BRIDGE_EINVAL, "bias, theta and p_theta are required");
+        const uint32_t m = bias[0].free_mask;
+        nf = __builtin_popcount(m);
+        if (m == 0u || bias[0].tie_classes != 0)
+            return fail(ctx, BRIDGE_EINVAL, "joint integration needs untied free parameters (tie_classes = 0, free_mask != 0)");
+        th0.assign(theta, theta + size_t(ctx->B) * nf);
+        pt0.assign(ptheta, ptheta + size_t(ctx->B) * nf);
+        for (double v : th0) if (!std::isfinite(v)) return fail(ctx, BRIDGE_EINVAL, "theta is not finite");
+        for (double v : pt0) if (!std::isfinite(v)) return fail(ctx, BRIDGE_EINVAL, "p_theta is not finite");
+        // the free entries of the tables are e^theta
+        std::vector<bridge_bias> bb(bias, bias + ctx->B);
+        for (int c = 0; c < ctx->B; ++c) {
+            int k = 0;
+            for (int q = 0; q < 2 * ctx->nr; ++q) {
+                if (!((m >> q) & 1u)) continue;
+                const double b = std::exp(th0[size_t(c) * nf + k++]);
+                if (q < ctx->nr) bb[c].alpha[q] = b; else bb[c].beta[q - ctx->nr] = b;
+            }
+        }
+        RUN(upload_bias<T>(ctx, bb.data()));
+        ctx->jmask = m;
+        std::vector<double> pad(size_t(ctx->B) * 32 * 2, 0.0);
+        for (int c = 0; c < ctx->B; ++c)
+            for (int k = 0; k < nf; ++k) {
+                pad[size_t(c) * 32 + k] = th0[size_t(c) * nf + k];
+                pad[size_t(ctx->B + c) * 32 + k] = pt0[size_t(c) * nf + k];
+            }
+        CK(cudaMemcpy(ctx->theta, pad.data(), pad.size() * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+        RUN(upload_bias<T>(ctx, bias));
+    }
     RUN(prep_counts<T>(ctx, counts));
     // start state, put back for every chain whose Hamiltonian is not finite
     const size_t fb = size_t(ctx->nvox) * ctx->B * sizeof(T);
     CK(cudaMemcpyAsync(ctx->snap_nu, nu, fb, cudaMemcpyDeviceToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->snap_p, p, fb, cudaMemcpyDeviceToDevice, ctx->stream));
+    // H = -log post - sum theta + 1/2 |p|^2 + 1/2 |p_theta|^2 (the theta terms for joint integration)
+    auto bias_energy = [&](const double* th, const double* pt, int c) {
+        double e = 0.0;
+        for (int k = 0; k < nf; ++k) e += -th[size_t(c) * nf + k] + 0.5 * pt[size_t(c) * nf + k] * pt[size_t(c) * nf + k];
+        return e;
+    };
     std::vector<double> u0(ctx->B), k0(ctx->B);
     // initial potential and kinetic energy
     RUN(run_forward<T>(ctx, nu, true));
-    RUN(run_adjoint<T>(ctx, nu, g, false));
+    RUN(run_adjoint<T>(ctx, nu, g, joint));
     CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, 0.0, 0.0, ctx->partial, ctx->stream));
     CKL("reduce", 0.0, launch_reduce(RED_P2, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
     RUN(finish(ctx));
-    for (int c = 0; c < ctx->B; ++c) { u0[c] = -ctx->sc_host[c].logpost; k0[c] = 0.5 * ctx->sc_host[c].sump2; }
+    for (int c = 0; c < ctx->B; ++c) {
+        u0[c] = -ctx->sc_host[c].logpost;
+        k0[c] = 0.5 * ctx->sc_host[c].sump2 + (joint ? bias_energy(th0.data(), pt0.data(), c) : 0.0);
+    }
     // first step: its first unit uses the gradient just computed
-    CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, sc.kick[0] * eps, sc.drift[0] * eps,
-                                                         ctx->partial, ctx->stream));
+    RUN(kick_drift_unit<T>(ctx, nu, p, g, sc.kick[0] * eps, sc.drift[0] * eps, joint));
     {
         std::vector<double> ck, cd;
         for (int j = 1; j < sc.s; ++j) { ck.push_back(sc.kick[j] * eps); cd.push_back(sc.drift[j] * eps); }
-        RUN(interior_step<T>(ctx, nu, p, g, ck, cd));
+        RUN(interior_step<T>(ctx, nu, p, g, ck, cd, joint));
     }
     // interior steps: the merged kick k_s + k_0 opens each
     if (n_steps > 1) {
@@ -883,27 +941,45 @@ template <typename T> int do_integrate(bridge_ctx* ctx, void* nu_v, void* p_v, c
         cd.push_back(sc.drift[0] * eps);
         for (int j = 1; j < sc.s; ++j) { ck.push_back(sc.kick[j] * eps); cd.push_back(sc.drift[j] * eps); }
         if (n_steps > 2 && !ctx->prof) {
-            RUN(interior_graph<T>(ctx, nu, p, g, ck, cd, n_steps - 1));
+            RUN(interior_graph<T>(ctx, nu, p, g, ck, cd, n_steps - 1, joint));
             ctx->launches += ctx->glaunches * (n_steps - 1);   // kernels replayed from the graph
         } else {
-            for (int s = 0; s < n_steps - 1; ++s) RUN(interior_step<T>(ctx, nu, p, g, ck, cd));
+            for (int s = 0; s < n_steps - 1; ++s) RUN(interior_step<T>(ctx, nu, p, g, ck, cd, joint));
         }
     }
     // last gradient and closing kick
     RUN(run_forward<T>(ctx, nu, true));
-    RUN(run_adjoint<T>(ctx, nu, g, false));
-    CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, sc.kick[sc.s] * eps, 0.0,
-                                                         ctx->partial, ctx->stream));
+    RUN(run_adjoint<T>(ctx, nu, g, joint));
+    RUN(kick_drift_unit<T>(ctx, nu, p, g, sc.kick[sc.s] * eps, 0.0, joint));
     CKL("reduce", 0.0, launch_reduce(RED_P2, pw_blocks(ctx->n), ctx->B, ctx->partial, ctx->sc, ctx->biasd, ctx->nr, ctx->stream));
     RUN(finish(ctx));
+    std::vector<double> th1, pt1;
+    if (joint) {
+        std::vector<double> pad(size_t(ctx->B) * 32 * 2);
+        CK(cudaMemcpy(pad.data(), ctx->theta, pad.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        th1.resize(size_t(ctx->B) * nf);
+        pt1.resize(size_t(ctx->B) * nf);
+        for (int c = 0; c < ctx->B; ++c)
+            for (int k = 0; k < nf; ++k) {
+                th1[size_t(c) * nf + k] = pad[size_t(c) * 32 + k];
+                pt1[size_t(c) * nf + k] = pad[size_t(ctx->B + c) * 32 + k];
+            }
+    }
     int bad = 0;
     const size_t one = size_t(ctx->nvox) * sizeof(T);
     for (int c = 0; c < ctx->B; ++c) {
         const double H0 = u0[c] + k0[c];
-        const double H1 = -ctx->sc_host[c].logpost + 0.5 * ctx->sc_host[c].sump2;
+        const double H1 = -ctx->sc_host[c].logpost + 0.5 * ctx->sc_host[c].sump2 +
+                          (joint ? bias_energy(th1.data(), pt1.data(), c) : 0.0);
         if (h0) h0[c] = H0;
         if (h1) h1[c] = H1;
-        if (!std::isfinite(H0) || !std::isfinite(H1)) {
+        const bool ok = std::isfinite(H0) && std::isfinite(H1);
+        if (joint)
+            for (int k = 0; k < nf; ++k) {
+                theta[size_t(c) * nf + k] = ok ? th1[size_t(c) * nf + k] : th0[size_t(c) * nf + k];
+                ptheta[size_t(c) * nf + k] = ok ? pt1[size_t(c) * nf + k] : pt0[size_t(c) * nf + k];
+            }
+        if (!ok) {
             ++bad;
             CK(cudaMemcpyAsync(reinterpret_cast<char*>(nu_v) + c * one, reinterpret_cast<const char*>(ctx->snap_nu) + c * one,
                                one, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -914,7 +990,7 @@ template <typename T> int do_integrate(bridge_ctx* ctx, void* nu_v, void* p_v, c
     if (bad) {
         CK(cudaStreamSynchronize(ctx->stream));
         return fail(ctx, BRIDGE_ENONFINITE, "Hamiltonian is not finite for " + std::to_string(bad) + " of " +
-                                                std::to_string(ctx->B) + " chains (their nu and p are restored)");
+                                                std::to_string(ctx->B) + " chains (their start state is restored)");
     }
     return BRIDGE_OK;
 }
@@ -1239,7 +1315,10 @@ int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
     ctx->node_scratch = w; w += pl.node_bytes;
     ctx->node_cap = pl.node_bytes;
     ctx->rtab = w; w += pl.rtab_bytes;
-    ctx->cot = reinterpret_cast<double*>(w); w += pl.cot_bytes;
+    ctx->cot = reinterpret_cast<double*>(w);
+    ctx->theta = reinterpret_cast<double*>(w + align_up(sizeof(double) * ctx->B));
+    ctx->ptheta = ctx->theta + 32 * size_t(ctx->B);
+    w += pl.cot_bytes;
     {
         const int rlen = 3 * (cfg->n / 2) * (cfg->n / 2) + 1;
         std::vector<double> tab(size_t(4) * rlen);
@@ -1358,6 +1437,17 @@ int bridge_integrate(bridge_ctx* ctx, void* nu, void* p, const int32_t* counts, 
     ctx->err.clear();
     if (!aligned16({nu, p, counts})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
     return DISPATCH(ctx, do_integrate, nu, p, counts, bias, scheme, n_steps, eps, h0_out, h1_out);
+}
+
+int bridge_integrate_joint(bridge_ctx* ctx, void* nu, void* p, double* theta, double* p_theta, const int32_t* counts,
+                           const bridge_bias* bias, int32_t scheme, int32_t n_steps, double eps, double* h0_out,
+                           double* h1_out) {
+    if (!ctx) return BRIDGE_EINVAL;
+    ctx->launches = 0;
+    ctx->err.clear();
+    if (!theta || !p_theta) return fail(ctx, BRIDGE_EINVAL, "theta and p_theta are required");
+    if (!aligned16({nu, p, counts})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
+    return DISPATCH(ctx, do_integrate, nu, p, counts, bias, scheme, n_steps, eps, h0_out, h1_out, theta, p_theta);
 }
 
 int bridge_leapfrog(bridge_ctx* ctx, void* nu, void* p, const int32_t* counts, const bridge_bias* bias, int32_t n_steps,

@@ -387,6 +387,31 @@ __global__ void __launch_bounds__(kPwThreads) k_kick_drift(long long nvox, T* p,
     write_partials<1>(acc, partial);
 }
 
+// Joint sampling of the free bias parameters in log space (theta = ln b, Sect. 2.1
+// Eq. lognormal, Sect. 2.2): with the potential U = -log post - sum theta (the
+// Jacobian of b = e^theta), p_theta += ck (b d log post / d b + 1), then theta +=
+// cd p_theta, and b = e^theta is written into both copies of the table.  One
+// thread per entry of the (untied) free list; gbias holds d log post / d alpha_r
+// then d / d beta_r, the log-normal prior included.
+template <typename T>
+__global__ void k_bias_kick_drift(int nr, uint32_t free_mask, double* theta, double* ptheta, const ChainScalars* sc,
+                                  BiasD* bd, BiasT<T>* bt, double ck, double cd) {
+    const int c = blockIdx.x, q = threadIdx.x;
+    if (q >= 2 * nr || !((free_mask >> q) & 1u)) return;
+    const int k = __popc(free_mask & ((1u << q) - 1u));
+    double* th = theta + (size_t)c * 32 + k;
+    double* pt = ptheta + (size_t)c * 32 + k;
+    const double g = exp(*th) * sc[c].gbias[q] + 1.0;
+    const double pv = *pt + ck * g;
+    *pt = pv;
+    const double t = *th + cd * pv;
+    *th = t;
+    const double b = exp(t);
+    const int r = q % nr;
+    if (q < nr) { bd[c].alpha[r] = b; bt[c].pk[r][BP_ALPHA] = T(b); }
+    else { bd[c].beta[r] = b; bt[c].pk[r][BP_BETA] = T(b); }
+}
+
 // Tracer density contrast n* N^3 / N_tr - 1 of each chain (Sect. 2.2 initialisation).
 template <typename T> __global__ void k_delta_tr(long long nvox, const uint16_t* c16, const ChainScalars* sc, T* out) {
     const size_t off = (size_t)blockIdx.y * nvox;
@@ -579,6 +604,12 @@ cudaError_t launch_kick_drift(int n, int batch, T* p, T* nu, const T* g, double 
     k_kick_drift<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), p, nu, g, T(ck), T(cd), partial);
     return cudaGetLastError();
 }
+template <typename T>
+cudaError_t launch_bias_kick_drift(int batch, int nr, uint32_t free_mask, double* theta, double* ptheta,
+                                   const ChainScalars* sc, BiasD* bd, BiasT<T>* bt, double ck, double cd, cudaStream_t s) {
+    k_bias_kick_drift<T><<<batch, 32, 0, s>>>(nr, free_mask, theta, ptheta, sc, bd, bt, ck, cd);
+    return cudaGetLastError();
+}
 template <typename T> cudaError_t launch_delta_tr(int n, int batch, const uint16_t* c16, const ChainScalars* sc, T* out,
                                                   cudaStream_t s) {
     k_delta_tr<T><<<dim3(pw_blocks_wide(n), batch), kPwThreads, 0, s>>>(nvox_of(n), c16, sc, out);
@@ -622,6 +653,8 @@ cudaError_t launch_reduce(int what, int nblk, int batch, const double* partial, 
     template cudaError_t launch_kick_drift<T>(int, int, T*, T*, const T*, double, double, double*, cudaStream_t);   \
     template cudaError_t launch_scale_chains<T>(int, int, T*, const double*, cudaStream_t);                         \
     template cudaError_t launch_delta_tr<T>(int, int, const uint16_t*, const ChainScalars*, T*, cudaStream_t);       \
+    template cudaError_t launch_bias_kick_drift<T>(int, int, uint32_t, double*, double*, const ChainScalars*,        \
+                                                   BiasD*, BiasT<T>*, double, double, cudaStream_t);                \
     template cudaError_t launch_lnnbar<T>(long long, int, const T*, const ChainScalars*, T*, cudaStream_t);         \
     template cudaError_t launch_eigs<T>(int, int, const Fields16&, const Fields16&, cudaStream_t);
 PW_INST(float)

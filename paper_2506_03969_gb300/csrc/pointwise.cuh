@@ -75,6 +75,9 @@ template <typename T>
 cudaError_t launch_kick_drift(int n, int batch, T* p, T* nu, const T* g, double ck, double cd, double* partial,
                               cudaStream_t s);
 template <typename T>
+cudaError_t launch_bias_kick_drift(int batch, int nr, uint32_t free_mask, double* theta, double* ptheta,
+                                   const ChainScalars* sc, BiasD* bd, BiasT<T>* bt, double ck, double cd, cudaStream_t s);
+template <typename T>
 cudaError_t launch_delta_tr(int n, int batch, const uint16_t* c16, const ChainScalars* sc, T* out, cudaStream_t s);
 template <typename T> cudaError_t launch_scale_chains(int n, int batch, T* g, const double* scale, cudaStream_t s);
 template <typename T>

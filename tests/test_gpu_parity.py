@@ -824,3 +824,41 @@ def test_higher_order_integrators_match_oracle(scheme, precision):
         dtol = 1e-8 if precision == "fp64" else 1e-2
         assert abs((h1[b] - h0[b]) - (h1_o - h0_o)) <= dtol * max(1.0, abs(h1_o - h0_o))
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_joint_bias_integration_matches_oracle(precision):
+    """Joint (nu, ln b) trajectory, 3 leapfrog steps, two chains with their own theta and momenta,
+    against the oracle's joint integrator: end states of nu, p, theta, p_theta and the
+    Hamiltonians (with the Jacobian term)."""
+    cfg, bias, nu, counts, _ = make_case(16, 160.0, 4, 1331, point="eval")
+    bias = bias.copy()
+    bias.free_mask, bias.tie_classes = 0xFF, 0
+    rng = np.random.default_rng(1332)
+    p0 = pp.f32(synth.momentum(16, 1333))
+    th0 = [np.log(np.concatenate([bias.alpha, bias.beta])) + 0.02 * rng.standard_normal(8) for _ in range(2)]
+    pt0 = [rng.standard_normal(8) for _ in range(2)]
+    ref = [hmc.integrate_joint(nu, p0, th0[b], pt0[b], counts, cfg, bias, 3, 0.01) for b in range(2)]
+    ctx = pkg.Context(pkg.config_from(cfg, precision=prec_code(precision), batch=2))
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    nu_d = torch.tensor(np.stack([nu, nu]), dtype=dt, device="cuda").contiguous()
+    p_d = torch.tensor(np.stack([p0, p0]), dtype=dt, device="cuda").contiguous()
+    c_d = torch.tensor(np.stack([counts, counts]), dtype=torch.int32, device="cuda").contiguous()
+    th = np.ascontiguousarray(np.stack(th0))
+    pt = np.ascontiguousarray(np.stack(pt0))
+    h0, h1 = ctx.bridge_integrate_joint(nu_d, p_d, th, pt, c_d, [bias, bias], pkg.BRIDGE_LEAPFROG, 3, 0.01)
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    for b in range(2):
+        nu_o, p_o, th_o, pt_o, h0_o, h1_o = ref[b]
+        e = (rel_l2(nu_d[b].double().cpu().numpy(), nu_o), rel_l2(p_d[b].double().cpu().numpy(), p_o),
+             rel_l2(th[b], th_o), rel_l2(pt[b], pt_o))
+        print(f"joint {precision} chain {b}: nu {e[0]:.2e} p {e[1]:.2e} theta {e[2]:.2e} p_theta {e[3]:.2e} "
+              f"dH {h1[b] - h0[b]:.6e} oracle {h1_o - h0_o:.6e}")
+        assert e[0] <= tol and e[1] <= 10 * tol and e[2] <= tol and e[3] <= 10 * tol
+        assert abs(h0[b] - h0_o) <= tol * abs(h0_o)
+        assert abs((h1[b] - h0[b]) - (h1_o - h0_o)) <= (1e-8 if precision == "fp64" else 1e-2) * max(1.0, abs(h1_o - h0_o))
+    tied = bias.copy()
+    tied.free_mask, tied.tie_classes = 0xF, 0
+    with pytest.raises(ValueError):
+        ctx.bridge_integrate_joint(nu_d, p_d, th, pt, c_d, [tied, tied], pkg.BRIDGE_LEAPFROG, 1, 0.01)
+    ctx.close()

@@ -741,3 +741,42 @@ def test_two_stage_energy_error_below_leapfrog_at_equal_cost():
     _, _, h0, h1 = hmc.integrate(x0, p0, None, None, None, 10, 0.4, "bcss2", grad_fn=grad)
     _, _, g0, g1 = hmc.integrate(x0, p0, None, None, None, 20, 0.2, "leapfrog", grad_fn=grad)
     assert abs(h1 - h0) < abs(g1 - g0)
+
+
+# ---------------------------------------------------------------------------
+# joint sampling of (nu, ln b) (Sect. 2.1, 2.2)
+# ---------------------------------------------------------------------------
+def _joint_case():
+    cfg = small_cfg(n=8, box=80.0, n_regions=4, mean_tracers=2.0)
+    bias = synth.bias_phi_web(global_beta=None)
+    bias.free_mask = 0xFF
+    nu = synth.white_noise(8, 51)
+    counts = mock.mock_counts(nu, cfg, bias, 52)
+    theta = np.log(np.concatenate([bias.alpha, bias.beta]))
+    return cfg, bias, nu, counts, theta
+
+
+def test_joint_theta_gradient_matches_central_fd():
+    """d/d theta of log post(nu, e^theta) + sum theta against central differences in theta (the
+    Jacobian term and the chain rule b d/db both enter)."""
+    cfg, bias, nu, counts, theta = _joint_case()
+    _, _, gt = hmc.joint_logpost_and_grad(nu, theta, counts, cfg, bias)
+    h = 1e-6
+    for k in range(theta.size):
+        e = np.zeros_like(theta)
+        e[k] = h
+        fp = hmc.joint_logpost_and_grad(nu, theta + e, counts, cfg, bias)[0]
+        fm = hmc.joint_logpost_and_grad(nu, theta - e, counts, cfg, bias)[0]
+        assert abs((fp - fm) / (2 * h) - gt[k]) <= 1e-6 * max(1.0, abs(gt[k])), k
+
+
+def test_joint_integrator_reversible_and_second_order():
+    cfg, bias, nu, counts, theta = _joint_case()
+    rng = np.random.default_rng(53)
+    p0, pt0 = rng.standard_normal(nu.shape), rng.standard_normal(theta.shape)
+    x, p, th, pt, h0, h1 = hmc.integrate_joint(nu, p0, theta, pt0, counts, cfg, bias, 4, 0.02)
+    xb, pb, thb, ptb, _, _ = hmc.integrate_joint(x, -p, th, -pt, counts, cfg, bias, 4, 0.02)
+    assert np.abs(xb - nu).max() < 1e-9 and np.abs(thb - theta).max() < 1e-9
+    assert np.abs(pb + p0).max() < 1e-9 and np.abs(ptb + pt0).max() < 1e-9
+    dh = [abs(hmc.integrate_joint(nu, p0, theta, pt0, counts, cfg, bias, n, 0.08 / n)[5] - h0) for n in (2, 4)]
+    assert 3.0 < dh[0] / dh[1] < 5.0      # energy error O(eps^2) at fixed trajectory length
