@@ -251,6 +251,24 @@ int bridge_integrate_joint(bridge_ctx* ctx, void* nu, void* p, double* theta, do
                            const bridge_bias* bias, int32_t scheme, int32_t n_steps, double eps, double* h0_out,
                            double* h1_out);
 
+/* Leapfrog steps for a sampler that drives the trajectory from the host (the
+ * No-U-Turn sampler of Sect. 2.2 grows its trajectory one step at a time in
+ * either direction).  Starting from (nu, p) and the gradient `grad` of the log
+ * posterior at nu (from bridge_logpost_grad or an earlier call), applies
+ * n_steps leapfrog steps of size eps (negative eps integrates backward):
+ *   nu, p, grad   device [B][N^3], in/out; grad returns the gradient at the new nu
+ *   logpost_out   host [B]: log posterior at the new nu; may be NULL
+ * One gradient evaluation per step; synchronises.  Non-finite values are
+ * returned as they are (the caller decides about divergence).  Errors: EINVAL,
+ * ECUDA. */
+int bridge_leapfrog_steps(bridge_ctx* ctx, void* nu, void* p, void* grad, const int32_t* counts,
+                          const bridge_bias* bias, int32_t n_steps, double eps, double* logpost_out);
+
+/* Per-chain dot product sum_i a_i b_i of two device fields [B][N^3] (float or
+ * double per precision), products and sums in FP64, into host out[B] (for a
+ * sampler's kinetic energy and U-turn test).  Synchronises. */
+int bridge_dot(bridge_ctx* ctx, const void* a, const void* b, double* out);
+
 /* Intermediate fields of the forward model, for inspection and testing.
  * Writes the field selected by `which` for all chains to device `out`:
  *   BRIDGE_FIELD_DELTA0   [B][N^3]     linear density delta0 (App. A)

@@ -118,3 +118,69 @@ def integrate_joint(nu0, p0, theta0, ptheta0, counts, cfg, bias, n_steps: int, e
         pt = pt + kicks[-1] * eps * gt
     h1 = -lp + 0.5 * float((p ** 2).sum()) + 0.5 * float((pt ** 2).sum())
     return nu, p, th, pt, h0, h1
+
+
+def nuts_step(nu0, p0, counts, cfg, bias, eps: float, rng, max_depth: int = 10, grad_fn=None, delta_max: float = 1000.0):
+    """One No-U-Turn transition (Hoffman & Gelman 2014, efficient NUTS with a slice variable) from
+    nu0 with momentum p0.  Uniform draws from rng, in the order: slice level; then per doubling
+    the direction, the subtree's proposal choices (taken only when the subtree has an admissible
+    point) and the doubling's own proposal choice (taken only when the subtree did not stop).
+    Returns (sample, depth, leapfrog steps)."""
+    if grad_fn is None:
+        def grad_fn(x):
+            lp, g, _, _ = model.logpost_and_grad(x, counts, cfg, bias)
+            return lp, g
+    steps = [0]
+
+    def leap(state, v):
+        x, r, lp, g = state
+        r = r + 0.5 * v * eps * g
+        x = x + v * eps * r
+        lp, g = grad_fn(x)
+        r = r + 0.5 * v * eps * g
+        steps[0] += 1
+        return (x, r, lp, g)
+
+    def joint(state):
+        return state[2] - 0.5 * float((state[1] ** 2).sum())
+
+    def turning(minus, plus):
+        d = plus[0] - minus[0]
+        return float((d * minus[1]).sum()) < 0.0 or float((d * plus[1]).sum()) < 0.0
+
+    def build(state, log_u, v, j):
+        if j == 0:
+            t = leap(state, v)
+            e = joint(t)
+            if not np.isfinite(e):
+                e = -np.inf
+            return t, t, t, int(log_u <= e), bool(log_u < e + delta_max)
+        minus, plus, prop, n1, ok = build(state, log_u, v, j - 1)
+        if ok:
+            if v < 0:
+                minus, _, prop2, n2, ok2 = build(minus, log_u, v, j - 1)
+            else:
+                _, plus, prop2, n2, ok2 = build(plus, log_u, v, j - 1)
+            if n1 + n2 > 0 and rng.random() < n2 / (n1 + n2):
+                prop = prop2
+            ok = ok2 and not turning(minus, plus)
+            n1 += n2
+        return minus, plus, prop, n1, ok
+
+    lp0, g0 = grad_fn(np.asarray(nu0, dtype=np.float64))
+    s0 = (np.asarray(nu0, dtype=np.float64), np.asarray(p0, dtype=np.float64), lp0, g0)
+    log_u = joint(s0) + math.log(rng.random())
+    minus = plus = sample = s0
+    n, depth, ok = 1, 0, True
+    while ok and depth < max_depth:
+        v = -1 if rng.random() < 0.5 else 1
+        if v < 0:
+            minus, _, prop, n2, ok2 = build(minus, log_u, v, depth)
+        else:
+            _, plus, prop, n2, ok2 = build(plus, log_u, v, depth)
+        if ok2 and rng.random() < min(1.0, n2 / n):
+            sample = prop
+        n += n2
+        ok = ok2 and not turning(minus, plus)
+        depth += 1
+    return sample[0], depth, steps[0]

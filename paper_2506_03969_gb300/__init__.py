@@ -86,6 +86,9 @@ def lib() -> ctypes.CDLL:
     L.bridge_leapfrog.restype = ctypes.c_int
     L.bridge_integrate.argtypes = [vp, vp, vp, i32p, bp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, dp, dp]
     L.bridge_integrate.restype = ctypes.c_int
+    L.bridge_leapfrog_steps.argtypes = [vp, vp, vp, vp, i32p, bp, ctypes.c_int32, ctypes.c_double, dp]
+    L.bridge_leapfrog_steps.restype = ctypes.c_int
+    L.bridge_dot.argtypes = [vp, vp, vp, dp]; L.bridge_dot.restype = ctypes.c_int
     L.bridge_integrate_joint.argtypes = [vp, vp, vp, dp, dp, i32p, bp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                          dp, dp]
     L.bridge_integrate_joint.restype = ctypes.c_int
@@ -329,6 +332,24 @@ class Context:
         if st != BRIDGE_ENONFINITE:
             self._check(st)
         return np.array(h0[:]), np.array(h1[:])
+
+    def bridge_leapfrog_steps(self, nu, p, grad, counts, biases, n_steps: int, eps: float):
+        """n leapfrog steps in place from (nu, p) with grad = gradient at nu (updated to the new nu);
+        returns the log posterior [B] at the new nu (non-finite values are returned, not raised)."""
+        self._field(nu, "nu"); self._field(p, "p"); self._field(grad, "grad"); self._counts(counts)
+        lp = (ctypes.c_double * self.batch)()
+        st = lib().bridge_leapfrog_steps(self.handle, ctypes.c_void_p(_ptr(nu)), ctypes.c_void_p(_ptr(p)),
+                                         ctypes.c_void_p(_ptr(grad)), ctypes.c_void_p(_ptr(counts)), bias_array(biases),
+                                         int(n_steps), float(eps), lp)
+        self._check(st)
+        return np.array(lp[:])
+
+    def bridge_dot(self, a, b):
+        """Per-chain sum a_i b_i in FP64 (host array [B])."""
+        self._field(a, "a"); self._field(b, "b")
+        out = (ctypes.c_double * self.batch)()
+        self._check(lib().bridge_dot(self.handle, ctypes.c_void_p(_ptr(a)), ctypes.c_void_p(_ptr(b)), out))
+        return np.array(out[:])
 
     def bridge_autotune(self, nu, counts, biases):
         """Pick launch shapes for this context by timing evaluations of this problem.

@@ -995,6 +995,43 @@ template <typename T> int do_integrate(bridge_ctx* ctx, void* nu_v, void* p_v, c
     return BRIDGE_OK;
 }
 
+// n leapfrog steps from (nu, p) with the gradient g at nu given; g returns the
+// gradient at the new nu.  One gradient evaluation per step; eps may be negative.
+template <typename T> int do_steps(bridge_ctx* ctx, void* nu_v, void* p_v, void* g_v, const int32_t* counts,
+                                   const bridge_bias* bias, int n, double eps, double* logpost_out) {
+    if (!nu_v || !p_v || !g_v) return fail(ctx, BRIDGE_EINVAL, "nu, p and grad are required");
+    if (n < 1 || !std::isfinite(eps)) return fail(ctx, BRIDGE_EINVAL, "n_steps >= 1 and finite eps required");
+    T* nu = reinterpret_cast<T*>(nu_v);
+    T* p = reinterpret_cast<T*>(p_v);
+    T* g = reinterpret_cast<T*>(g_v);
+    RUN(upload_bias<T>(ctx, bias));
+    RUN(prep_counts<T>(ctx, counts));
+    CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, 0.5 * eps, eps, ctx->partial, ctx->stream));
+    for (int s = 1; s < n; ++s) {
+        RUN(run_forward<T>(ctx, nu, true));
+        RUN(run_adjoint<T>(ctx, nu, g, false));
+        CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, eps, eps, ctx->partial, ctx->stream));
+    }
+    RUN(run_forward<T>(ctx, nu, true));
+    RUN(run_adjoint<T>(ctx, nu, g, false));
+    CKL("leapfrog", 5 * rby<T>(ctx), launch_kick_drift<T>(ctx->n, ctx->B, p, nu, g, 0.5 * eps, 0.0, ctx->partial, ctx->stream));
+    RUN(finish(ctx));
+    for (int c = 0; c < ctx->B; ++c)
+        if (logpost_out) logpost_out[c] = ctx->sc_host[c].logpost;
+    return BRIDGE_OK;
+}
+
+template <typename T> int do_dot(bridge_ctx* ctx, const void* a, const void* b, double* out) {
+    if (!a || !b || !out) return fail(ctx, BRIDGE_EINVAL, "a, b and out are required");
+    CKL("dot", 2 * rby<T>(ctx), launch_dot<T>(ctx->n, ctx->B, reinterpret_cast<const T*>(a), reinterpret_cast<const T*>(b),
+                                               ctx->partial, red_args(ctx), ctx->stream));
+    cudaError_t e = cudaMemcpyAsync(ctx->sc_host, ctx->sc, sizeof(ChainScalars) * ctx->B, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, BRIDGE_ECUDA, std::string("dot: ") + cudaGetErrorString(e));
+    for (int c = 0; c < ctx->B; ++c) out[c] = ctx->sc_host[c].dot;
+    return BRIDGE_OK;
+}
+
 template <typename T> int do_debug(bridge_ctx* ctx, const void* nu, const int32_t* counts, const bridge_bias* bias,
                                    int which, void* out) {
     if (!nu || !out) return fail(ctx, BRIDGE_EINVAL, "nu and out are required");
@@ -1448,6 +1485,23 @@ int bridge_integrate_joint(bridge_ctx* ctx, void* nu, void* p, double* theta, do
     if (!theta || !p_theta) return fail(ctx, BRIDGE_EINVAL, "theta and p_theta are required");
     if (!aligned16({nu, p, counts})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
     return DISPATCH(ctx, do_integrate, nu, p, counts, bias, scheme, n_steps, eps, h0_out, h1_out, theta, p_theta);
+}
+
+int bridge_leapfrog_steps(bridge_ctx* ctx, void* nu, void* p, void* grad, const int32_t* counts, const bridge_bias* bias,
+                          int32_t n_steps, double eps, double* logpost_out) {
+    if (!ctx) return BRIDGE_EINVAL;
+    ctx->launches = 0;
+    ctx->err.clear();
+    if (!aligned16({nu, p, grad, counts})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
+    return DISPATCH(ctx, do_steps, nu, p, grad, counts, bias, n_steps, eps, logpost_out);
+}
+
+int bridge_dot(bridge_ctx* ctx, const void* a, const void* b, double* out) {
+    if (!ctx) return BRIDGE_EINVAL;
+    ctx->launches = 0;
+    ctx->err.clear();
+    if (!aligned16({a, b})) return fail(ctx, BRIDGE_EINVAL, kAlignMsg);
+    return DISPATCH(ctx, do_dot, a, b, out);
 }
 
 int bridge_leapfrog(bridge_ctx* ctx, void* nu, void* p, const int32_t* counts, const bridge_bias* bias, int32_t n_steps,

@@ -387,6 +387,15 @@ __global__ void __launch_bounds__(kPwThreads) k_kick_drift(long long nvox, T* p,
     write_partials<1>(acc, partial);
 }
 
+// sum a_i b_i per chain: FP64 products, per-thread partials in FP64.
+template <typename T>
+__global__ void __launch_bounds__(kPwThreads) k_dot(long long nvox, const T* a, const T* b, double* partial, RedArgs ra) {
+    const size_t off = (size_t)blockIdx.y * nvox;
+    double acc[1] = {0.0};
+    PW_LOOP(i, nvox) acc[0] += double(a[off + i]) * double(b[off + i]);
+    finish_partials<1>(acc, partial, RED_DOT, ra);
+}
+
 // Joint sampling of the free bias parameters in log space (theta = ln b, Sect. 2.1
 // Eq. lognormal, Sect. 2.2): with the potential U = -log post - sum theta (the
 // Jacobian of b = e^theta), p_theta += ck (b d log post / d b + 1), then theta +=
@@ -516,6 +525,7 @@ __device__ void reduce_body(int what, int chain, int nblk, int K, const double* 
     if (what == RED_NTR) S.ntr = tot[0];
     else if (what == RED_SUMF) { S.sumf = tot[0]; S.lnC = log(S.ntr) - log(tot[0]); }
     else if (what == RED_P2) S.sump2 = tot[0];
+    else if (what == RED_DOT) S.dot = tot[0];
     else if (what == RED_LIK) {
         S.loglik = tot[0]; S.G = tot[1]; S.sumnu2 = tot[2];
         S.logprior = lpr;
@@ -605,6 +615,11 @@ cudaError_t launch_kick_drift(int n, int batch, T* p, T* nu, const T* g, double 
     return cudaGetLastError();
 }
 template <typename T>
+cudaError_t launch_dot(int n, int batch, const T* a, const T* b, double* partial, const RedArgs& ra, cudaStream_t s) {
+    k_dot<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), a, b, partial, ra);
+    return cudaGetLastError();
+}
+template <typename T>
 cudaError_t launch_bias_kick_drift(int batch, int nr, uint32_t free_mask, double* theta, double* ptheta,
                                    const ChainScalars* sc, BiasD* bd, BiasT<T>* bt, double ck, double cd, cudaStream_t s) {
     k_bias_kick_drift<T><<<batch, 32, 0, s>>>(nr, free_mask, theta, ptheta, sc, bd, bt, ck, cd);
@@ -653,6 +668,7 @@ cudaError_t launch_reduce(int what, int nblk, int batch, const double* partial, 
     template cudaError_t launch_kick_drift<T>(int, int, T*, T*, const T*, double, double, double*, cudaStream_t);   \
     template cudaError_t launch_scale_chains<T>(int, int, T*, const double*, cudaStream_t);                         \
     template cudaError_t launch_delta_tr<T>(int, int, const uint16_t*, const ChainScalars*, T*, cudaStream_t);       \
+    template cudaError_t launch_dot<T>(int, int, const T*, const T*, double*, const RedArgs&, cudaStream_t);         \
     template cudaError_t launch_bias_kick_drift<T>(int, int, uint32_t, double*, double*, const ChainScalars*,        \
                                                    BiasD*, BiasT<T>*, double, double, cudaStream_t);                \
     template cudaError_t launch_lnnbar<T>(long long, int, const T*, const ChainScalars*, T*, cudaStream_t);         \

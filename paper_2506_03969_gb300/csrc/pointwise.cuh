@@ -33,6 +33,7 @@ struct ChainScalars {
     double logprior;  // log-normal prior of the bias tables
     double logpost;
     double sump2;     // sum p^2 (leapfrog)
+    double dot;       // sum a b (bridge_dot)
     double gbias[32]; // d/d alpha_r then d/d beta_r
 };
 
@@ -74,6 +75,9 @@ template <typename T> cudaError_t launch_shift(long long count, const T* in, T* 
 template <typename T>
 cudaError_t launch_kick_drift(int n, int batch, T* p, T* nu, const T* g, double ck, double cd, double* partial,
                               cudaStream_t s);
+// Per-chain FP64 sum of a b (partial sums reduced by the last block into sc[chain].dot).
+template <typename T>
+cudaError_t launch_dot(int n, int batch, const T* a, const T* b, double* partial, const RedArgs& ra, cudaStream_t s);
 template <typename T>
 cudaError_t launch_bias_kick_drift(int batch, int nr, uint32_t free_mask, double* theta, double* ptheta,
                                    const ChainScalars* sc, BiasD* bd, BiasT<T>* bt, double ck, double cd, cudaStream_t s);
@@ -89,7 +93,7 @@ cudaError_t launch_eigs(int n, int batch, const Fields16& t6, const Fields16& ou
 // partial slots per chain (the grid of the kernel that wrote them).
 cudaError_t launch_reduce(int what, int nblk, int batch, const double* partial, ChainScalars* sc, const BiasD* bias,
                           int n_regions, cudaStream_t s);
-enum { RED_NTR = 0, RED_SUMF = 1, RED_LIK = 2, RED_BIASGRAD = 3, RED_P2 = 4 };
+enum { RED_NTR = 0, RED_SUMF = 1, RED_LIK = 2, RED_BIASGRAD = 3, RED_P2 = 4, RED_DOT = 5 };
 
 
 }  // namespace bridge

@@ -862,3 +862,36 @@ def test_joint_bias_integration_matches_oracle(precision):
     with pytest.raises(ValueError):
         ctx.bridge_integrate_joint(nu_d, p_d, th, pt, c_d, [tied, tied], pkg.BRIDGE_LEAPFROG, 1, 0.01)
     ctx.close()
+
+
+def test_nuts_host_driver_matches_oracle():
+    """The host-driven NUTS (paper_2506_03969_gb300.nuts) on the FP64 path against the oracle's
+    NUTS with the same seeded draws, 16^3: three transitions in a row reach the same sample, tree
+    depth and number of leapfrog steps.  An FP32 context runs the same transitions to finite
+    samples."""
+    from paper_2506_03969_gb300 import nuts
+    cfg, bias, nu, counts, _ = make_case(16, 160.0, 4, 1341, point="eval")
+    x_o = nu.copy()
+    rng_o, rng_g, rng_p = np.random.default_rng(7), np.random.default_rng(7), np.random.default_rng(8)
+    moms = [pp.f32(rng_p.standard_normal(nu.shape)) for _ in range(3)]
+    ctx, nu_d, c_d = run_gpu(cfg, bias, nu, counts, pkg.BRIDGE_FP64)
+    sampler = nuts.NUTS(ctx, c_d, [bias], eps=0.05, max_depth=6)
+    lp, g, _ = ctx.bridge_logpost_grad(nu_d, c_d, [bias], want_bias_grad=False)
+    x_g, lp_g = nu_d, float(lp[0])
+    for t in range(3):
+        x_o, depth_o, steps_o = hmc.nuts_step(x_o, moms[t], counts, cfg, bias, 0.05, rng_o, max_depth=6)
+        p_d = torch.tensor(moms[t], dtype=torch.float64, device="cuda").contiguous()
+        res = sampler.step(x_g, p_d, g, lp_g, rng_g)
+        x_g, g, lp_g = res.nu, res.grad, res.logpost
+        e = rel_l2(x_g.cpu().numpy(), x_o)
+        print(f"NUTS transition {t}: depth {res.depth} / {depth_o}, leapfrog steps {res.n_leapfrog} / {steps_o}, "
+              f"sample rel L2 {e:.2e}")
+        assert res.depth == depth_o and res.n_leapfrog == steps_o and e <= 1e-10
+    ctx.close()
+    c32, nu32, c_d = run_gpu(cfg, bias, nu, counts, pkg.BRIDGE_FP32)
+    s32 = nuts.NUTS(c32, c_d, [bias], eps=0.05, max_depth=6)
+    lp, g, _ = c32.bridge_logpost_grad(nu32, c_d, [bias], want_bias_grad=False)
+    res = s32.step(nu32, torch.tensor(moms[0], dtype=torch.float32, device="cuda").contiguous(), g, float(lp[0]),
+                   np.random.default_rng(7))
+    assert torch.isfinite(res.nu).all() and 2 ** (res.depth - 1) <= res.n_leapfrog <= 2 ** res.depth - 1
+    c32.close()

@@ -780,3 +780,21 @@ def test_joint_integrator_reversible_and_second_order():
     assert np.abs(pb + p0).max() < 1e-9 and np.abs(ptb + pt0).max() < 1e-9
     dh = [abs(hmc.integrate_joint(nu, p0, theta, pt0, counts, cfg, bias, n, 0.08 / n)[5] - h0) for n in (2, 4)]
     assert 3.0 < dh[0] / dh[1] < 5.0      # energy error O(eps^2) at fixed trajectory length
+
+
+def test_nuts_leaves_a_gaussian_invariant():
+    """The oracle's NUTS transition on a standard normal target (prior only): after many
+    transitions from a fixed start the samples have mean 0 and variance 1 (detailed balance of
+    the slice / doubling construction); trajectories stop by U-turns well before the depth cap."""
+    grad = lambda x: (-0.5 * float((x ** 2).sum()), -x)
+    rng = np.random.default_rng(61)
+    x = np.full(3, 2.0)
+    xs, depths = [], []
+    for _ in range(3000):
+        x, depth, _ = hmc.nuts_step(x, rng.standard_normal(3), None, None, None, 0.3, rng, max_depth=8, grad_fn=grad)
+        xs.append(x.copy())
+        depths.append(depth)
+    xs = np.array(xs[200:])
+    se = 3.0 / math.sqrt(len(xs))
+    assert np.all(np.abs(xs.mean(0)) < 4 * se) and np.all(np.abs(xs.var(0) - 1.0) < 0.12)
+    assert max(depths) < 8
