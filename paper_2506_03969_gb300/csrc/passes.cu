@@ -332,6 +332,9 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YP
     TL::tile_pos(blockIdx.x, kz, c0);
     const size_t base = TL::tile_base(kz, c0);
     const int g = TL::b_g(t);
+    // outputs alternate between two transpose buffers: one barrier per output (see k_x_node)
+    V* sm2 = sm + TL::SM_ELEMS;
+    int produced = 0;
     for (int s = 0; s < P.n_in; ++s) {
         bool used = false;
         for (int m = 0; m < P.n_expand; ++m) used |= (P.expand[m].src == s);
@@ -382,11 +385,11 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YP
                     }
                 }
             }
-            __syncthreads();
-            TL::invB(Y, sm, t);
+            V* smo = (produced++ & 1) ? sm2 : sm;
+            TL::invB(Y, smo, t);
             __syncthreads();
             V* dst = reinterpret_cast<V*>(P.out[tm.dst]) + chain * P.out_cs + base;
-            TL::invA(sm, dst, t);
+            TL::invA(smo, dst, t);
         }
     }
 }
@@ -504,8 +507,9 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_n
     const int g = TL::b_g(t);
     const int my = signed_freq(c0 + g, N), mz = kz;
     const int m2yz = my * my + mz * mz;
-    // x factor of the blend, when a term of the program uses it
+    // x factor of the blend, when a term of the program uses it; then the second transpose buffer
     T* skx = reinterpret_cast<T*>(sm + TL::SM_ELEMS + TL::STAGE_ELEMS);
+    V* sm2 = sm + TL::SM_ELEMS + TL::STAGE_ELEMS + (N * sizeof(T) + sizeof(V) - 1) / sizeof(V);
     bool blend = false;
     for (int m = 0; m < P.n_merge; ++m) blend |= sep_blend<T>(P.merge[m].rcode);
     for (int m = 0; m < P.n_expand; ++m) blend |= sep_blend<T>(P.expand[m].rcode);
@@ -587,11 +591,15 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_n
                 }
             }
         }
-        __syncthreads();
-        TL::invB(Y, sm, t);
+        // outputs alternate between two transpose buffers (output 0 takes the second one, so
+        // the merge loop's last reads of the first need no barrier): a thread reaches the
+        // barrier after output m only once it has finished reading the buffer of output m - 1,
+        // which output m + 1 overwrites, so one barrier per output suffices
+        V* smo = (m & 1) ? sm : sm2;
+        TL::invB(Y, smo, t);
         __syncthreads();
         V* dst = reinterpret_cast<V*>(P.out[tm.dst]) + chain * P.out_cs + base;
-        TL::invA(sm, dst, t);
+        TL::invA(smo, dst, t);
     }
 }
 
@@ -703,7 +711,7 @@ template <typename T, int N> static cudaError_t z_inv_n(int batch, const ZProgra
 template <typename T, int N, bool XM, bool FWD>
 static cudaError_t col_n(int batch, const PassProgram& p, const KParams& kp, cudaStream_t s) {
     using TL = Tile<T, N, XM>;
-    const size_t sm = size_t(TL::SM_ELEMS + (FWD ? TL::STAGE_ELEMS : 0)) * sizeof(cplx_t<T>);
+    const size_t sm = size_t(TL::SM_ELEMS + (FWD ? TL::STAGE_ELEMS : TL::SM_ELEMS)) * sizeof(cplx_t<T>);
     auto kern = FWD ? k_col_fwd<T, N, XM> : (!XM && p.accumulate ? k_col_inv_acc<T, N> : k_col_inv<T, N, XM>);
     cudaError_t e = set_smem(kern, sm);
     if (e != cudaSuccess) return e;
@@ -723,7 +731,8 @@ static cudaError_t col_n(int batch, const PassProgram& p, const KParams& kp, cud
 }
 template <typename T, int N> static cudaError_t xnode_n(int batch, const PassProgram& p, const KParams& kp, cudaStream_t s) {
     using TL = Tile<T, N, true>;
-    const size_t sm = size_t(TL::SM_ELEMS + TL::STAGE_ELEMS) * sizeof(cplx_t<T>) + N * sizeof(T);
+    const size_t sm = size_t(2 * TL::SM_ELEMS + TL::STAGE_ELEMS) * sizeof(cplx_t<T>) +
+                      ((N * sizeof(T) + sizeof(cplx_t<T>) - 1) / sizeof(cplx_t<T>)) * sizeof(cplx_t<T>);
     cudaError_t e = set_smem(k_x_node<T, N>, sm);
     if (e != cudaSuccess) return e;
     k_x_node<T, N><<<dim3(TL::TILES, batch), TL::NT, sm, s>>>(p, kp);

@@ -17,8 +17,10 @@ that every cell keeps a stated gap from the collapse threshold, and optionally
 clears the counts of near-empty cells; the result is a point where the FP64
 gradient moves by less than the FP32 bounds under an FP32 rounding of the
 input, so that a GPU/oracle difference above the bound is an error of the
-GPU path, not of the point.  Every input stays synthetic and seeded; nothing
-here reads the CUDA path.
+GPU path, not of the point.  Near-empty cells with tracers occur even in a mock
+drawn from the model itself (at 256^3 a few hundred of the 16.8M cells), and
+there they dominate the gradient: the data-consistent points clear them too.
+Every input stays synthetic and seeded; nothing here reads the CUDA path.
 """
 from __future__ import annotations
 

@@ -52,15 +52,16 @@ def rel_l2(a, b):
 
 def make_case(n, box, n_regions, seed, beta=None, mean=0.5, point="eval", gap=1e-3, **cfg_kw):
     """Workload geometry at mesh n; counts are the oracle's gamma-Poisson mock of nu_true (Sect. 3).
-    point: "truth" (nu_true, treated), "eval" (nu_true + 0.3 noise, treated and near-empty
-    counts cleared) or "raw" (nu_true + 0.3 noise as it is; only rounded to FP32)."""
+    point: "truth" (nu_true) or "eval" (nu_true + 0.3 noise), each treated -- kept off the
+    collapse threshold, near-empty counts cleared -- or "raw" (nu_true + 0.3 noise as it is;
+    only rounded to FP32)."""
     cfg = synth.Config(f"{n}^3", n, box, n_regions=n_regions, nb_beta=beta, mean_tracers=mean,
                        seed_truth=seed, seed_counts=seed + 1, seed_eval=seed + 2, **cfg_kw)
     bias = synth.default_bias(cfg)
     nu_t = synth.white_noise(n, cfg.seed_truth)
     counts = mock.mock_counts(nu_t, cfg, bias, cfg.seed_counts)
     if point == "truth":
-        nu, counts, moved, cleared = pp.condition(nu_t, counts, cfg, bias, gap=gap)
+        nu, counts, moved, cleared = pp.condition(nu_t, counts, cfg, bias, gap=gap, clear_empty=True)
     elif point == "eval":
         nu0 = synth.eval_point(n, cfg.seed_truth, cfg.seed_eval, scale=0.3 if n < 256 else 0.1)
         nu, counts, moved, cleared = pp.condition(nu0, counts, cfg, bias, gap=gap, clear_empty=True)
@@ -257,8 +258,8 @@ def test_full_size_256_against_oracle():
     bias = synth.default_bias(cfg)
     nu_t = synth.white_noise(cfg.n, cfg.seed_truth)
     counts = mock.mock_counts(nu_t, cfg, bias, cfg.seed_counts)
-    nu, c_t, moved, _ = pp.condition(nu_t, counts, cfg, bias, gap=1e-3)
-    print(f"256 truth: {moved} cells moved off the collapse threshold")
+    nu, c_t, moved, cleared = pp.condition(nu_t, counts, cfg, bias, gap=1e-3, clear_empty=True)
+    print(f"256 truth: {moved} cells moved off the collapse threshold, {cleared} near-empty cells cleared")
     for precision in ("fp64", "fp32"):
         ctx = _full_check("256_truth", cfg, bias, nu, c_t, precision, conditioning="fields")[0]
         ctx.close()
@@ -289,7 +290,7 @@ def test_second_cutoff_against_oracle(precision):
     bias.epsp = [1.2] * 16
     nu_t = synth.white_noise(cfg.n, cfg.seed_truth)
     counts = mock.mock_counts(nu_t, cfg, bias, cfg.seed_counts)
-    nu, counts, _, _ = pp.condition(nu_t, counts, cfg, bias)
+    nu, counts, _, _ = pp.condition(nu_t, counts, cfg, bias, clear_empty=True)
     ctx = _full_check("32_cut2", cfg, bias, nu, counts, precision)[0]
     ctx.close()
 
@@ -431,7 +432,8 @@ def test_redshift_space_256():
     bias = synth.default_bias(cfg)
     nu_t = synth.white_noise(cfg.n, cfg.seed_truth)
     counts = mock.mock_counts(nu_t, cfg, bias, cfg.seed_counts)
-    nu, counts, _, _ = pp.condition(nu_t, counts, cfg, bias)
+    nu, counts, _, cleared = pp.condition(nu_t, counts, cfg, bias, clear_empty=True)
+    print(f"256 RSD truth: {cleared} near-empty cells cleared")
     ctx = _full_check("256_rsd", cfg, bias, nu, counts, "fp32", conditioning="fields")[0]
     ctx.close()
 
@@ -501,7 +503,7 @@ def test_batched_16x128_workload():
                              seed_counts=cb.seed_counts + 100 * b)
             nu_t = synth.white_noise(cb.n, c.seed_truth)
             counts = mock.mock_counts(nu_t, c, biases[b], c.seed_counts)
-            nu, counts, _, _ = pp.condition(nu_t, counts, c, biases[b])
+            nu, counts, _, _ = pp.condition(nu_t, counts, c, biases[b], clear_empty=True)
             ref[b] = oracle_ref(f"b16_{b}", c, biases[b], nu, counts)
         else:
             nu = pp.f32(synth.white_noise(cb.n, cb.seed_truth + 100 * b))
@@ -576,8 +578,8 @@ def test_large_single_field_512():
     gradient against the FP64 path's gradient on the same input (the FP64 path matches the
     oracle at <= 256^3 with the same kernel templates); the FP64 gradient against central
     differences along 4 random directions (h = 1e-5).  Counts: a gamma-Poisson draw (beta = 2)
-    from the FP64 path's own nbar at nu (a data-consistent point, no near-empty cell with
-    tracers), nu kept 1e-3 off the collapse threshold."""
+    from the FP64 path's own nbar at nu (a data-consistent point), tracers removed from cells
+    with a CIC mass below 1e-2, nu kept 1e-3 off the collapse threshold."""
     c5 = synth.config(4)
     b5 = synth.default_bias(c5)
     nu, moved = pp.off_collapse(synth.white_noise(c5.n, c5.seed_eval), c5, 1e-3)
@@ -591,6 +593,12 @@ def test_large_single_field_512():
     lnnbar = None
     counts = torch.poisson(lam, generator=gen).clamp_(max=65535).to(torch.int32).reshape(ones.shape).contiguous()
     del lam, ones
+    # as at the smaller meshes, no tracers in cells with a CIC mass below 1e-2 (here the FP64
+    # path's mass: this check compares two precisions of the library, no oracle output involved)
+    rho = c64.bridge_debug_field(nu64, counts, [b5], pkg.FIELD_DELTA).reshape(counts.shape) + 1.0
+    cleared = int(((rho < 1e-2) & (counts > 0)).sum())
+    counts[rho < 1e-2] = 0
+    del rho
     ntr = float(counts.sum())
     d0 = c64.bridge_debug_field(nu64, counts, [b5], pkg.FIELD_DELTA0).cpu().numpy().reshape(-1)
     cells = np.random.default_rng(5).integers(0, c5.n ** 3, 16)
@@ -612,7 +620,7 @@ def test_large_single_field_512():
     e_n = abs(np.exp(lnn).sum() / ntr - 1)
     _, g32, _ = c32.bridge_logpost_grad(nu32, counts, [b5], want_bias_grad=False)
     e_g = rel_l2(g32.double().cpu().numpy(), g64.numpy())
-    print(f"512: moved {moved}; delta0 samples rel FP32 {e0:.2e} FP64 {e0_64:.2e}; mass "
+    print(f"512: moved {moved}, cleared {cleared}; delta0 samples rel FP32 {e0:.2e} FP64 {e0_64:.2e}; mass "
           f"{abs(delta.sum()) / delta.size:.2e}; sum nbar / N_tr - 1 = {e_n:.2e}; FP32 vs FP64 gradient {e_g:.2e}; "
           f"FP64 gradient vs FD (4 directions) {e_fd:.2e}")
     assert e0 <= FP32_FIELD and e0_64 <= FP64_FIELD
