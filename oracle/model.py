@@ -355,11 +355,15 @@ def bias_tables(bias, requires_grad=False):
 
 
 def forward(nu: torch.Tensor, cfg, tables, counts: Optional[torch.Tensor] = None,
-            n_tracers: Optional[float] = None, keep: bool = False):
-    """Forward model; returns dict with ln_nbar, beta_i (and intermediates if keep)."""
+            n_tracers: Optional[float] = None, keep: bool = False, psi_shift: Optional[torch.Tensor] = None):
+    """Forward model; returns dict with ln_nbar, beta_i (and intermediates if keep).
+    psi_shift: an optional displacement (cells) added to Psi before the mass assignment, for
+    measuring how the results depend on the particle positions (conditioning studies)."""
     g = Grid(cfg.n, cfg.box)
     d0 = delta0_from_nu(nu, cfg, g)
     psi = alpt_displacement(d0, cfg, g)
+    if psi_shift is not None:
+        psi = psi + psi_shift
     delta = cic_delta(psi)
     T = tidal_tensor(delta, g)
     lam_phi = eigenvalues_desc(T)
@@ -391,9 +395,9 @@ def log_prior_bias(tables, bias) -> torch.Tensor:
     return lp
 
 
-def log_posterior(nu: torch.Tensor, counts: torch.Tensor, cfg, bias, tables=None, keep=False):
+def log_posterior(nu: torch.Tensor, counts: torch.Tensor, cfg, bias, tables=None, keep=False, psi_shift=None):
     tables = tables if tables is not None else bias_tables(bias)
-    fw = forward(nu, cfg, tables, counts=counts, keep=keep)
+    fw = forward(nu, cfg, tables, counts=counts, keep=keep, psi_shift=psi_shift)
     n = counts.to(DT)
     loglik = nb_logpmf_ln(n, fw["ln_nbar"], fw["beta"]).sum()
     lp = -0.5 * (nu ** 2).sum() + loglik + log_prior_bias(tables, bias)
@@ -403,12 +407,13 @@ def log_posterior(nu: torch.Tensor, counts: torch.Tensor, cfg, bias, tables=None
     return lp
 
 
-def logpost_and_grad(nu_np, counts_np, cfg, bias):
-    """(log posterior, d/d nu, d/d alpha_r, d/d beta_r) by autograd, float64."""
+def logpost_and_grad(nu_np, counts_np, cfg, bias, psi_shift=None):
+    """(log posterior, d/d nu, d/d alpha_r, d/d beta_r) by autograd, float64 (psi_shift: see forward)."""
     nu = torch.tensor(np.asarray(nu_np), dtype=DT, requires_grad=True)
     counts = torch.tensor(np.asarray(counts_np))
     tables = bias_tables(bias, requires_grad=True)
-    lp = log_posterior(nu, counts, cfg, bias, tables)
+    shift = None if psi_shift is None else torch.tensor(np.asarray(psi_shift), dtype=DT)
+    lp = log_posterior(nu, counts, cfg, bias, tables, psi_shift=shift)
     g_nu, g_a, g_b = torch.autograd.grad(lp, (nu, tables["alpha"], tables["beta"]))
     return float(lp.detach()), g_nu.numpy(), g_a.numpy(), g_b.numpy()
 

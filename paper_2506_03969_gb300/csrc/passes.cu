@@ -247,6 +247,7 @@ template <typename T, int N, typename F> __device__ __forceinline__ bool ydispat
 // copied into shared memory (cp.async) while the current one is transformed.
 template <typename T, int N, bool XM>
 __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YPASS_MINB : 1) k_col_fwd(const PassProgram P, const KParams kp) {
+    pdl_prologue();
     using TL = Tile<T, N, XM>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -323,6 +324,7 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YP
 // Inverse (expand) column pass: out[dst] = IDFT(mult * in[src]) for each term.
 template <typename T, int N, bool XM>
 __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YPASS_MINB : 1) k_col_inv(const PassProgram P, const KParams kp) {
+    pdl_prologue();
     using TL = Tile<T, N, XM>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -332,9 +334,6 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YP
     TL::tile_pos(blockIdx.x, kz, c0);
     const size_t base = TL::tile_base(kz, c0);
     const int g = TL::b_g(t);
-    // outputs alternate between two transpose buffers: one barrier per output (see k_x_node)
-    V* sm2 = sm + TL::SM_ELEMS;
-    int produced = 0;
     for (int s = 0; s < P.n_in; ++s) {
         bool used = false;
         for (int m = 0; m < P.n_expand; ++m) used |= (P.expand[m].src == s);
@@ -385,11 +384,11 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YP
                     }
                 }
             }
-            V* smo = (produced++ & 1) ? sm2 : sm;
-            TL::invB(Y, smo, t);
+            __syncthreads();
+            TL::invB(Y, sm, t);
             __syncthreads();
             V* dst = reinterpret_cast<V*>(P.out[tm.dst]) + chain * P.out_cs + base;
-            TL::invA(smo, dst, t);
+            TL::invA(sm, dst, t);
         }
     }
 }
@@ -400,6 +399,7 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YP
 // own, so that the one-term-per-output pass above keeps its register budget.
 template <typename T, int N>
 __global__ void __launch_bounds__(Tile<T, N, false>::NT, 1) k_col_inv_acc(const PassProgram P, const KParams kp) {
+    pdl_prologue();
     using TL = Tile<T, N, false>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -496,6 +496,7 @@ __device__ __forceinline__ cplx_t<T> xmult(const XTerm<T>& x, int mx, int ix, in
 #endif
 template <typename T, int N>
 __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_node(const PassProgram P, const KParams kp) {
+    pdl_prologue();
     using TL = Tile<T, N, true>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -507,9 +508,8 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_n
     const int g = TL::b_g(t);
     const int my = signed_freq(c0 + g, N), mz = kz;
     const int m2yz = my * my + mz * mz;
-    // x factor of the blend, when a term of the program uses it; then the second transpose buffer
+    // x factor of the blend, when a term of the program uses it
     T* skx = reinterpret_cast<T*>(sm + TL::SM_ELEMS + TL::STAGE_ELEMS);
-    V* sm2 = sm + TL::SM_ELEMS + TL::STAGE_ELEMS + (N * sizeof(T) + sizeof(V) - 1) / sizeof(V);
     bool blend = false;
     for (int m = 0; m < P.n_merge; ++m) blend |= sep_blend<T>(P.merge[m].rcode);
     for (int m = 0; m < P.n_expand; ++m) blend |= sep_blend<T>(P.expand[m].rcode);
@@ -591,15 +591,11 @@ __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_n
                 }
             }
         }
-        // outputs alternate between two transpose buffers (output 0 takes the second one, so
-        // the merge loop's last reads of the first need no barrier): a thread reaches the
-        // barrier after output m only once it has finished reading the buffer of output m - 1,
-        // which output m + 1 overwrites, so one barrier per output suffices
-        V* smo = (m & 1) ? sm : sm2;
-        TL::invB(Y, smo, t);
+        __syncthreads();
+        TL::invB(Y, sm, t);
         __syncthreads();
         V* dst = reinterpret_cast<V*>(P.out[tm.dst]) + chain * P.out_cs + base;
-        TL::invA(smo, dst, t);
+        TL::invA(sm, dst, t);
     }
 }
 
@@ -616,6 +612,7 @@ template <typename T, int N> using ZPass = ZCfg<T, N, 256 / (8 * Split<N>::N2)>;
 #endif
 template <typename T, int N>
 __global__ void __launch_bounds__(ZPass<T, N>::NT, (sizeof(T) == 4 && N <= 256) ? BRIDGE_ZFWD_MINB : 0) k_z_fwd(const ZProgram P) {
+    pdl_prologue();
     using ZT = ZPass<T, N>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -638,6 +635,7 @@ template <typename T> struct SubLineIO {
 
 template <typename T, int N, bool SUB>
 __global__ void __launch_bounds__(ZPass<T, N>::NT, BRIDGE_ZINV_MINB) k_z_inv(const ZProgram P) {
+    pdl_prologue();
     using ZT = ZPass<T, N>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -689,7 +687,7 @@ template <typename T, int N> static cudaError_t z_fwd_n(int batch, const ZProgra
     const size_t sm = size_t(ZT::SM_ELEMS) * sizeof(cplx_t<T>);
     cudaError_t e = set_smem(k_z_fwd<T, N>, sm);
     if (e != cudaSuccess) return e;
-    k_z_fwd<T, N><<<dim3(ZT::TILES, p.n_fields, batch), ZT::NT, sm, s>>>(p);
+    { const cudaError_t le_ = launch_k(k_z_fwd<T, N>, dim3(ZT::TILES, p.n_fields, batch), ZT::NT, sm, s, p); if (le_ != cudaSuccess) return le_; }
     return cudaGetLastError();
 }
 template <typename T, int N, bool SUB> static cudaError_t z_inv_nk(int batch, const ZProgram& p, cudaStream_t s) {
@@ -697,7 +695,7 @@ template <typename T, int N, bool SUB> static cudaError_t z_inv_nk(int batch, co
     const size_t sm = size_t(ZT::SM_ELEMS) * sizeof(cplx_t<T>);
     cudaError_t e = set_smem(k_z_inv<T, N, SUB>, sm);
     if (e != cudaSuccess) return e;
-    k_z_inv<T, N, SUB><<<dim3(ZT::TILES, p.n_fields, batch), ZT::NT, sm, s>>>(p);
+    { const cudaError_t le_ = launch_k(k_z_inv<T, N, SUB>, dim3(ZT::TILES, p.n_fields, batch), ZT::NT, sm, s, p); if (le_ != cudaSuccess) return le_; }
     return cudaGetLastError();
 }
 template <typename T, int N> static cudaError_t z_inv_n(int batch, const ZProgram& p, cudaStream_t s) {
@@ -711,7 +709,7 @@ template <typename T, int N> static cudaError_t z_inv_n(int batch, const ZProgra
 template <typename T, int N, bool XM, bool FWD>
 static cudaError_t col_n(int batch, const PassProgram& p, const KParams& kp, cudaStream_t s) {
     using TL = Tile<T, N, XM>;
-    const size_t sm = size_t(TL::SM_ELEMS + (FWD ? TL::STAGE_ELEMS : TL::SM_ELEMS)) * sizeof(cplx_t<T>);
+    const size_t sm = size_t(TL::SM_ELEMS + (FWD ? TL::STAGE_ELEMS : 0)) * sizeof(cplx_t<T>);
     auto kern = FWD ? k_col_fwd<T, N, XM> : (!XM && p.accumulate ? k_col_inv_acc<T, N> : k_col_inv<T, N, XM>);
     cudaError_t e = set_smem(kern, sm);
     if (e != cudaSuccess) return e;
@@ -723,19 +721,18 @@ static cudaError_t col_n(int batch, const PassProgram& p, const KParams& kp, cud
             for (int m = 0; m < p.n_merge; ++m)
                 if (p.merge[m].dst == o) q.merge[k++] = p.merge[m];
         q.n_merge = k;
-        kern<<<dim3(TL::TILES, batch), TL::NT, sm, s>>>(q, kp);
+        { const cudaError_t le_ = launch_k(kern, dim3(TL::TILES, batch), TL::NT, sm, s, q, kp); if (le_ != cudaSuccess) return le_; }
     } else {
-        kern<<<dim3(TL::TILES, batch), TL::NT, sm, s>>>(p, kp);
+        { const cudaError_t le_ = launch_k(kern, dim3(TL::TILES, batch), TL::NT, sm, s, p, kp); if (le_ != cudaSuccess) return le_; }
     }
     return cudaGetLastError();
 }
 template <typename T, int N> static cudaError_t xnode_n(int batch, const PassProgram& p, const KParams& kp, cudaStream_t s) {
     using TL = Tile<T, N, true>;
-    const size_t sm = size_t(2 * TL::SM_ELEMS + TL::STAGE_ELEMS) * sizeof(cplx_t<T>) +
-                      ((N * sizeof(T) + sizeof(cplx_t<T>) - 1) / sizeof(cplx_t<T>)) * sizeof(cplx_t<T>);
+    const size_t sm = size_t(TL::SM_ELEMS + TL::STAGE_ELEMS) * sizeof(cplx_t<T>) + N * sizeof(T);
     cudaError_t e = set_smem(k_x_node<T, N>, sm);
     if (e != cudaSuccess) return e;
-    k_x_node<T, N><<<dim3(TL::TILES, batch), TL::NT, sm, s>>>(p, kp);
+    { const cudaError_t le_ = launch_k(k_x_node<T, N>, dim3(TL::TILES, batch), TL::NT, sm, s, p, kp); if (le_ != cudaSuccess) return le_; }
     return cudaGetLastError();
 }
 

@@ -798,3 +798,18 @@ def test_nuts_leaves_a_gaussian_invariant():
     se = 3.0 / math.sqrt(len(xs))
     assert np.all(np.abs(xs.mean(0)) < 4 * se) and np.all(np.abs(xs.var(0) - 1.0) < 0.12)
     assert max(depths) < 8
+
+
+def test_displacement_shift_hook_moves_particles():
+    """The conditioning hook adds a displacement (cells) before the mass assignment: a uniform
+    shift by one cell along x rolls the density by one cell (CIC permutation invariance), and a
+    zero shift changes nothing."""
+    cfg = small_cfg(n=8, box=80.0, n_regions=4)
+    nu = torch.tensor(synth.white_noise(8, 71))
+    t = model.bias_tables(synth.bias_phi_web())
+    d = model.forward(nu, cfg, t, n_tracers=10.0, keep=True)["delta"]
+    shift = torch.zeros(3, 8, 8, 8, dtype=model.DT)
+    assert torch.equal(model.forward(nu, cfg, t, n_tracers=10.0, keep=True, psi_shift=shift)["delta"], d)
+    shift[0] = 1.0
+    d1 = model.forward(nu, cfg, t, n_tracers=10.0, keep=True, psi_shift=shift)["delta"]
+    assert float((d1 - torch.roll(d, 1, dims=0)).abs().max()) < 1e-12
