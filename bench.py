@@ -512,8 +512,57 @@ def run_extras(pkg, synth, cfg, bias, nu32, counts, args):
         del nu_c, cn_c, gg
     out["alpt_stored_vs_recompute"] = rec
 
-    # batched: 16 chains at 128^3 in one launch per pass
+    # the batched workload's HMC: 16 FP32 chains at 128^3 advanced together against single FP64
+    # chains, at the step size where the FP64 dH is O(1) (data drawn from the model at nu_true)
     cb = synth.config(3)
+    bb = synth.perturbed_biases(synth.default_bias(cb), cb.batch, cb.seed_perturb)
+    c64b = pkg.Context(pkg.config_from(cb, precision=pkg.BRIDGE_FP64, batch=1))
+    nts = [torch.tensor(synth.white_noise(cb.n, cb.seed_truth + 100 * b), dtype=torch.float64, device="cuda")
+           for b in range(cb.batch)]
+    cms = []
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(cb.seed_counts)
+    ones = torch.ones(cb.n, cb.n, cb.n, dtype=torch.int32, device="cuda")
+    for b in range(cb.batch):
+        _, ln = c64b.bridge_forward(nts[b], ones, [bb[b]], want_ln_nbar=True)
+        beta_b = 10.0
+        lam = cb.mean_tracers * torch.exp(ln) * torch._standard_gamma(torch.full_like(ln, beta_b), generator=gen) / beta_b
+        cms.append(torch.poisson(lam, generator=gen).clamp_(max=65535).to(torch.int32).reshape(ones.shape))
+    pms = [torch.tensor(synth.momentum(cb.n, cb.seed_momentum + b), dtype=torch.float64, device="cuda")
+           for b in range(cb.batch)]
+    eps_b = None
+    for eps in (4e-4, 2e-4, 1e-4, 5e-5):
+        h0, h1 = c64b.bridge_leapfrog(nts[0].clone(), pms[0].clone(), cms[0], [bb[0]], 10, eps)
+        if np.isfinite(h1[0] - h0[0]) and abs(h1[0] - h0[0]) <= 1.0:
+            eps_b = eps
+            break
+    if eps_b is not None:
+        c32b = pkg.Context(pkg.config_from(cb))
+        nb = torch.stack(nts).float().contiguous()
+        pb = torch.stack(pms).float().contiguous()
+        cnb = torch.stack(cms).contiguous()
+        c32b.bridge_leapfrog(nb.clone(), pb.clone(), cnb, bb, 10, eps_b)   # graph capture
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h0b, h1b = c32b.bridge_leapfrog(nb, pb, cnb, bb, 10, eps_b)
+        torch.cuda.synchronize()
+        t32 = time.perf_counter() - t0
+        d64s, t64 = [], 0.0
+        for b in range(4):
+            t0 = time.perf_counter()
+            h0, h1 = c64b.bridge_leapfrog(nts[b].clone(), pms[b].clone(), cms[b], [bb[b]], 10, eps_b)
+            torch.cuda.synchronize()
+            t64 += time.perf_counter() - t0
+            d64s.append(h1[0] - h0[0])
+        d32s = [h1b[b] - h0b[b] for b in range(4)]
+        out["hmc_equal_accuracy_16x128"] = {
+            "eps": eps_b, "chains_fp32_batched": cb.batch, "compared": 4, "dH_fp64": d64s, "dH_fp32": d32s,
+            "max_abs_dH_fp32_minus_fp64": float(max(abs(a - b) for a, b in zip(d32s, d64s))),
+            "fp32_batched_trajectories_per_s": cb.batch / t32, "fp64_single_trajectories_per_s": 4 / t64,
+            "speedup": (cb.batch / t32) / (4 / t64)}
+        del c32b, nb, pb, cnb
+    del c64b, nts, cms, pms, ones
+    # batched: 16 chains at 128^3 in one launch per pass
     biases = synth.perturbed_biases(synth.default_bias(cb), cb.batch, cb.seed_perturb)
     ctxb = pkg.Context(pkg.config_from(cb))
     nub = torch.tensor(synth.white_noise(cb.n, cb.seed_eval, cb.batch), dtype=torch.float32, device="cuda")

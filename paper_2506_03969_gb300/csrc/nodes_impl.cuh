@@ -35,7 +35,6 @@ template <> struct NodeShape<NODE_GATHER> { static constexpr int IN = 3, SLAB = 
 
 template <typename T, int N, int KIND>
 __global__ void __launch_bounds__(kNodeThreads) k_node(const NodeArgs A, int batch, long long nspec) {
-    pdl_prologue();
     using C = NodeCfg<T, N>;
     using V = cplx_t<T>;
     using SH = NodeShape<KIND>;
@@ -172,7 +171,7 @@ template <typename T, int N, int KIND> struct NodeLaunch {
         if (a.scratch_bytes > 0 && size_t(g) * SH::SLAB * C::TILE_VOX * sizeof(T) > a.scratch_bytes)
             return cudaErrorInvalidValue;   // not even one slab fits
         if (gu) *gu = g;
-        { const cudaError_t le_ = launch_k(kern, g, kNodeThreads, smem(), s, a, batch, nspec); if (le_ != cudaSuccess) return le_; }
+        kern<<<g, kNodeThreads, smem(), s>>>(a, batch, nspec);
         return cudaGetLastError();
     }
     static size_t scratch(int batch, int sms) { return size_t(grid(batch, sms)) * SH::SLAB * C::TILE_VOX * sizeof(T); }

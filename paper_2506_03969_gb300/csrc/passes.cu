@@ -247,7 +247,6 @@ template <typename T, int N, typename F> __device__ __forceinline__ bool ydispat
 // copied into shared memory (cp.async) while the current one is transformed.
 template <typename T, int N, bool XM>
 __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YPASS_MINB : 1) k_col_fwd(const PassProgram P, const KParams kp) {
-    pdl_prologue();
     using TL = Tile<T, N, XM>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -324,7 +323,6 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YP
 // Inverse (expand) column pass: out[dst] = IDFT(mult * in[src]) for each term.
 template <typename T, int N, bool XM>
 __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YPASS_MINB : 1) k_col_inv(const PassProgram P, const KParams kp) {
-    pdl_prologue();
     using TL = Tile<T, N, XM>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -399,7 +397,6 @@ __global__ void __launch_bounds__(Tile<T, N, XM>::NT, sizeof(T) == 4 ? BRIDGE_YP
 // own, so that the one-term-per-output pass above keeps its register budget.
 template <typename T, int N>
 __global__ void __launch_bounds__(Tile<T, N, false>::NT, 1) k_col_inv_acc(const PassProgram P, const KParams kp) {
-    pdl_prologue();
     using TL = Tile<T, N, false>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -496,7 +493,6 @@ __device__ __forceinline__ cplx_t<T> xmult(const XTerm<T>& x, int mx, int ix, in
 #endif
 template <typename T, int N>
 __global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_node(const PassProgram P, const KParams kp) {
-    pdl_prologue();
     using TL = Tile<T, N, true>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -612,7 +608,6 @@ template <typename T, int N> using ZPass = ZCfg<T, N, 256 / (8 * Split<N>::N2)>;
 #endif
 template <typename T, int N>
 __global__ void __launch_bounds__(ZPass<T, N>::NT, (sizeof(T) == 4 && N <= 256) ? BRIDGE_ZFWD_MINB : 0) k_z_fwd(const ZProgram P) {
-    pdl_prologue();
     using ZT = ZPass<T, N>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -635,7 +630,6 @@ template <typename T> struct SubLineIO {
 
 template <typename T, int N, bool SUB>
 __global__ void __launch_bounds__(ZPass<T, N>::NT, BRIDGE_ZINV_MINB) k_z_inv(const ZProgram P) {
-    pdl_prologue();
     using ZT = ZPass<T, N>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -687,7 +681,7 @@ template <typename T, int N> static cudaError_t z_fwd_n(int batch, const ZProgra
     const size_t sm = size_t(ZT::SM_ELEMS) * sizeof(cplx_t<T>);
     cudaError_t e = set_smem(k_z_fwd<T, N>, sm);
     if (e != cudaSuccess) return e;
-    { const cudaError_t le_ = launch_k(k_z_fwd<T, N>, dim3(ZT::TILES, p.n_fields, batch), ZT::NT, sm, s, p); if (le_ != cudaSuccess) return le_; }
+    k_z_fwd<T, N><<<dim3(ZT::TILES, p.n_fields, batch), ZT::NT, sm, s>>>(p);
     return cudaGetLastError();
 }
 template <typename T, int N, bool SUB> static cudaError_t z_inv_nk(int batch, const ZProgram& p, cudaStream_t s) {
@@ -695,7 +689,7 @@ template <typename T, int N, bool SUB> static cudaError_t z_inv_nk(int batch, co
     const size_t sm = size_t(ZT::SM_ELEMS) * sizeof(cplx_t<T>);
     cudaError_t e = set_smem(k_z_inv<T, N, SUB>, sm);
     if (e != cudaSuccess) return e;
-    { const cudaError_t le_ = launch_k(k_z_inv<T, N, SUB>, dim3(ZT::TILES, p.n_fields, batch), ZT::NT, sm, s, p); if (le_ != cudaSuccess) return le_; }
+    k_z_inv<T, N, SUB><<<dim3(ZT::TILES, p.n_fields, batch), ZT::NT, sm, s>>>(p);
     return cudaGetLastError();
 }
 template <typename T, int N> static cudaError_t z_inv_n(int batch, const ZProgram& p, cudaStream_t s) {
@@ -721,9 +715,9 @@ static cudaError_t col_n(int batch, const PassProgram& p, const KParams& kp, cud
             for (int m = 0; m < p.n_merge; ++m)
                 if (p.merge[m].dst == o) q.merge[k++] = p.merge[m];
         q.n_merge = k;
-        { const cudaError_t le_ = launch_k(kern, dim3(TL::TILES, batch), TL::NT, sm, s, q, kp); if (le_ != cudaSuccess) return le_; }
+        kern<<<dim3(TL::TILES, batch), TL::NT, sm, s>>>(q, kp);
     } else {
-        { const cudaError_t le_ = launch_k(kern, dim3(TL::TILES, batch), TL::NT, sm, s, p, kp); if (le_ != cudaSuccess) return le_; }
+        kern<<<dim3(TL::TILES, batch), TL::NT, sm, s>>>(p, kp);
     }
     return cudaGetLastError();
 }
@@ -732,7 +726,7 @@ template <typename T, int N> static cudaError_t xnode_n(int batch, const PassPro
     const size_t sm = size_t(TL::SM_ELEMS + TL::STAGE_ELEMS) * sizeof(cplx_t<T>) + N * sizeof(T);
     cudaError_t e = set_smem(k_x_node<T, N>, sm);
     if (e != cudaSuccess) return e;
-    { const cudaError_t le_ = launch_k(k_x_node<T, N>, dim3(TL::TILES, batch), TL::NT, sm, s, p, kp); if (le_ != cudaSuccess) return le_; }
+    k_x_node<T, N><<<dim3(TL::TILES, batch), TL::NT, sm, s>>>(p, kp);
     return cudaGetLastError();
 }
 

@@ -51,7 +51,6 @@ __device__ __forceinline__ void finish_partials(const double (&acc)[K], double* 
 __global__ void __launch_bounds__(kPwThreads) k_counts_prep(long long nvox, const int32_t* __restrict__ counts,
                                                            uint16_t* __restrict__ c16, double* partial, int* err,
                                                            RedArgs ra) {
-    pdl_prologue();
     const size_t off = (size_t)blockIdx.y * nvox;
     double acc[1] = {0.0};
     long long s = 0;
@@ -76,7 +75,6 @@ __global__ void __launch_bounds__(kPwThreads) k_counts_prep(long long nvox, cons
 
 // Constant fill (the CIC mass is zeroed before each scatter).
 template <typename T> __global__ void k_fill(long long count, T* p, T v) {
-    pdl_prologue();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
         p[i] = v;
 }
@@ -154,7 +152,6 @@ __device__ __forceinline__ void cic_flush4(double* g, const CicWin<double>& W, i
 #endif
 template <typename T, int BZ>
 __global__ void __launch_bounds__(kPwThreads) k_cic_scatter(int N, long long nvox, Fields16 psi3, T* rho) {
-    pdl_prologue();
     using CB = CicBlock<T>;
     constexpr int BX = CB::BX, BY = CB::BY, H = CB::H;
     constexpr int WX = BX + 2 * H, WY = BY + 2 * H, WZ = BZ + 2 * H, CELLS = WX * WY * WZ;
@@ -238,7 +235,6 @@ template <typename T, int NR>
 __global__ void __launch_bounds__(kPwThreads, BRIDGE_PASSA_MINB) k_pass_a(long long nvox, Fields16 th, const T* rho, T* lnf_out,
                                                       T* beta_out, const BiasT<T>* bias, WebParams wp, double* partial,
                                                       RedArgs ra) {
-    pdl_prologue();
     __shared__ BiasT<T> B;
     const int chain = blockIdx.y;
     if (threadIdx.x == 0) B = bias[chain];
@@ -276,7 +272,6 @@ template <typename T>
 __global__ void __launch_bounds__(kPwThreads, BRIDGE_PASSB_MINB) k_pass_b(long long nvox, const T* lnf, const T* beta_i,
                                                       const uint16_t* c16, const T* nu, const ChainScalars* sc,
                                                       double* partial, RedArgs ra) {
-    pdl_prologue();
     using V4 = typename Vec4<T>::type;
     const int chain = blockIdx.y;
     const size_t off = (size_t)chain * nvox;
@@ -319,7 +314,6 @@ template <typename T, int NR, bool BIASG>
 __global__ void __launch_bounds__(kPwThreads, (webadj_minb<T, BIASG>())) k_web_adj(long long nvox, Fields16 th, const T* rho,
                                                           const uint16_t* c16, const BiasT<T>* bias, WebParams wp,
                                                           const ChainScalars* sc, Fields16 out, double* partial) {
-    pdl_prologue();
     __shared__ BiasT<T> B;
     const int chain = blockIdx.y;
     if (threadIdx.x == 0) B = bias[chain];
@@ -369,7 +363,6 @@ __global__ void __launch_bounds__(kPwThreads, (webadj_minb<T, BIASG>())) k_web_a
 
 
 template <typename T> __global__ void k_shift(long long count, const T* in, T* out, T c) {
-    pdl_prologue();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
         out[i] = in[i] + c;
 }
@@ -378,7 +371,6 @@ template <typename T> __global__ void k_shift(long long count, const T* in, T* o
 template <typename T>
 __global__ void __launch_bounds__(kPwThreads) k_kick_drift(long long nvox, T* p, T* nu, const T* g, T ck, T cd,
                                                           double* partial) {
-    pdl_prologue();
     const size_t off = (size_t)blockIdx.y * nvox;
     T a = 0;
     double acc[1] = {0.0};
@@ -398,7 +390,6 @@ __global__ void __launch_bounds__(kPwThreads) k_kick_drift(long long nvox, T* p,
 // sum a_i b_i per chain: FP64 products, per-thread partials in FP64.
 template <typename T>
 __global__ void __launch_bounds__(kPwThreads) k_dot(long long nvox, const T* a, const T* b, double* partial, RedArgs ra) {
-    pdl_prologue();
     const size_t off = (size_t)blockIdx.y * nvox;
     double acc[1] = {0.0};
     PW_LOOP(i, nvox) acc[0] += double(a[off + i]) * double(b[off + i]);
@@ -414,7 +405,6 @@ __global__ void __launch_bounds__(kPwThreads) k_dot(long long nvox, const T* a, 
 template <typename T>
 __global__ void k_bias_kick_drift(int nr, uint32_t free_mask, double* theta, double* ptheta, const ChainScalars* sc,
                                   BiasD* bd, BiasT<T>* bt, double ck, double cd) {
-    pdl_prologue();
     const int c = blockIdx.x, q = threadIdx.x;
     if (q >= 2 * nr || !((free_mask >> q) & 1u)) return;
     const int k = __popc(free_mask & ((1u << q) - 1u));
@@ -433,7 +423,6 @@ __global__ void k_bias_kick_drift(int nr, uint32_t free_mask, double* theta, dou
 
 // Tracer density contrast n* N^3 / N_tr - 1 of each chain (Sect. 2.2 initialisation).
 template <typename T> __global__ void k_delta_tr(long long nvox, const uint16_t* c16, const ChainScalars* sc, T* out) {
-    pdl_prologue();
     const size_t off = (size_t)blockIdx.y * nvox;
     const T scale = T(double(nvox) / sc[blockIdx.y].ntr);
     PW_LOOP(i, nvox) out[off + i] = T(c16[off + i]) * scale - T(1);
@@ -441,7 +430,6 @@ template <typename T> __global__ void k_delta_tr(long long nvox, const uint16_t*
 
 // g[chain] *= scale[chain] (the cotangent of a vector-Jacobian product).
 template <typename T> __global__ void k_scale_chains(long long nvox, T* g, const double* scale) {
-    pdl_prologue();
     const size_t off = (size_t)blockIdx.y * nvox;
     const T c = T(scale[blockIdx.y]);
     PW_LOOP(i, nvox) g[off + i] *= c;
@@ -449,7 +437,6 @@ template <typename T> __global__ void k_scale_chains(long long nvox, T* g, const
 
 template <typename T>
 __global__ void k_lnnbar(long long nvox, const T* lnf, const ChainScalars* sc, T* out) {
-    pdl_prologue();
     const size_t off = (size_t)blockIdx.y * nvox;
     const T lnC = T(sc[blockIdx.y].lnC);
     PW_LOOP(i, nvox) out[off + i] = lnf[off + i] + lnC;
@@ -457,7 +444,6 @@ __global__ void k_lnnbar(long long nvox, const T* lnf, const ChainScalars* sc, T
 
 template <typename T>
 __global__ void k_eigs(long long nvox, Fields16 t6, Fields16 out3) {
-    pdl_prologue();
     const size_t off = (size_t)blockIdx.y * nvox;
     PW_LOOP(i, nvox) {
         T a6[6];
@@ -551,7 +537,6 @@ __device__ void reduce_body(int what, int chain, int nblk, int K, const double* 
 
 __global__ void __launch_bounds__(1024) k_reduce(int what, int nblk, int K, const double* partial, ChainScalars* sc,
                                                  const BiasD* bias, int n_regions) {
-    pdl_prologue();
     reduce_body(what, blockIdx.x, nblk, K, partial, sc, bias, n_regions);
 }
 
@@ -563,12 +548,12 @@ static inline long long nvox_of(int n) { return (long long)n * n * n; }
 template <typename T>
 cudaError_t launch_counts_prep(int n, int batch, const int32_t* counts, uint16_t* c16, double* partial, int* err,
                                const RedArgs& ra, cudaStream_t s) {
-    { const cudaError_t le_ = launch_k(k_counts_prep, dim3(pw_blocks(n), batch), kPwThreads, 0, s, nvox_of(n), counts, c16, partial, err, ra); if (le_ != cudaSuccess) return le_; }
+    k_counts_prep<<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), counts, c16, partial, err, ra);
     return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_fill(long long count, T* p, T v, cudaStream_t s) {
     long long b = (count + 1023) / 1024;
-    { const cudaError_t le_ = launch_k(k_fill<T>, (unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b)), 256, 0, s, count, p, v); if (le_ != cudaSuccess) return le_; }
+    k_fill<T><<<(unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b)), 256, 0, s>>>(count, p, v);
     return cudaGetLastError();
 }
 template <typename T>
@@ -581,7 +566,7 @@ cudaError_t launch_cic_scatter(int n, int batch, const Fields16& psi3, T* delta,
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         if (e != cudaSuccess) return e;
         const unsigned blocks = unsigned((n / CB::BX) * (n / CB::BY) * (n / bz));
-        { const cudaError_t le_ = launch_k(kern, dim3(blocks, batch), kPwThreads, sm, s, n, nvox_of(n), psi3, delta); if (le_ != cudaSuccess) return le_; }
+        kern<<<dim3(blocks, batch), kPwThreads, sm, s>>>(n, nvox_of(n), psi3, delta);
         return cudaGetLastError();
     };
     return n >= BRIDGE_CIC_BZ ? run(k_cic_scatter<T, BRIDGE_CIC_BZ>, BRIDGE_CIC_BZ) : run(k_cic_scatter<T, 16>, 16);
@@ -591,15 +576,15 @@ cudaError_t launch_pass_a(int n, int batch, const Fields16& th, const T* delta, 
                           const BiasT<T>* bias, const WebParams& wp, double* partial, const RedArgs& ra,
                           cudaStream_t s) {
     if (wp.n_regions == 16)
-        { const cudaError_t le_ = launch_k(k_pass_a<T, 16>, dim3(pw_blocks(n), batch), kPwThreads, 0, s, nvox_of(n), th, delta, lnf, beta_i, bias, wp, partial, ra); if (le_ != cudaSuccess) return le_; }
+        k_pass_a<T, 16><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), th, delta, lnf, beta_i, bias, wp, partial, ra);
     else
-        { const cudaError_t le_ = launch_k(k_pass_a<T, 4>, dim3(pw_blocks(n), batch), kPwThreads, 0, s, nvox_of(n), th, delta, lnf, beta_i, bias, wp, partial, ra); if (le_ != cudaSuccess) return le_; }
+        k_pass_a<T, 4><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), th, delta, lnf, beta_i, bias, wp, partial, ra);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_pass_b(int n, int batch, const T* lnf, const T* beta_i, const uint16_t* c16, const T* nu,
                           const ChainScalars* sc, double* partial, const RedArgs& ra, cudaStream_t s) {
-    { const cudaError_t le_ = launch_k(k_pass_b<T>, dim3(pw_blocks(n), batch), kPwThreads, 0, s, nvox_of(n), lnf, beta_i, c16, nu, sc, partial, ra); if (le_ != cudaSuccess) return le_; }
+    k_pass_b<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), lnf, beta_i, c16, nu, sc, partial, ra);
     return cudaGetLastError();
 }
 template <typename T>
@@ -610,60 +595,60 @@ cudaError_t launch_web_adjoint(int n, int batch, const Fields16& th, const T* de
     // otherwise blocks per chain as requested (grid-stride loop), else the wide grid
     const dim3 g(bias_grad ? pw_blocks(n) : (blocks > 0 ? blocks : pw_blocks_wide(n)), batch);
     if (wp.n_regions == 16) {
-        if (bias_grad) { const cudaError_t le_ = launch_k(k_web_adj<T, 16, true>, g, kPwThreads, 0, s, nvox_of(n), th, delta, c16, bias, wp, sc, out, partial); if (le_ != cudaSuccess) return le_; }
-        else { const cudaError_t le_ = launch_k(k_web_adj<T, 16, false>, g, kPwThreads, 0, s, nvox_of(n), th, delta, c16, bias, wp, sc, out, partial); if (le_ != cudaSuccess) return le_; }
+        if (bias_grad) k_web_adj<T, 16, true><<<g, kPwThreads, 0, s>>>(nvox_of(n), th, delta, c16, bias, wp, sc, out, partial);
+        else k_web_adj<T, 16, false><<<g, kPwThreads, 0, s>>>(nvox_of(n), th, delta, c16, bias, wp, sc, out, partial);
     } else {
-        if (bias_grad) { const cudaError_t le_ = launch_k(k_web_adj<T, 4, true>, g, kPwThreads, 0, s, nvox_of(n), th, delta, c16, bias, wp, sc, out, partial); if (le_ != cudaSuccess) return le_; }
-        else { const cudaError_t le_ = launch_k(k_web_adj<T, 4, false>, g, kPwThreads, 0, s, nvox_of(n), th, delta, c16, bias, wp, sc, out, partial); if (le_ != cudaSuccess) return le_; }
+        if (bias_grad) k_web_adj<T, 4, true><<<g, kPwThreads, 0, s>>>(nvox_of(n), th, delta, c16, bias, wp, sc, out, partial);
+        else k_web_adj<T, 4, false><<<g, kPwThreads, 0, s>>>(nvox_of(n), th, delta, c16, bias, wp, sc, out, partial);
     }
     return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_shift(long long count, const T* in, T* out, T c, cudaStream_t s) {
     long long b = (count + 1023) / 1024;
-    { const cudaError_t le_ = launch_k(k_shift<T>, (unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b)), 256, 0, s, count, in, out, c); if (le_ != cudaSuccess) return le_; }
+    k_shift<T><<<(unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b)), 256, 0, s>>>(count, in, out, c);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_kick_drift(int n, int batch, T* p, T* nu, const T* g, double ck, double cd, double* partial,
                               cudaStream_t s) {
-    { const cudaError_t le_ = launch_k(k_kick_drift<T>, dim3(pw_blocks(n), batch), kPwThreads, 0, s, nvox_of(n), p, nu, g, T(ck), T(cd), partial); if (le_ != cudaSuccess) return le_; }
+    k_kick_drift<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), p, nu, g, T(ck), T(cd), partial);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_dot(int n, int batch, const T* a, const T* b, double* partial, const RedArgs& ra, cudaStream_t s) {
-    { const cudaError_t le_ = launch_k(k_dot<T>, dim3(pw_blocks(n), batch), kPwThreads, 0, s, nvox_of(n), a, b, partial, ra); if (le_ != cudaSuccess) return le_; }
+    k_dot<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), a, b, partial, ra);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_bias_kick_drift(int batch, int nr, uint32_t free_mask, double* theta, double* ptheta,
                                    const ChainScalars* sc, BiasD* bd, BiasT<T>* bt, double ck, double cd, cudaStream_t s) {
-    { const cudaError_t le_ = launch_k(k_bias_kick_drift<T>, batch, 32, 0, s, nr, free_mask, theta, ptheta, sc, bd, bt, ck, cd); if (le_ != cudaSuccess) return le_; }
+    k_bias_kick_drift<T><<<batch, 32, 0, s>>>(nr, free_mask, theta, ptheta, sc, bd, bt, ck, cd);
     return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_delta_tr(int n, int batch, const uint16_t* c16, const ChainScalars* sc, T* out,
                                                   cudaStream_t s) {
-    { const cudaError_t le_ = launch_k(k_delta_tr<T>, dim3(pw_blocks_wide(n), batch), kPwThreads, 0, s, nvox_of(n), c16, sc, out); if (le_ != cudaSuccess) return le_; }
+    k_delta_tr<T><<<dim3(pw_blocks_wide(n), batch), kPwThreads, 0, s>>>(nvox_of(n), c16, sc, out);
     return cudaGetLastError();
 }
 template <typename T> cudaError_t launch_scale_chains(int n, int batch, T* g, const double* scale, cudaStream_t s) {
-    { const cudaError_t le_ = launch_k(k_scale_chains<T>, dim3(pw_blocks_wide(n), batch), kPwThreads, 0, s, nvox_of(n), g, scale); if (le_ != cudaSuccess) return le_; }
+    k_scale_chains<T><<<dim3(pw_blocks_wide(n), batch), kPwThreads, 0, s>>>(nvox_of(n), g, scale);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_lnnbar(long long nvox, int batch, const T* lnf, const ChainScalars* sc, T* out, cudaStream_t s) {
-    { const cudaError_t le_ = launch_k(k_lnnbar<T>, dim3(256, batch), kPwThreads, 0, s, nvox, lnf, sc, out); if (le_ != cudaSuccess) return le_; }
+    k_lnnbar<T><<<dim3(256, batch), kPwThreads, 0, s>>>(nvox, lnf, sc, out);
     return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_eigs(int n, int batch, const Fields16& t6, const Fields16& out3, cudaStream_t s) {
-    { const cudaError_t le_ = launch_k(k_eigs<T>, dim3(pw_blocks(n), batch), kPwThreads, 0, s, nvox_of(n), t6, out3); if (le_ != cudaSuccess) return le_; }
+    k_eigs<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(nvox_of(n), t6, out3);
     return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(int what, int nblk, int batch, const double* partial, ChainScalars* sc, const BiasD* bias,
                           int n_regions, cudaStream_t s) {
     int K = what == RED_LIK ? 3 : (what == RED_BIASGRAD ? 2 * n_regions : 1);
-    { const cudaError_t le_ = launch_k(k_reduce, batch, 32 * K, 0, s, what, nblk, K, partial, sc, bias, n_regions); if (le_ != cudaSuccess) return le_; }
+    k_reduce<<<batch, 32 * K, 0, s>>>(what, nblk, K, partial, sc, bias, n_regions);
     return cudaGetLastError();
 }
 

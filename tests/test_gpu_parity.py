@@ -194,12 +194,12 @@ def _full_check(name, cfg, bias, nu, counts, precision, conditioning=True, psi=F
     lp, g, gb = ctx.bridge_logpost_grad(nu_d, c_d, [bias])
     e_lp = abs(lp[0] - lp_o) / abs(lp_o)
     e_g = rel_l2(g.double().cpu().numpy().reshape(g_o.shape), g_o)
-    e_b = float(np.max(np.abs(gb[0] - gb_o)) / np.max(np.abs(gb_o)))
+    e_b = rel_l2(gb[0], gb_o)
     btol = bias_tol(precision, f)
     sp = f.get("cond_psi")
     print(f"{name} {precision}: logpost rel {e_lp:.2e}  grad rel L2 {e_g:.2e} (tol {gtol:.1e}, S {cond:.1e}"
           + (f", S_psi {sp:.1e}" if sp is not None else "") + f")  "
-          f"free bias grad rel {e_b:.2e} (tol {btol:.1e}, {gb.shape[1]} parameters)")
+          f"free bias grad rel L2 {e_b:.2e} (tol {btol:.1e}, {gb.shape[1]} parameters)")
     assert e_lp <= ltol, (lp[0], lp_o)
     assert e_g <= gtol
     assert e_b <= btol
@@ -558,9 +558,10 @@ def test_batched_16x128_workload():
         if b in ref:
             f_o, lp_o, g_o, gb_o, cond = ref[b]
             e_o = rel_l2(g[b].double().cpu().numpy(), g_o)
-            e_b = float(np.max(np.abs(gb[b] - gb_o)) / np.max(np.abs(gb_o)))
-            print(f"chain {b} vs oracle: lp {abs(lp[b] - lp_o) / abs(lp_o):.2e} grad {e_o:.2e} (S {cond:.1e}) "
-                  f"bias {e_b:.2e} (tol {bias_tol('fp32', f_o):.1e})")
+            e_b = rel_l2(gb[b], gb_o)
+            print(f"chain {b} vs oracle: lp {abs(lp[b] - lp_o) / abs(lp_o):.2e} grad {e_o:.2e} (S {cond:.1e}, "
+                  f"S_psi {f_o['cond_psi']:.1e}) bias {e_b:.2e} (tol {bias_tol('fp32', f_o):.1e}, S {f_o['cond_bias']:.1e}, "
+                  f"S_psi {f_o['cond_psi_bias']:.1e})")
             assert abs(lp[b] - lp_o) <= FP32_LP * abs(lp_o) and e_o <= grad_tol("fp32", f_o)
             assert e_b <= bias_tol("fp32", f_o)
     print(f"16 x 128^3: worst single-vs-batched gradient rel L2 {worst:.2e}")
