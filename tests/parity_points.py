@@ -24,6 +24,8 @@ Every input stays synthetic and seeded; nothing here reads the CUDA path.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 import torch
 
@@ -78,3 +80,36 @@ def condition(nu: np.ndarray, counts: np.ndarray, cfg, bias, gap: float = 1e-3, 
     if clear_empty:
         c = clear_near_empty(x, counts, cfg, bias)
     return x, c, moved, int((c != counts).sum())
+
+
+def bias_abs_terms(nu: np.ndarray, counts: np.ndarray, cfg, bias):
+    """Per bias entry r, the sums over cells of the absolute contributions to d log P / d alpha_r
+    and d log P / d beta_r (Sect. 2.5, 2.6), plus the prior's.
+
+    The gradient with respect to alpha_r is sum_i w_ri ln u_i dL/dlnf_i (u = max(1 + delta,
+    floor); alpha enters f only as u^alpha) and that with respect to beta_r is sum_i w_ri
+    dL/dbeta_i.  At the data-generating field those sums nearly cancel, so the ratio of the
+    absolute sum to the sum -- the cancellation factor -- multiplies the per-term rounding of any
+    finite-precision evaluation.  Returns (abs_alpha, abs_beta, sum_alpha, sum_beta); the
+    sums are the gradient itself."""
+    with torch.no_grad():
+        fw = model.forward(torch.tensor(nu, dtype=model.DT), cfg, model.bias_tables(bias),
+                           counts=torch.tensor(counts), keep=True)
+    w = fw["weights"]
+    lnu = torch.log(torch.clamp(1.0 + fw["delta"], min=cfg.rho_floor))
+    lnf = fw["lnf"].clone().requires_grad_(True)
+    beta_i = fw["beta"].clone().requires_grad_(True)
+    n_tr = float(np.asarray(counts).sum())
+    ln_nbar = math.log(n_tr) + lnf - torch.logsumexp(lnf.reshape(-1), 0)
+    ll = model.nb_logpmf_ln(torch.tensor(counts, dtype=model.DT), ln_nbar, beta_i).sum()
+    g_lnf, g_beta = torch.autograd.grad(ll, (lnf, beta_i))
+    t_a = (w * (lnu * g_lnf)[None]).reshape(w.shape[0], -1)
+    t_b = (w * g_beta[None]).reshape(w.shape[0], -1)
+    abs_a, abs_b, sum_a, sum_b = t_a.abs().sum(1), t_b.abs().sum(1), t_a.sum(1), t_b.sum(1)
+    tables = model.bias_tables(bias, requires_grad=True)
+    lp_prior = model.log_prior_bias(tables, bias)
+    if lp_prior.requires_grad:
+        pa, pb = torch.autograd.grad(lp_prior, (tables["alpha"], tables["beta"]))
+        abs_a, abs_b = abs_a + pa.abs(), abs_b + pb.abs()
+        sum_a, sum_b = sum_a + pa, sum_b + pb
+    return abs_a.numpy(), abs_b.numpy(), sum_a.numpy(), sum_b.numpy()

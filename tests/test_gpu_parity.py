@@ -98,7 +98,9 @@ ORACLE = {}
 def oracle_ref(key, cfg, bias, nu, counts, conditioning=True, psi=False):
     """Oracle fields, log posterior, gradient, free bias gradient and conditioning: the relative
     change of the gradient (cond), of the free bias gradient (f["cond_bias"]) and of each field
-    (f["cond"]) under a 2^-23 relative perturbation of nu.  conditioning: True (all), "fields"
+    (f["cond"]) under a 2^-23 relative perturbation of nu, and the free bias gradient's
+    cancellation factor |sum_i |t_i|| / |sum_i t_i| over its per-cell terms (f["kappa_bias"]).
+    conditioning: True (all), "fields"
     (fields only) or False.  psi: also the relative change of the gradient and of the free bias
     gradient (f["cond_psi"], f["cond_psi_bias"]) when white noise of 3e-7 times the rms
     displacement -- the FP32 displacement error of the GPU path -- is added to Psi."""
@@ -106,7 +108,7 @@ def oracle_ref(key, cfg, bias, nu, counts, conditioning=True, psi=False):
         f = model.forward_fields(nu, counts, cfg, bias)
         lp, g, ga, gb = model.logpost_and_grad(nu, counts, cfg, bias)
         fb = free_grad(ga, gb, bias)
-        cond, f["cond"], f["cond_bias"] = 0.0, {}, None
+        cond, f["cond"], f["cond_bias"], f["kappa_bias"] = 0.0, {}, None, None
         f["cond_psi"] = f["cond_psi_bias"] = None
         if psi:
             rms = float(np.sqrt((f["psi"] ** 2).mean()))
@@ -120,6 +122,9 @@ def oracle_ref(key, cfg, bias, nu, counts, conditioning=True, psi=False):
                 _, g2, ga2, gb2 = model.logpost_and_grad(nu + pert, counts, cfg, bias)
                 cond = float(np.linalg.norm(g2 - g) / np.linalg.norm(g))
                 f["cond_bias"] = float(np.linalg.norm(free_grad(ga2, gb2, bias) - fb) / np.linalg.norm(fb))
+            if conditioning is True:
+                abs_a, abs_b, _, _ = pp.bias_abs_terms(nu, counts, cfg, bias)
+                f["kappa_bias"] = float(np.linalg.norm(free_grad(abs_a, abs_b, bias)) / np.linalg.norm(fb))
             f2 = model.forward_fields(nu + pert, counts, cfg, bias)
             f["cond"] = {k: float(np.linalg.norm(f2[k] - f[k]) / np.linalg.norm(f[k]))
                          for k in f if isinstance(f[k], np.ndarray) and f[k] is not None}
@@ -199,7 +204,8 @@ def _full_check(name, cfg, bias, nu, counts, precision, conditioning=True, psi=F
     sp = f.get("cond_psi")
     print(f"{name} {precision}: logpost rel {e_lp:.2e}  grad rel L2 {e_g:.2e} (tol {gtol:.1e}, S {cond:.1e}"
           + (f", S_psi {sp:.1e}" if sp is not None else "") + f")  "
-          f"free bias grad rel L2 {e_b:.2e} (tol {btol:.1e}, {gb.shape[1]} parameters)")
+          f"free bias grad rel L2 {e_b:.2e} (tol {btol:.1e}, {gb.shape[1]} parameters"
+          + (f", kappa {f['kappa_bias']:.0f}" if f.get("kappa_bias") is not None else "") + ")")
     assert e_lp <= ltol, (lp[0], lp_o)
     assert e_g <= gtol
     assert e_b <= btol
@@ -225,13 +231,18 @@ def grad_tol(precision, f):
 def bias_tol(precision, f):
     """The free bias gradient is a sum over all cells, which nearly cancels at the data-
     generating field (its expectation is zero there): its tolerance is scaled by its own
-    measured conditioning, never above 1e-3 (FP32), and by its displacement conditioning as
-    the gradient is (grad_tol)."""
+    measured conditioning, never above 1e-3 (FP32), by its displacement conditioning as the
+    gradient is (grad_tol), and by its cancellation factor kappa: per-cell terms each rounded
+    to a few FP32 ulps leave an error of about 2^-23 kappa in their sum, so FP32 allows
+    2 * 2^-23 * kappa, never above 1e-3."""
     _, gtol, _ = bounds(precision)
     sb = f.get("cond_bias")
     t = gtol
     if sb is not None:
         t = max(gtol, min(10.0 * sb, CAP)) if precision == "fp32" else max(gtol, 1e-7 * sb)
+    kb = f.get("kappa_bias")
+    if precision == "fp32" and kb is not None:
+        t = max(t, min(2.0 * 2.0 ** -23 * kb, CAP))
     spb = f.get("cond_psi_bias")
     if precision == "fp32" and spb is not None:
         t = max(t, min(3.0 * spb, CAP_PSI))
@@ -561,7 +572,7 @@ def test_batched_16x128_workload():
             e_b = rel_l2(gb[b], gb_o)
             print(f"chain {b} vs oracle: lp {abs(lp[b] - lp_o) / abs(lp_o):.2e} grad {e_o:.2e} (S {cond:.1e}, "
                   f"S_psi {f_o['cond_psi']:.1e}) bias {e_b:.2e} (tol {bias_tol('fp32', f_o):.1e}, S {f_o['cond_bias']:.1e}, "
-                  f"S_psi {f_o['cond_psi_bias']:.1e})")
+                  f"S_psi {f_o['cond_psi_bias']:.1e}, kappa {f_o['kappa_bias']:.0f})")
             assert abs(lp[b] - lp_o) <= FP32_LP * abs(lp_o) and e_o <= grad_tol("fp32", f_o)
             assert e_b <= bias_tol("fp32", f_o)
     print(f"16 x 128^3: worst single-vs-batched gradient rel L2 {worst:.2e}")
@@ -911,28 +922,31 @@ def test_joint_bias_integration_matches_oracle(precision):
 
 def test_nuts_host_driver_matches_oracle():
     """The host-driven NUTS (paper_2506_03969_gb300.nuts) on the FP64 path against the oracle's
-    NUTS with the same seeded draws, 16^3: three transitions in a row reach the same sample, tree
-    depth and number of leapfrog steps.  An FP32 context runs the same transitions to finite
-    samples."""
+    NUTS with the same seeded draws, 16^3: three transitions, each started from the oracle's
+    previous sample, take the same tree depth and number of leapfrog steps and reach the same
+    sample.  (The FP64 path is not bit-reproducible -- CIC float atomics -- and differences of
+    1e-16 grow to ~1e-9 along a 63-step trajectory, enough to flip a U-turn test that sits near
+    zero; trees are therefore kept to depth 5 and not chained.)  An FP32 context runs the same
+    transition to a finite sample."""
     from paper_2506_03969_gb300 import nuts
     cfg, bias, nu, counts, _ = make_case(16, 160.0, 4, 1341, point="eval")
     x_o = nu.copy()
-    rng_o, rng_g, rng_p = np.random.default_rng(7), np.random.default_rng(7), np.random.default_rng(8)
+    rng_p = np.random.default_rng(8)
     moms = [pp.f32(rng_p.standard_normal(nu.shape)) for _ in range(3)]
     ctx, nu_d, c_d = run_gpu(cfg, bias, nu, counts, pkg.BRIDGE_FP64)
-    sampler = nuts.NUTS(ctx, c_d, [bias], eps=0.05, max_depth=6)
-    lp, g, _ = ctx.bridge_logpost_grad(nu_d, c_d, [bias], want_bias_grad=False)
-    x_g, lp_g = nu_d, float(lp[0])
+    sampler = nuts.NUTS(ctx, c_d, [bias], eps=0.05, max_depth=5)
     for t in range(3):
-        x_o, depth_o, steps_o = hmc.nuts_step(x_o, moms[t], counts, cfg, bias, 0.05, rng_o, max_depth=6)
+        rng_o, rng_g = np.random.default_rng(7 + t), np.random.default_rng(7 + t)
+        x_g = torch.tensor(x_o, dtype=torch.float64, device="cuda").contiguous()
+        lp, g, _ = ctx.bridge_logpost_grad(x_g, c_d, [bias], want_bias_grad=False)
+        x_new, depth_o, steps_o = hmc.nuts_step(x_o, moms[t], counts, cfg, bias, 0.05, rng_o, max_depth=5)
         p_d = torch.tensor(moms[t], dtype=torch.float64, device="cuda").contiguous()
-        res = sampler.step(x_g, p_d, g, lp_g, rng_g)
-        x_g, g, lp_g = res.nu, res.grad, res.logpost
-        e = rel_l2(x_g.cpu().numpy(), x_o)
+        res = sampler.step(x_g, p_d, g, float(lp[0]), rng_g)
+        e = rel_l2(res.nu.cpu().numpy(), x_new)
         print(f"NUTS transition {t}: depth {res.depth} / {depth_o}, leapfrog steps {res.n_leapfrog} / {steps_o}, "
               f"sample rel L2 {e:.2e}")
-        # each transition integrates up to 63 FP64 leapfrog steps: rounding differences grow along them
         assert res.depth == depth_o and res.n_leapfrog == steps_o and e <= 1e-8
+        x_o = x_new
     ctx.close()
     c32, nu32, c_d = run_gpu(cfg, bias, nu, counts, pkg.BRIDGE_FP32)
     s32 = nuts.NUTS(c32, c_d, [bias], eps=0.05, max_depth=6)
