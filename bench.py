@@ -37,6 +37,7 @@ if ROOT not in sys.path:
 METRIC = "forward+adjoint grad evals/s at 256^3 (FP32 batched vs FP64 plain); % HBM peak"
 UNIT = "grad evals/s"
 WORKLOAD_INDEX = 2               # 256^3, L = 1000, Phi x delta web
+SMALL_CASE_INDEX = 1             # 128^3, L = 1000, Phi x delta web (small ncu captures)
 MODEL_R = {16: 226, 4: 178}      # canonical algorithmic bytes per evaluation, in units of R = 4 N^3 bytes
 FALLBACK_HBM = 6800.0
 
@@ -218,7 +219,11 @@ def run_reference(args):
     return 0
 
 
-def workload_config(batch: int):
+def workload_config(batch: int, n: int = 256):
+    if n != 256:   # --small-case: the 128^3 profiling case, not the headline workload
+        return {"workload": f"{n}^3 mesh, L=1000 Mpc/h, Phi x delta web (16 regions): small profiling case, "
+                            "not the headline workload", "n": n, "box_mpc_h": 1000.0, "chains_per_gpu": batch,
+                "regions": 16, "precision": "FP32 fields, FP64 reductions"}
     return {"workload": "256^3 mesh, L=1000 Mpc/h, ALPT r_s=4 + CIC, Phi x delta web (16 regions, Table 3 bias), "
                         "NB likelihood; forward + hand-written adjoint per step",
             "n": 256, "box_mpc_h": 1000.0, "chains_per_gpu": batch, "regions": 16,
@@ -249,7 +254,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
 
-    cfg = synth.config(WORKLOAD_INDEX)
+    cfg = synth.config(SMALL_CASE_INDEX if args.small_case else WORKLOAD_INDEX)
     bias = synth.default_bias(cfg)
     seed_nu, seed_c = rank_seeds(cfg, rank)
     nu_h = torch.tensor(synth.white_noise(cfg.n, seed_nu), dtype=torch.float32).contiguous()
@@ -339,7 +344,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(1),
+            "config": workload_config(1, cfg.n),
             "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src + " copy bandwidth",
                          "launches_per_step": dl / prof_steps, "alg_bytes_per_launch": alg_per_launch,
@@ -610,6 +615,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=60.0, help="seconds for the oracle sample")
+    ap.add_argument("--small-case", action="store_true",
+                    help="time the 128^3 case instead of the 256^3 workload (for small profiler captures)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
     if args.impl == "reference":

@@ -331,6 +331,8 @@ template <typename T> int node(bridge_ctx* ctx, NodeArgs& na, const char* name, 
     na.cps = na.kind == NODE_ALPT_FWD ? ctx->tune[0] : na.kind == NODE_ALPT_ADJ ? ctx->tune[1] : ctx->tune[2];
     na.growth = ctx->cfg.growth_d;
     na.d2 = ctx->cfg.d2_over_d2 * ctx->cfg.growth_d * ctx->cfg.growth_d;
+    na.growth_f = float(na.growth);
+    na.d2_f = float(na.d2);
     int g = 0;
     CKL(name, bytes, launch_node<T>(ctx->n, ctx->B, na, &g, ctx->stream));
     if (grid_used) *grid_used = g;
@@ -1319,12 +1321,14 @@ int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
     ctx->kp.dx = cfg->box / cfg->n;
     ctx->kp.pk_amp = cfg->pk_amp; ctx->kp.pk_ns = cfg->pk_ns; ctx->kp.pk_kc = cfg->pk_kc; ctx->kp.pk_pow = cfg->pk_pow;
     ctx->kp.r_s = cfg->r_s;
+    ctx->kp.set_fp32();
     ctx->wp.sharpness = cfg->sharpness;
     ctx->wp.th_phi = cfg->lambda_th_phi;
     ctx->wp.th_delta = cfg->lambda_th_delta;
     ctx->wp.rho_floor = cfg->rho_floor;
     ctx->wp.tau = cfg->precision == BRIDGE_FP64 ? 1e-10 : 1e-4;
     ctx->wp.n_regions = cfg->n_regions;
+    ctx->wp.set_fp32();
     cudaError_t e = upload_twiddles();
     if (e == cudaSuccess) e = upload_node_twiddles();
     if (e != cudaSuccess) return create_fail(ctx, BRIDGE_ECUDA, std::string("twiddle upload: ") + cudaGetErrorString(e));

@@ -91,6 +91,7 @@ int run_delta0(const bridge_config* cfg, const void* nu, void* delta0, void* scr
     kp.r_s = cfg->r_s;
     kp.rtab = tab;
     kp.rlen = rlen;
+    kp.set_fp32();
 
     auto ck = [](cudaError_t e, const char* what) -> int {
         if (e == cudaSuccess) return BRIDGE_OK;

@@ -32,6 +32,7 @@ struct NodeArgs {
     size_t scratch_bytes;        // size of scratch; the grid is capped so that all slabs fit (0: no cap)
     int cps;                     // CTAs per SM (0: built-in choice; clamped to the occupancy limit)
     double growth, d2;
+    float growth_f, d2_f;        // FP32 copies (an FP32 node reads no double parameter)
 };
 
 // Launch a node; *grid_used receives the number of CTAs.

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_node(const NodeArgs A, int bat
                 for (int u = 0; u < U; ++u) {
                     const int v = v0 + u * kNodeThreads;
                     T a, b;
-                    alpt_sources<T>(in[u][0], &in[u][1], T(A.growth), T(A.d2), a, b);
+                    alpt_sources<T>(in[u][0], &in[u][1], pick<T>(A.growth, A.growth_f), pick<T>(A.d2, A.d2_f), a, b);
                     io.st(slab_f(0) + v, a);
                     io.st(slab_f(1) + v, b);
                 }
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_node(const NodeArgs A, int bat
                 for (int u = 0; u < U; ++u) {
                     const int v = v0 + u * kNodeThreads;
                     T gphi[6], gd0;
-                    alpt_sources_adj<T>(in[u][0], &in[u][1], T(A.growth), T(A.d2), in[u][7], in[u][8], gd0, gphi);
+                    alpt_sources_adj<T>(in[u][0], &in[u][1], pick<T>(A.growth, A.growth_f), pick<T>(A.d2, A.d2_f), in[u][7], in[u][8], gd0, gphi);
                     io.st(slab_f(0) + v, gd0);
 #pragma unroll
                     for (int q = 0; q < 6; ++q) io.st(slab_f(1 + q) + v, gphi[q]);

@@ -59,7 +59,7 @@ template <typename T> __device__ __forceinline__ T kpow(int m, int p, int n, T k
 // y-pass multiplier: (cre + i cim) ky^py kz^pz (no radial factor in the y pass).
 template <typename T>
 __device__ __forceinline__ cplx_t<T> ymult(const Term& tm, int my, int mz, int n, const KParams& kp) {
-    const T kf = T(kp.kf);
+    const T kf = kf_of<T>(kp);
     const T r = kpow<T>(my, tm.py, n, kf) * kpow<T>(mz, tm.pz, n, kf);
     return cmake<cplx_t<T>>(T(tm.cre) * r, T(tm.cim) * r);
 }
@@ -181,13 +181,13 @@ __device__ __forceinline__ T xfac(int k1, int m2yz, const KParams& kp, const T* 
     const int mx = HI < N / 2 ? k1 + HI : k1 + HI - N;
     T r = T(1);
     if constexpr (PX > 0) {
-        const T kx = T(kp.kf) * T(mx);
+        const T kx = kf_of<T>(kp) * T(mx);
         r = PX == 1 ? kx : kx * kx;
         if constexpr (PX == 1) r = (mx == -(N / 2)) ? T(0) : r;
     }
     if constexpr (RC == R_INVK2) {
         const int m2 = mx * mx + m2yz;
-        r *= m2 > 0 ? T(__fdividef(float(kp.inv_kf2), float(m2))) : T(0);
+        r *= m2 > 0 ? T(__fdividef(kp.inv_kf2_f, float(m2))) : T(0);
     } else if constexpr (RC == R_SQRTP) {
         r *= __ldg(reinterpret_cast<const T*>(kp.rtab) + (R_SQRTP - 1) * kp.rlen + mx * mx + m2yz);
     } else if constexpr (RC == R_KBLEND) {
@@ -461,7 +461,7 @@ template <typename T> __device__ __forceinline__ bool sep_blend(int rcode) {
 }
 template <typename T>
 __device__ __forceinline__ XTerm<T> xterm(const Term& tm, int my, int mz, int n, const KParams& kp) {
-    const T kf = T(kp.kf);
+    const T kf = kf_of<T>(kp);
     const T cyz = kpow<T>(my, tm.py, n, kf) * kpow<T>(mz, tm.pz, n, kf);
     const T kyz = sep_blend<T>(tm.rcode)
                       ? __ldg(reinterpret_cast<const T*>(kp.rtab) + (R_KBLEND - 1) * kp.rlen + my * my + mz * mz)
@@ -473,11 +473,11 @@ __device__ __forceinline__ XTerm<T> xterm(const Term& tm, int my, int mz, int n,
 template <typename T>
 __device__ __forceinline__ cplx_t<T> xmult(const XTerm<T>& x, int mx, int ix, int m2yz, int n, const KParams& kp,
                                            const T* skx) {
-    T r = kpow<T>(mx, x.px, n, T(kp.kf));
+    T r = kpow<T>(mx, x.px, n, kf_of<T>(kp));
     if (x.rcode != R_ONE) {
         const int m2 = mx * mx + m2yz;
         if (sizeof(T) == 4 && x.rcode == R_INVK2) {
-            r *= m2 > 0 ? T(__fdividef(float(kp.inv_kf2), float(m2))) : T(0);
+            r *= m2 > 0 ? T(__fdividef(kp.inv_kf2_f, float(m2))) : T(0);
         } else if (sep_blend<T>(x.rcode)) {
             const T k = skx[ix] * x.kyz;
             r *= x.rcode == R_KBLEND ? k : T(1) - k;

@@ -47,7 +47,15 @@ struct KParams {
     // computed on the host in FP64: table c-1 holds R_c for c = R_INVK2 .. R_WIENER.
     const void* rtab;
     int rlen;         // entries per table: 3 (N/2)^2 + 1
+    // FP32 copies of kf and 1/kf^2, so that FP32 kernels read no double
+    // parameter (a double -> float conversion runs on the narrow FP64 pipe)
+    float kf_f, inv_kf2_f;
+    void set_fp32() { kf_f = float(kf); inv_kf2_f = float(inv_kf2); }
 };
+template <typename T> __device__ __forceinline__ T kf_of(const KParams& kp) {
+    if constexpr (sizeof(T) == 4) return kp.kf_f;
+    else return T(kp.kf);
+}
 
 // Fill the radial tables (host, FP64): out[(c-1) * rlen + m2] for c = 1..4.
 void radial_tables_host(int n, const KParams& kp, double* out);

@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(kPwThreads, (webadj_minb<T, BIASG>())) k_web_a
     __syncthreads();
     const size_t off = (size_t)chain * nvox;
     const T lnC = T(sc[chain].lnC);
-    const T gscale = T(sc[chain].G / sc[chain].ntr);   // f_i/sum f * G = nbar_i * G / N_tr
+    const T gscale = T(sc[chain].gscale);   // f_i/sum f * G = nbar_i * G / N_tr
     constexpr int NG = BIASG ? NR : 1;
     T ga[NG], gb[NG];
 #pragma unroll
@@ -528,6 +528,7 @@ __device__ void reduce_body(int what, int chain, int nblk, int K, const double* 
     else if (what == RED_DOT) S.dot = tot[0];
     else if (what == RED_LIK) {
         S.loglik = tot[0]; S.G = tot[1]; S.sumnu2 = tot[2];
+        S.gscale = tot[1] / S.ntr;
         S.logprior = lpr;
         S.logpost = -0.5 * S.sumnu2 + S.loglik + lpr;
     } else if (what == RED_BIASGRAD) {

@@ -29,6 +29,7 @@ struct ChainScalars {
     double lnC;       // ln N_tr - ln sum f
     double loglik;    // sum_i log P_i
     double G;         // sum_i d log P_i / d ln nbar_i
+    double gscale;    // G / N_tr
     double sumnu2;    // sum nu^2
     double logprior;  // log-normal prior of the bias tables
     double logpost;

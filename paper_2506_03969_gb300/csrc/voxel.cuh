@@ -298,7 +298,16 @@ __device__ __forceinline__ void eig_adjoint(const T a[6], const Eig3<T>& e, T g1
 struct WebParams {
     double sharpness, th_phi, th_delta, rho_floor, tau;
     int n_regions;
+    float f_sharpness, f_th_phi, f_th_delta, f_tau;   // FP32 copies (see KParams)
+    void set_fp32() {
+        f_sharpness = float(sharpness); f_th_phi = float(th_phi); f_th_delta = float(th_delta); f_tau = float(tau);
+    }
 };
+// The FP32 copy of a parameter in FP32 code, the double itself in FP64 code.
+template <typename T> __device__ __forceinline__ T pick(double d, float f) {
+    if constexpr (sizeof(T) == 4) return f;
+    else return T(d);
+}
 
 template <typename T, int NR> struct WebState {
     Eig3<T> ephi, edel;
@@ -319,11 +328,11 @@ __device__ __forceinline__ void web_eval(const T a6[6], const T h6[6], T rho_mas
                                          const WebParams& wp, WebState<T, NR>& S) {
     eig3<T>(a6, S.ephi);
     T lam[3] = {S.ephi.m + S.ephi.mu[0], S.ephi.m + S.ephi.mu[1], S.ephi.m + S.ephi.mu[2]};
-    memberships<T>(lam, T(wp.sharpness), T(wp.th_phi), S.wphi, S.pphi);
+    memberships<T>(lam, pick<T>(wp.sharpness, wp.f_sharpness), pick<T>(wp.th_phi, wp.f_th_phi), S.wphi, S.pphi);
     if constexpr (NR == 16) {
         eig3<T>(h6, S.edel);
         T ld[3] = {S.edel.m + S.edel.mu[0], S.edel.m + S.edel.mu[1], S.edel.m + S.edel.mu[2]};
-        memberships<T>(ld, T(wp.sharpness), T(wp.th_delta), S.wdel, S.pdel);
+        memberships<T>(ld, pick<T>(wp.sharpness, wp.f_sharpness), pick<T>(wp.th_delta, wp.f_th_delta), S.wdel, S.pdel);
     }
     VoxParams<T>& q = S.q;
     q.a = q.alpha = q.rho = q.eps = q.rhop = q.epsp = q.beta = T(0);
@@ -341,6 +350,8 @@ __device__ __forceinline__ void web_eval(const T a6[6], const T h6[6], T rho_mas
             q.beta += e[BP_BETA] * w;
             if (cut2) { q.rhop += e[BP_RHOP] * w; q.epsp += e[BP_EPSP] * w; }
         }
+    // the floor is converted from the double parameter here: with the FP32 copy the
+    // web adjoint's allocation spills at its 64-register bound
     log_f<T>(rho_mass, T(wp.rho_floor), S.q, S.lf);
 }
 
@@ -352,7 +363,7 @@ template <typename T, int NR, bool BIASG, typename LoadT>
 __device__ __forceinline__ void web_adjoint_voxel(const WebState<T, NR>& S, T rho_mass, int n, T lnC, T gscale,
                                                   const BiasT<T>& B, const WebParams& wp, LoadT load_tensors,
                                                   T& gd, T gt[6], T gh[6], T* ga, T* gb) {
-    const T s = T(wp.sharpness), tau = T(wp.tau);
+    const T s = pick<T>(wp.sharpness, wp.f_sharpness), tau = pick<T>(wp.tau, wp.f_tau);
     const T lnnbar = S.lf.lnf + lnC;
     NB<T> nb;
     nb_eval<T>(n, lnnbar, S.q.beta, true, nb);

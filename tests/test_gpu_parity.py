@@ -560,12 +560,23 @@ def test_batched_16x128_workload():
     lp, g, gb = ctx.bridge_logpost_grad(nu_d, c_d, biases)
     del ctx
     single = pkg.Context(pkg.config_from(cb, batch=1))
-    worst = 0.0
+    # Two evaluations of one input differ by the order of the CIC atomic adds; at the untreated
+    # chains that difference is amplified by their conditioning.  The batched gradient must agree
+    # with the single-chain one to 1e-5 or, where larger, to three times the largest difference
+    # between two single-chain evaluations of the same input.
+    e_bat, e_rr, lps = [], [], []
     for b in range(cb.batch):
         lp1, g1, _ = single.bridge_logpost_grad(nu_d[b].contiguous(), c_d[b].contiguous(), [biases[b]])
-        e = rel_l2(g1.cpu().numpy(), g[b].cpu().numpy())
-        worst = max(worst, e)
-        assert abs(lp1[0] - lp[b]) <= 1e-7 * abs(lp[b]) and e <= 1e-5, (b, e)
+        g1 = g1.cpu().numpy()
+        _, g1b, _ = single.bridge_logpost_grad(nu_d[b].contiguous(), c_d[b].contiguous(), [biases[b]])
+        e_bat.append(rel_l2(g1, g[b].cpu().numpy()))
+        e_rr.append(rel_l2(g1b.cpu().numpy(), g1))
+        lps.append(lp1[0])
+    tol_b = max(1e-5, 3.0 * max(e_rr))
+    print(f"16 x 128^3: batched vs single gradient rel L2 max {max(e_bat):.2e}, run-to-run max {max(e_rr):.2e} "
+          f"(tolerance {tol_b:.1e})")
+    for b in range(cb.batch):
+        assert abs(lps[b] - lp[b]) <= 1e-7 * abs(lp[b]) and e_bat[b] <= tol_b, (b, e_bat[b], tol_b)
         if b in ref:
             f_o, lp_o, g_o, gb_o, cond = ref[b]
             e_o = rel_l2(g[b].double().cpu().numpy(), g_o)
@@ -575,7 +586,6 @@ def test_batched_16x128_workload():
                   f"S_psi {f_o['cond_psi_bias']:.1e}, kappa {f_o['kappa_bias']:.0f})")
             assert abs(lp[b] - lp_o) <= FP32_LP * abs(lp_o) and e_o <= grad_tol("fp32", f_o)
             assert e_b <= bias_tol("fp32", f_o)
-    print(f"16 x 128^3: worst single-vs-batched gradient rel L2 {worst:.2e}")
 
 
 def central_differences(ctx, nu_d, c_d, bias, dirs, h):
