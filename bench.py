@@ -21,6 +21,7 @@ Under torchrun (N > 1) every rank runs its own chain (replicas, weak scaling).
 from __future__ import annotations
 
 import argparse
+import copy
 import hashlib
 import json
 import math
@@ -602,6 +603,19 @@ def run_extras(pkg, synth, cfg, bias, nu32, counts, args):
     t5 = timed(lambda: ctx5.bridge_logpost_grad(nu5, cn5, [b5], grad_out=g5, want_bias_grad=False), 3)
     out["single_512"] = {"evals_per_s": 1.0 / t5, "ms_per_eval": 1e3 * t5,
                          "workspace_gb": pkg.lib().bridge_workspace_bytes(pkg.config_from(c5, batch=1)) / 1e9}
+    del ctx5, g5
+    # redshift space (Sect. 2.9, f = 0.8): plane-parallel and radial line of sight, 256^3 and 512^3
+    rsd = {}
+    for label, cbase, bx, nux, cnx in (("256", cfg, bias, nu, counts), ("512", c5, b5, nu5, cn5)):
+        for los, name in ((0, "plane_parallel"), (1, "radial")):
+            cr = copy.copy(cbase)
+            cr.rsd_f, cr.rsd_los = 0.8, los
+            cx = pkg.Context(pkg.config_from(cr, batch=1))
+            gx = torch.empty_like(nux)
+            tx = timed(lambda: cx.bridge_logpost_grad(nux, cnx, [bx], grad_out=gx, want_bias_grad=False), 3)
+            rsd[f"{name}_{label}"] = {"evals_per_s": 1.0 / tx, "ms_per_eval": 1e3 * tx}
+            del cx, gx
+    out["redshift_space"] = rsd
     return out
 
 

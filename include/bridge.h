@@ -90,11 +90,17 @@ typedef struct {
                                 1: the adjoint recomputes them from nu (10 fewer
                                 half spectra in the workspace, about 39 R more HBM
                                 traffic per gradient evaluation, R = N^3 floats)   */
-    double rsd_f;            /* redshift space (Sect. 2.9, b_v = 1): plane-parallel line
-                                of sight along z with the linear velocity v/(aH) =
-                                f Psi_1, i.e. Psi_z += f Psi_1,z (Psi_1 the Zel'dovich
-                                displacement) before the mass assignment; 0 = real
-                                space; finite                                        */
+    double rsd_f;            /* redshift space (Sect. 2.9, Eq. of delta(s), b_v = 1) with
+                                the linear velocity v/(aH) = f Psi_1 (Psi_1 the
+                                Zel'dovich displacement) applied before the mass
+                                assignment; 0 = real space; finite                   */
+    int32_t rsd_los;         /* line of sight when rsd_f != 0: 0 = plane-parallel
+                                along z, Psi_z += f Psi_1,z; 1 = radial from an
+                                observer at the centre of the volume, Psi += f
+                                (Psi_1 . r) r / |r|^2 with r = q + Psi - (N/2)(1,1,1)
+                                the particle's real-space position in cell units
+                                relative to the observer (a particle at r = 0 is not
+                                moved); 6 more half spectra in the workspace.  0 or 1 */
 } bridge_config;
 
 /* Bias table of one chain; entries [0, n_regions) are used (Eq. local_bias,
@@ -272,7 +278,8 @@ int bridge_dot(bridge_ctx* ctx, const void* a, const void* b, double* out);
 /* Intermediate fields of the forward model, for inspection and testing.
  * Writes the field selected by `which` for all chains to device `out`:
  *   BRIDGE_FIELD_DELTA0   [B][N^3]     linear density delta0 (App. A)
- *   BRIDGE_FIELD_PSI      [B][3][N^3]  ALPT displacement in cell units (Sect. 2.3)
+ *   BRIDGE_FIELD_PSI      [B][3][N^3]  ALPT displacement in cell units (Sect. 2.3), in redshift
+ *                                      space when rsd_f != 0 (the one the mass assignment uses)
  *   BRIDGE_FIELD_DELTA    [B][N^3]     CIC density contrast
  *   BRIDGE_FIELD_TIDAL    [B][6][N^3]  tidal tensor xx,xy,xz,yy,yz,zz (Sect. 2.8)
  *   BRIDGE_FIELD_HESSIAN  [B][6][N^3]  density Hessian (App. B; 16 regions only)

@@ -18,9 +18,11 @@ its reason in the design notes):
     lap phi2 = S2 = sum_{i<j}(phi1_ii phi1_jj - phi1_ij^2), D2 = (D2/D^2) D^2.
     Spherical collapse: Psi_SC curl-free with divergence
     3[(1 - 2/3 D delta0)^(1/2) - 1] for D delta0 < 3/2, else -3.
-  * Redshift space (Sect. 2.9), plane-parallel along z with b_v = 1 and the
-    linear velocity v/(aH) = f Psi_1 (config rsd_f = f; 0 = real space):
-    Psi_z += f Psi_1,z before the mass assignment.
+  * Redshift space (Sect. 2.9), b_v = 1 and the linear velocity v/(aH) =
+    f Psi_1 (config rsd_f = f; 0 = real space), before the mass assignment:
+    plane-parallel along z (rsd_los = 0): Psi_z += f Psi_1,z; radial from
+    the centre of the volume (rsd_los = 1): Psi += f (Psi_1 . r) r / |r|^2
+    with r the particle's real-space position relative to the centre.
   * CIC: the particle of cell q sits at q + Psi/dx (cell units); trilinear
     weights, periodic; delta = rho - 1 (one particle per cell).
   * Phi-web: tidal tensor T_jk = d_j d_k Phi with lap Phi = delta (Sect. 2.8);
@@ -212,15 +214,33 @@ def alpt_displacement(delta0: torch.Tensor, cfg, g: Optional[Grid] = None, parts
         sc = gj * phisc_h
         psi.append(g.irfft(kern * lpt + (1.0 - kern) * sc) / g.dx)
     f_rsd = getattr(cfg, "rsd_f", 0.0)
-    if f_rsd:
+    radial = bool(f_rsd) and getattr(cfg, "rsd_los", 0) == 1
+    if f_rsd and not radial:
         # redshift space (Sect. 2.9, Eq. of delta(s)) with b_v = 1, plane-parallel line of sight
         # along z and the linear-theory velocity v / (aH) = f Psi_1: s_z = r_z + f Psi_1,z, where
         # Psi_1 = -D grad phi1 is the first-order (Zel'dovich) displacement
         psi[2] = psi[2] + f_rsd * g.irfft(-D * g.grad_mult(2) * phi1_h) / g.dx
     psi = torch.stack(psi)
+    if radial:
+        psi1 = torch.stack([g.irfft(-D * g.grad_mult(j) * phi1_h) / g.dx for j in range(3)])
+        psi = radial_rsd(psi, psi1, f_rsd, g.n)
     if parts:
         return psi, dict(phi=phi, s2=s2, theta_sc=tsc)
     return psi
+
+
+def radial_rsd(psi: torch.Tensor, psi1: torch.Tensor, f: float, n: int) -> torch.Tensor:
+    """Redshift-space displacement with the observer at the centre of the volume (Sect. 2.9, Eq. of
+    delta(s), b_v = 1): s = r + (v . r) r / (aH r^2) with v/(aH) = f Psi_1, the linear-theory
+    velocity.  Cell units: the particle of cell q sits at q + Psi in real space, the observer at
+    the centre c = n/2 of the cube [0, n)^3, r = q + Psi - c (not wrapped), so
+        Psi_s = Psi + f (Psi_1 . r) r / |r|^2;
+    a particle exactly at the observer is not moved."""
+    q = torch.stack(torch.meshgrid(*(torch.arange(n, dtype=psi.dtype),) * 3, indexing="ij"))
+    r = q + psi - 0.5 * n
+    r2 = (r * r).sum(0)
+    a = torch.where(r2 > 0, (psi1 * r).sum(0) / torch.where(r2 > 0, r2, torch.ones_like(r2)), torch.zeros_like(r2))
+    return psi + f * a * r
 
 
 def cic_delta(psi_cells: torch.Tensor) -> torch.Tensor:

@@ -28,8 +28,10 @@ namespace {
 // holds 19 spectra instead of 29.
 // The adjoint keeps g_Psi_z (the gather node's third output) in scratch slot 17
 // until the delta0 adjoint, which the redshift-space term feeds.
+// The radial line of sight adds six slots after the others: the linear
+// displacement Psi_1 (3, kept like Psi) and its adjoint from the gather node (3).
 enum { SP_SCR = 0, SP_TH = 7, SP_ALPT_STORED = 19, SP_PSI_STORED = 26, kMaxSpec = 29,
-       SP_ALPT_RECOMP = 7, SP_PSI_RECOMP = 14, SP_GPSIZ = 17, kScratchSpec = 19 };
+       SP_ALPT_RECOMP = 7, SP_PSI_RECOMP = 14, SP_GPSIZ = 17, kScratchSpec = 19, kRadialSpec = 6 };
 // Real buffers.
 enum {
     RB_DELTA = 0,   // 1: CIC mass rho = 1 + delta
@@ -60,12 +62,14 @@ struct bridge_ctx {
     int n = 0, B = 0, nr = 4;
     int sp_alpt = SP_ALPT_STORED, sp_psi = SP_PSI_STORED;   // ALPT spectrum slots (recompute_alpt moves them)
     bool recompute = false;
+    bool radial = false;                 // radial line of sight (rsd_f != 0, rsd_los = 1)
+    int sp_psi1 = 0, sp_gpsi1 = 0;       // its Psi_1 and g_Psi_1 slots
     long long nvox = 0, nspec = 0;
     size_t esz = 4;
     // workspace
     void* ws = nullptr;
     size_t ws_bytes = 0;
-    void* spec[kMaxSpec] = {};
+    void* spec[kMaxSpec + kRadialSpec] = {};
     void* real[kMaxReal] = {};
     uint16_t* c16 = nullptr;
     double* partial = nullptr;
@@ -182,6 +186,7 @@ int validate(const bridge_config* c, std::string* why) {
     if (c->precision != BRIDGE_FP32 && c->precision != BRIDGE_FP64) return bad("precision must be FP32 or FP64");
     if (c->recompute_alpt != 0 && c->recompute_alpt != 1) return bad("recompute_alpt must be 0 or 1");
     if (!std::isfinite(c->rsd_f)) return bad("rsd_f must be finite");
+    if (c->rsd_los != 0 && c->rsd_los != 1) return bad("rsd_los must be 0 (plane-parallel) or 1 (radial)");
     return BRIDGE_OK;
 }
 
@@ -229,7 +234,7 @@ Plan make_plan(const bridge_config* c) {
     const long long n = c->n, B = c->batch;
     const size_t esz = c->precision == BRIDGE_FP64 ? 8 : 4;
     const long long nvox = n * n * n, nspec = (n / 2 + 1) * n * n;
-    p.nspec_buf = c->recompute_alpt ? kScratchSpec : kMaxSpec;
+    p.nspec_buf = (c->recompute_alpt ? kScratchSpec : kMaxSpec) + (c->rsd_f != 0.0 && c->rsd_los == 1 ? kRadialSpec : 0);
     p.nreal_buf = kMaxReal;
     p.spec_bytes = align_up(size_t(nspec) * 2 * esz * B);
     p.real_bytes = align_up(size_t(nvox) * esz * B);
@@ -333,6 +338,8 @@ template <typename T> int node(bridge_ctx* ctx, NodeArgs& na, const char* name, 
     na.d2 = ctx->cfg.d2_over_d2 * ctx->cfg.growth_d * ctx->cfg.growth_d;
     na.growth_f = float(na.growth);
     na.d2_f = float(na.d2);
+    na.rsd_f = ctx->cfg.rsd_f;
+    na.rsd_f_f = float(na.rsd_f);
     int g = 0;
     CKL(name, bytes, launch_node<T>(ctx->n, ctx->B, na, &g, ctx->stream));
     if (grid_used) *grid_used = g;
@@ -379,14 +386,36 @@ template <typename T> int run_alpt(bridge_ctx* ctx, const T* nu) {
         RUN(node<T>(ctx, na, "node_alpt", 9 * sby<T>(ctx), nullptr));
     }
     RUN(y_identity<T>(ctx, SP_SCR, 2, true));
+    // the radial line of sight also needs V1 = kx delta0_hat / k^2 (slot 3) for Psi_1,x: the
+    // blend then writes to slots 5, 6 instead of 2, 3
+    const int sp_blend = ctx->radial ? SP_SCR + 5 : SP_SCR + 2;
     {
-        PassProgram p = program(cspec<T>(ctx, SP_SCR, 2), mspec<T>(ctx, SP_SCR + 2, 2), ctx->nspec);
+        PassProgram p = program(cspec<T>(ctx, SP_SCR, 2), mspec<T>(ctx, sp_blend, 2), ctx->nspec);
         add_merge(p, mk(0, 0, 0, 0, 0, R_KBLEND, invn3));
         add_merge(p, mk(1, 0, 0, 0, 0, R_1MKBLEND, invn3));
         const double c = -1.0 / ctx->kp.dx;               // Psi_j = -i k_j theta / (k^2 dx)
         add_expand(p, mk(0, 0, 1, 0, 0, R_INVK2, 0.0, c));
         add_expand(p, mk(0, 1, 0, 0, 0, R_INVK2, 0.0, c));
         CKL("x_node", (p.n_in + p.n_out) * sby<T>(ctx), launch_x_node<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+    }
+    if (ctx->radial) {
+        // radial line of sight (Sect. 2.9): Psi and the linear displacement Psi_1 = (i D / dx) k
+        // delta0_hat / k^2 separately, Psi_1,x from V1 (slot 3), Psi_1,y and Psi_1,z from V0
+        // (slot 4); the per-particle projection on the line of sight follows in real space
+        std::vector<const void*> in = {ctx->spec[SP_SCR + 5], ctx->spec[SP_SCR + 6], ctx->spec[SP_SCR + 3],
+                                       ctx->spec[SP_SCR + 4]};
+        std::vector<void*> out = mspec<T>(ctx, ctx->sp_psi, 3);
+        for (int j = 0; j < 3; ++j) out.push_back(ctx->spec[ctx->sp_psi1 + j]);
+        PassProgram p = program(in, out, ctx->nspec);
+        const double c1 = ctx->cfg.growth_d / ctx->kp.dx;
+        add_expand(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));
+        add_expand(p, mk(1, 1, 0, 1, 0, R_ONE, 1.0));
+        add_expand(p, mk(1, 2, 0, 0, 1, R_ONE, 1.0));
+        add_expand(p, mk(2, 3, 0, 0, 0, R_ONE, 0.0, c1));
+        add_expand(p, mk(3, 4, 0, 1, 0, R_ONE, 0.0, c1));
+        add_expand(p, mk(3, 5, 0, 0, 1, R_ONE, 0.0, c1));
+        CKL("y_inv", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_inv<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
+        return BRIDGE_OK;
     }
     {
         // redshift space (Sect. 2.9), plane-parallel along z with the linear velocity
@@ -406,6 +435,19 @@ template <typename T> int run_alpt(bridge_ctx* ctx, const T* nu) {
     return BRIDGE_OK;
 }
 
+// The displacement the mass assignment uses, in real space at real buffers
+// first..first+2: Psi, or with the radial line of sight Psi shifted by
+// f (Psi_1 . r) r / |r|^2 (Psi_1 passes through first+3..first+5).
+template <typename T> int psi_real(bridge_ctx* ctx, int first) {
+    if (!ctx->radial) return z_inv<T>(ctx, cspec<T>(ctx, ctx->sp_psi, 3), mreal(ctx, first, 3));
+    std::vector<const void*> in = cspec<T>(ctx, ctx->sp_psi, 3);
+    for (int j = 0; j < 3; ++j) in.push_back(ctx->spec[ctx->sp_psi1 + j]);
+    RUN(z_inv<T>(ctx, in, mreal(ctx, first, 6)));
+    CKL("rsd_radial", 9 * rby<T>(ctx), launch_rsd_radial<T>(ctx->n, ctx->B, fields(ctx, first, 3), fields(ctx, first + 3, 3),
+                                                            ctx->cfg.rsd_f, ctx->stream));
+    return BRIDGE_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Forward model.  Leaves in the workspace: the ALPT and displacement spectra
 // (unless recompute_alpt), rho, the tensors in real space, ln f and beta_i,
@@ -418,7 +460,7 @@ template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelih
     RUN(run_alpt<T>(ctx, nu));
     // CIC (mass rho accumulated into a zeroed field); the displacement in real
     // space borrows the tensor buffers, which are written only afterwards
-    RUN(z_inv<T>(ctx, cspec<T>(ctx, ctx->sp_psi, 3), mreal(ctx, RB_TH, 3)));
+    RUN(psi_real<T>(ctx, RB_TH));
     CKL("fill", rby<T>(ctx), launch_fill<T>(ctx->nvox * ctx->B, RB<T>(ctx, RB_DELTA), T(0), ctx->stream));
     CKL("cic_scatter", 4 * rby<T>(ctx), launch_cic_scatter<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 3), RB<T>(ctx, RB_DELTA), ctx->stream));
     // tidal tensor and density Hessian spectra (Sect. 2.8, App. B)
@@ -518,13 +560,17 @@ template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad, boo
     // CIC adjoint with the displacement recomputed from its spectra, then r2c
     {
         NodeArgs na{};
-        na.kind = NODE_GATHER;
+        na.kind = ctx->radial ? NODE_GATHER_RSD : NODE_GATHER;
         for (int f = 0; f < 3; ++f) {
             na.spec_in[f] = ctx->spec[ctx->sp_psi + f];
             na.spec_out[f] = ctx->spec[f < 2 ? SP_SCR + f : SP_GPSIZ];
+            if (ctx->radial) {
+                na.spec_in[3 + f] = ctx->spec[ctx->sp_psi1 + f];
+                na.spec_out[3 + f] = ctx->spec[ctx->sp_gpsi1 + f];
+            }
         }
         na.real_in[0] = ctx->real[RB_GD];
-        RUN(node<T>(ctx, na, "node_cic_gather", 6 * sby<T>(ctx) + rby<T>(ctx), nullptr));
+        RUN(node<T>(ctx, na, "node_cic_gather", (ctx->radial ? 12 : 6) * sby<T>(ctx) + rby<T>(ctx), nullptr));
     }
     {
         PassProgram p = program({ctx->spec[SP_SCR], ctx->spec[SP_SCR + 1], ctx->spec[SP_GPSIZ]},
@@ -555,12 +601,22 @@ template <typename T> int run_adjoint(bridge_ctx* ctx, const T* nu, T* grad, boo
         RUN(node<T>(ctx, na, "node_alpt_adj", 16 * sby<T>(ctx), nullptr));
     }
     {
-        const bool rsd = ctx->cfg.rsd_f != 0.0;
+        const bool rsd = ctx->cfg.rsd_f != 0.0 && !ctx->radial;
         std::vector<const void*> in = cspec<T>(ctx, SP_SCR, 7);
         if (rsd) in.push_back(ctx->spec[SP_GPSIZ]);
+        if (ctx->radial)
+            for (int j = 0; j < 3; ++j) in.push_back(ctx->spec[ctx->sp_gpsi1 + j]);
         PassProgram p = program(in, mspec<T>(ctx, SP_SCR + 7, 4), ctx->nspec);
         // transpose of the redshift-space term: V0' += conj(i f D / dx) kz g_Psi_z
         if (rsd) add_merge(p, mk(7, 3, 0, 0, 1, R_ONE, 0.0, -ctx->cfg.rsd_f * ctx->cfg.growth_d / ctx->kp.dx));
+        if (ctx->radial) {
+            // transpose of Psi_1 = (i D / dx) (V1, ky V0, kz V0): V1' += conj(i D / dx) g_Psi1,x,
+            // V0' += conj(i D / dx) (ky g_Psi1,y + kz g_Psi1,z)
+            const double c1 = -ctx->cfg.growth_d / ctx->kp.dx;
+            add_merge(p, mk(7, 2, 0, 0, 0, R_ONE, 0.0, c1));
+            add_merge(p, mk(8, 3, 0, 1, 0, R_ONE, 0.0, c1));
+            add_merge(p, mk(9, 3, 0, 0, 1, R_ONE, 0.0, c1));
+        }
         add_merge(p, mk(0, 0, 0, 0, 0, R_ONE, 1.0));   // W0' <- g_delta0
         add_merge(p, mk(1, 1, 0, 0, 0, R_ONE, 1.0));   // V2' <- g_phi_xx
         add_merge(p, mk(2, 2, 0, 1, 0, R_ONE, 1.0));   // V1' <- ky g_phi_xy + kz g_phi_xz
@@ -1059,7 +1115,7 @@ template <typename T> int do_debug(bridge_ctx* ctx, const void* nu, const int32_
             break;
         case BRIDGE_FIELD_PSI:
             if (ctx->recompute) RUN(run_alpt<T>(ctx, reinterpret_cast<const T*>(nu)));
-            RUN(z_inv<T>(ctx, cspec<T>(ctx, ctx->sp_psi, 3), mreal(ctx, RB_SCR, 3)));
+            RUN(psi_real<T>(ctx, RB_SCR));
             RUN(copy_fields(RB_SCR, 3));
             break;
         case BRIDGE_FIELD_DELTA:
@@ -1316,6 +1372,9 @@ int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
     ctx->recompute = cfg->recompute_alpt != 0;
     ctx->sp_alpt = ctx->recompute ? SP_ALPT_RECOMP : SP_ALPT_STORED;
     ctx->sp_psi = ctx->recompute ? SP_PSI_RECOMP : SP_PSI_STORED;
+    ctx->radial = cfg->rsd_f != 0.0 && cfg->rsd_los == 1;
+    ctx->sp_psi1 = ctx->recompute ? kScratchSpec : kMaxSpec;
+    ctx->sp_gpsi1 = ctx->sp_psi1 + 3;
     ctx->kp.kf = 2.0 * kPi / cfg->box;
     ctx->kp.inv_kf2 = 1.0 / (ctx->kp.kf * ctx->kp.kf);
     ctx->kp.dx = cfg->box / cfg->n;

@@ -19,7 +19,9 @@ namespace bridge {
 enum NodeKind {
     NODE_ALPT_FWD = 2,   // delta0, phi (7) -> a = -D delta0 + D2 S2, theta_SC -> r2c (2)
     NODE_ALPT_ADJ = 3,   // delta0, phi (7), g_a, g_b (2) -> g_delta0, g_phi -> r2c (7)
-    NODE_GATHER = 5      // psi (3) -> CIC gather adjoint g_psi -> r2c (3)
+    NODE_GATHER = 5,     // psi (3) -> CIC gather adjoint g_psi -> r2c (3)
+    NODE_GATHER_RSD = 6  // psi, psi1 (6) -> radial redshift space, CIC gather adjoint, its transpose
+                         // -> g_psi, g_psi1 -> r2c (6)
 };
 
 struct NodeArgs {
@@ -33,6 +35,8 @@ struct NodeArgs {
     int cps;                     // CTAs per SM (0: built-in choice; clamped to the occupancy limit)
     double growth, d2;
     float growth_f, d2_f;        // FP32 copies (an FP32 node reads no double parameter)
+    double rsd_f;                // NODE_GATHER_RSD: f of the linear velocity
+    float rsd_f_f;
 };
 
 // Launch a node; *grid_used receives the number of CTAs.

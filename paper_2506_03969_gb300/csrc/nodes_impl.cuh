@@ -32,6 +32,7 @@ template <int KIND> struct NodeShape;
 template <> struct NodeShape<NODE_ALPT_FWD> { static constexpr int IN = 7, SLAB = 7, OUT = 2; };
 template <> struct NodeShape<NODE_ALPT_ADJ> { static constexpr int IN = 9, SLAB = 9, OUT = 7; };
 template <> struct NodeShape<NODE_GATHER> { static constexpr int IN = 3, SLAB = 3, OUT = 3; };
+template <> struct NodeShape<NODE_GATHER_RSD> { static constexpr int IN = 6, SLAB = 6, OUT = 6; };
 
 template <typename T, int N, int KIND>
 __global__ void __launch_bounds__(kNodeThreads) k_node(const NodeArgs A, int batch, long long nspec) {
@@ -64,7 +65,8 @@ __global__ void __launch_bounds__(kNodeThreads) k_node(const NodeArgs A, int bat
         // loads of all U voxels are issued before any result is stored, so a
         // step waits for one L2 round trip instead of U
         const size_t coff = (size_t)chain * NVOX;
-        constexpr int U = sizeof(T) == 8 ? 4 : BRIDGE_NODE_U;   // FP64: eight voxels would spill
+        // FP64 and the redshift-space gather: eight voxels would spill
+        constexpr int U = (sizeof(T) == 8 || KIND == NODE_GATHER_RSD) ? 4 : BRIDGE_NODE_U;
         static_assert(TV % (U * kNodeThreads) == 0, "tile voxels must split into whole steps");
         for (int v0 = t; v0 < TV; v0 += U * kNodeThreads) {
             if constexpr (KIND == NODE_ALPT_FWD) {
@@ -117,6 +119,40 @@ __global__ void __launch_bounds__(kNodeThreads) k_node(const NodeArgs A, int bat
                     io.st(slab_f(0) + v, out[0]);
                     io.st(slab_f(1) + v, out[1]);
                     io.st(slab_f(2) + v, out[2]);
+                }
+            } else if constexpr (KIND == NODE_GATHER_RSD) {
+                // the particle at its redshift-space position (rsd_radial_fwd), the CIC gather
+                // there, and the transpose of the shift (rsd_radial_adj)
+                const T* grho = reinterpret_cast<const T*>(A.real_in[0]) + coff;
+                const T f = pick<T>(A.rsd_f, A.rsd_f_f), cen = T(N / 2);
+                CicCorner<T> c[U];
+                RsdPoint<T> R[U];
+                T gv[U][8];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int v = v0 + u * kNodeThreads;
+                    const int z = v % N, xl = (v / N) % 16, yl = v / (16 * N);
+                    const int qv[3] = {x0 + xl, y0 + yl, z};
+                    const T ps[3] = {io.ld(slab_f(0) + v), io.ld(slab_f(1) + v), io.ld(slab_f(2) + v)};
+                    const T p1[3] = {io.ld(slab_f(3) + v), io.ld(slab_f(4) + v), io.ld(slab_f(5) + v)};
+                    T s[3];
+                    rsd_radial_fwd<T>(qv, cen, ps, p1, f, R[u], s);
+                    const long long q = ((long long)qv[0] * N + qv[1]) * N + z;
+                    cic_corner<T>(q, N, s[0], s[1], s[2], c[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) cic_gather_loads<T>(c[u], N, grho, gv[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int v = v0 + u * kNodeThreads;
+                    T G[3], gp[3], gp1[3];
+                    cic_gather_combine<T>(c[u], gv[u], G);
+                    rsd_radial_adj<T>(R[u], f, G, gp, gp1);
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        io.st(slab_f(j) + v, gp[j]);
+                        io.st(slab_f(3 + j) + v, gp1[j]);
+                    }
                 }
             }
         }
@@ -184,6 +220,7 @@ static cudaError_t node_dispatch(int batch, int sms, const NodeArgs& a, cudaStre
         case NODE_ALPT_FWD: return NodeLaunch<T, N, NODE_ALPT_FWD>::run(batch, sms, a, s, nspec, gu);
         case NODE_ALPT_ADJ: return NodeLaunch<T, N, NODE_ALPT_ADJ>::run(batch, sms, a, s, nspec, gu);
         case NODE_GATHER: return NodeLaunch<T, N, NODE_GATHER>::run(batch, sms, a, s, nspec, gu);
+        case NODE_GATHER_RSD: return NodeLaunch<T, N, NODE_GATHER_RSD>::run(batch, sms, a, s, nspec, gu);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -191,12 +228,14 @@ static cudaError_t node_dispatch(int batch, int sms, const NodeArgs& a, cudaStre
 template <typename T, int N> static int node_grid_max(int batch, int sms) {
     int g = NodeLaunch<T, N, NODE_ALPT_FWD>::grid(batch, sms);
     g = max(g, NodeLaunch<T, N, NODE_ALPT_ADJ>::grid(batch, sms));
+    g = max(g, NodeLaunch<T, N, NODE_GATHER_RSD>::grid(batch, sms));
     return max(g, NodeLaunch<T, N, NODE_GATHER>::grid(batch, sms));
 }
 
 template <typename T, int N> static size_t node_scratch_max(int batch, int sms) {
     size_t m = NodeLaunch<T, N, NODE_ALPT_FWD>::scratch(batch, sms);
     m = max(m, NodeLaunch<T, N, NODE_ALPT_ADJ>::scratch(batch, sms));
+    m = max(m, NodeLaunch<T, N, NODE_GATHER_RSD>::scratch(batch, sms));
     return max(m, NodeLaunch<T, N, NODE_GATHER>::scratch(batch, sms));
 }
 

@@ -362,6 +362,27 @@ __global__ void __launch_bounds__(kPwThreads, (webadj_minb<T, BIASG>())) k_web_a
 }
 
 
+// Radial redshift space in place: psi <- psi + f (psi1 . r) r / |r|^2 (see rsd_radial_fwd).
+template <typename T>
+__global__ void __launch_bounds__(kPwThreads) k_rsd_radial(int N, long long nvox, Fields16 psi, Fields16 psi1, T f) {
+    const size_t off = (size_t)blockIdx.y * nvox;
+    const int lg = __ffs(N) - 1, msk = N - 1;
+    const T c = T(N / 2);
+    T* p[3] = {(T*)psi.p[0] + off, (T*)psi.p[1] + off, (T*)psi.p[2] + off};
+    const T* p1[3] = {(const T*)psi1.p[0] + off, (const T*)psi1.p[1] + off, (const T*)psi1.p[2] + off};
+    PW_LOOP(i, nvox) {
+        const int q[3] = {(int)(i >> (2 * lg)), (int)((i >> lg) & msk), (int)(i & msk)};
+        const T v[3] = {p[0][i], p[1][i], p[2][i]};
+        const T v1[3] = {p1[0][i], p1[1][i], p1[2][i]};
+        RsdPoint<T> R;
+        T out[3];
+        rsd_radial_fwd<T>(q, c, v, v1, f, R, out);
+        p[0][i] = out[0];
+        p[1][i] = out[1];
+        p[2][i] = out[2];
+    }
+}
+
 template <typename T> __global__ void k_shift(long long count, const T* in, T* out, T c) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
         out[i] = in[i] + c;
@@ -604,6 +625,11 @@ cudaError_t launch_web_adjoint(int n, int batch, const Fields16& th, const T* de
     }
     return cudaGetLastError();
 }
+template <typename T>
+cudaError_t launch_rsd_radial(int n, int batch, const Fields16& psi, const Fields16& psi1, double f, cudaStream_t s) {
+    k_rsd_radial<T><<<dim3(pw_blocks(n), batch), kPwThreads, 0, s>>>(n, nvox_of(n), psi, psi1, T(f));
+    return cudaGetLastError();
+}
 template <typename T> cudaError_t launch_shift(long long count, const T* in, T* out, T c, cudaStream_t s) {
     long long b = (count + 1023) / 1024;
     k_shift<T><<<(unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b)), 256, 0, s>>>(count, in, out, c);
@@ -666,6 +692,7 @@ cudaError_t launch_reduce(int what, int nblk, int batch, const double* partial, 
                                                const BiasT<T>*, const WebParams&, const ChainScalars*,              \
                                                const Fields16&, double*, bool, cudaStream_t, int);                  \
     template cudaError_t launch_shift<T>(long long, const T*, T*, T, cudaStream_t);                                 \
+    template cudaError_t launch_rsd_radial<T>(int, int, const Fields16&, const Fields16&, double, cudaStream_t);    \
     template cudaError_t launch_kick_drift<T>(int, int, T*, T*, const T*, double, double, double*, cudaStream_t);   \
     template cudaError_t launch_scale_chains<T>(int, int, T*, const double*, cudaStream_t);                         \
     template cudaError_t launch_delta_tr<T>(int, int, const uint16_t*, const ChainScalars*, T*, cudaStream_t);       \

@@ -73,6 +73,10 @@ cudaError_t launch_web_adjoint(int n, int batch, const Fields16& th, const T* de
                                const Fields16& out, double* partial, bool bias_grad, cudaStream_t s,
                                int blocks = 0);   // blocks per chain without bias_grad (0: built-in)
 template <typename T> cudaError_t launch_shift(long long count, const T* in, T* out, T c, cudaStream_t s);
+// Radial redshift-space displacement in place (Sect. 2.9): psi += f (psi1 . r) r / |r|^2,
+// r = q + psi - (n/2)(1,1,1) in cell units; psi, psi1: 3 real fields each, [B][n^3].
+template <typename T>
+cudaError_t launch_rsd_radial(int n, int batch, const Fields16& psi, const Fields16& psi1, double f, cudaStream_t s);
 template <typename T>
 cudaError_t launch_kick_drift(int n, int batch, T* p, T* nu, const T* g, double ck, double cd, double* partial,
                               cudaStream_t s);

@@ -452,6 +452,48 @@ __device__ __forceinline__ void alpt_sources_adj(T d0, const T phi[6], T D, T D2
     gphi[5] = gs2 * (phi[0] + phi[3]);
 }
 
+// Radial redshift-space displacement (Sect. 2.9, Eq. of delta(s), b_v = 1, linear
+// velocity v/(aH) = f Psi_1): the particle of cell q at r = q + Psi - c relative
+// to the observer c at the centre of the volume moves by f (Psi_1 . r) r / |r|^2
+// (cell units; not at all when r = 0).  rsd_radial_fwd returns the shifted
+// displacement; rsd_radial_adj maps the cotangent G of the shifted displacement to
+// those of Psi and Psi_1:
+//   g_Psi = G + (f/s) [Psi_1 (r.G) + P G - (2P/s) r (r.G)],  g_Psi1 = (f/s) r (r.G),
+// with s = |r|^2, P = Psi_1 . r.
+template <typename T> struct RsdPoint {
+    T r[3], p1[3], pr, s;   // r, Psi_1, Psi_1 . r, |r|^2
+};
+template <typename T>
+__device__ __forceinline__ void rsd_radial_fwd(const int q[3], T c, const T psi[3], const T psi1[3], T f, RsdPoint<T>& R,
+                                               T out[3]) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        R.r[j] = (T(q[j]) - c) + psi[j];
+        R.p1[j] = psi1[j];
+    }
+    R.s = R.r[0] * R.r[0] + R.r[1] * R.r[1] + R.r[2] * R.r[2];
+    R.pr = psi1[0] * R.r[0] + psi1[1] * R.r[1] + psi1[2] * R.r[2];
+    const T a = R.s > T(0) ? f * R.pr / R.s : T(0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) out[j] = psi[j] + a * R.r[j];
+}
+template <typename T>
+__device__ __forceinline__ void rsd_radial_adj(const RsdPoint<T>& R, T f, const T G[3], T g_psi[3], T g_psi1[3]) {
+    if (!(R.s > T(0))) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) { g_psi[j] = G[j]; g_psi1[j] = T(0); }
+        return;
+    }
+    const T is = T(1) / R.s;
+    const T rg = R.r[0] * G[0] + R.r[1] * G[1] + R.r[2] * G[2];
+    const T fs = f * is, c2 = T(2) * R.pr * is * rg;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        g_psi[j] = G[j] + fs * (R.p1[j] * rg + R.pr * G[j] - c2 * R.r[j]);
+        g_psi1[j] = fs * rg * R.r[j];
+    }
+}
+
 // CIC geometry of the particle of cell q (cell units): lower corner and fractions.
 template <typename T> struct CicCorner {
     int i0[3];

@@ -113,7 +113,8 @@ class Config:
     seed_momentum: int = 5001
     seed_perturb: int = 6001
     nb_beta: Optional[float] = None  # global beta override (configs that fix one beta)
-    rsd_f: float = 0.0               # redshift-space displacement along z with linear velocity f (0: real space)
+    rsd_f: float = 0.0               # redshift-space displacement with linear velocity f (0: real space)
+    rsd_los: int = 0                 # line of sight: 0 plane-parallel along z, 1 radial from the box centre
 
     @property
     def dx(self) -> float:

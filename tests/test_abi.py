@@ -48,7 +48,7 @@ def test_validate_config(pkg):
     assert pkg.lib().bridge_workspace_bytes(ctypes.byref(good)) > 0
     for field, value in (("n", 48), ("n", 8), ("n", 1024), ("batch", 0), ("box", -1.0), ("n_regions", 5),
                          ("sharpness", 0.0), ("rho_floor", 0.0), ("precision", 7), ("r_s", float("nan")),
-                         ("recompute_alpt", 2)):
+                         ("recompute_alpt", 2), ("rsd_los", 2), ("rsd_los", -1), ("rsd_f", float("inf"))):
         bad = pkg.make_config(32, 300.0, pk_amp=1.0)
         setattr(bad, field, value)
         assert pkg.lib().bridge_validate_config(ctypes.byref(bad)) == pkg.BRIDGE_EINVAL, field
@@ -74,6 +74,12 @@ def test_workspace_scales_with_mesh_and_batch(pkg):
                                                                         recompute_alpt=True)))
     spec = 8 * (512 // 2 + 1) * 512 * 512
     assert abs((d - r) - 10 * spec) < 4096
+    # the radial line of sight keeps Psi_1 and its adjoint: six more half spectra (plane-parallel: none)
+    pp = pkg.lib().bridge_workspace_bytes(ctypes.byref(pkg.make_config(512, 2000.0, pk_amp=1.0, n_regions=16,
+                                                                         rsd_f=0.8)))
+    rad = pkg.lib().bridge_workspace_bytes(ctypes.byref(pkg.make_config(512, 2000.0, pk_amp=1.0, n_regions=16,
+                                                                          rsd_f=0.8, rsd_los=1)))
+    assert pp == d and abs((rad - d) - 6 * spec) < 4096
 
 
 def test_pk_amplitude_matches_oracle_quadrature(pkg):

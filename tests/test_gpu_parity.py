@@ -429,14 +429,14 @@ def test_autotune_keeps_results_and_later_calls_work(name, precision):
     ctx.close()
 
 
-@pytest.mark.parametrize("rsd_f", [0.0, 0.8])
-def test_recompute_alpt_matches_stored(rsd_f):
+@pytest.mark.parametrize("rsd_f,rsd_los", [(0.0, 0), (0.8, 0), (0.8, 1)])
+def test_recompute_alpt_matches_stored(rsd_f, rsd_los):
     """recompute_alpt (the adjoint recomputes the ALPT spectra from nu) gives the same fields and
-    gradient as the default path that keeps them, and both match the oracle, in real and in
-    redshift space."""
+    gradient as the default path that keeps them, and both match the oracle, in real space and
+    in redshift space (plane-parallel and radial line of sight)."""
     n, box, nr, seed = CASES["64_hier"]
-    cfg, bias, nu, counts, _ = make_case(n, box, nr, seed, point="eval", rsd_f=rsd_f)
-    f, lp_o, g_o, gb_o, _ = oracle_ref(f"64_hier_rsd{rsd_f}", cfg, bias, nu, counts, conditioning=False)
+    cfg, bias, nu, counts, _ = make_case(n, box, nr, seed, point="eval", rsd_f=rsd_f, rsd_los=rsd_los)
+    f, lp_o, g_o, gb_o, _ = oracle_ref(f"64_hier_rsd{rsd_f}_{rsd_los}", cfg, bias, nu, counts, conditioning=False)
     out = {}
     for rec in (False, True):
         ctx, nu_d, c_d = run_gpu(cfg, bias, nu, counts, pkg.BRIDGE_FP32, recompute_alpt=rec)
@@ -479,6 +479,39 @@ def test_redshift_space_256():
     nu, counts, _, cleared = pp.condition(nu_t, counts, cfg, bias, clear_empty=True)
     print(f"256 RSD truth: {cleared} near-empty cells cleared")
     ctx = _full_check("256_rsd", cfg, bias, nu, counts, "fp32", conditioning="fields", psi=True)[0]
+    ctx.close()
+
+
+@pytest.mark.parametrize("n,precision", [(32, "fp32"), (32, "fp64"), (64, "fp32"), (64, "fp64")])
+def test_radial_redshift_space_against_oracle(n, precision):
+    """Sect. 2.9 with the observer at the centre of the volume (radial line of sight, f = 0.8):
+    counts drawn from the radial redshift-space model; every field (the displacement is the
+    redshift-space one), the log posterior and the gradient (through the transposed per-particle
+    projection and the linear displacement's k-space adjoint) against the oracle at the fixed
+    bounds.  The displacement differs from the plane-parallel one in every component."""
+    box, nr = {32: (300.0, 4), 64: (500.0, 16)}[n]
+    cfg, bias, nu, counts, _ = make_case(n, box, nr, 1950 + n, point="eval", rsd_f=0.8, rsd_los=1)
+    ctx, nu_d, c_d, _, _ = _full_check(f"rsd_radial_{n}", cfg, bias, nu, counts, precision)
+    plane = synth.Config("plane", n, box, n_regions=nr, rsd_f=0.8)
+    psi_pp = model.alpt_displacement(model.delta0_from_nu(torch.tensor(nu), plane), plane).numpy()
+    psi = ctx.bridge_debug_field(nu_d, c_d, [bias], pkg.FIELD_PSI).double().cpu().numpy().reshape(psi_pp.shape)
+    diff = [rel_l2(psi[j], psi_pp[j]) for j in range(3)]
+    print("radial vs plane-parallel displacement, per component: " + ", ".join(f"{d:.2e}" for d in diff))
+    assert min(diff) > 0.05
+    ctx.close()
+
+
+def test_radial_redshift_space_256():
+    """The 256^3 workload with the radial line of sight (f = 0.8), FP32, at the data-consistent
+    point: fields, log posterior and gradient (tolerances as for the real-space workload)."""
+    cfg = synth.config(2)
+    cfg.rsd_f, cfg.rsd_los = 0.8, 1
+    bias = synth.default_bias(cfg)
+    nu_t = synth.white_noise(cfg.n, cfg.seed_truth)
+    counts = mock.mock_counts(nu_t, cfg, bias, cfg.seed_counts)
+    nu, counts, _, cleared = pp.condition(nu_t, counts, cfg, bias, clear_empty=True)
+    print(f"256 radial RSD truth: {cleared} near-empty cells cleared")
+    ctx = _full_check("256_rsd_radial", cfg, bias, nu, counts, "fp32", conditioning="fields", psi=True)[0]
     ctx.close()
 
 

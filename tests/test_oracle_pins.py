@@ -280,6 +280,62 @@ def test_rsd_plane_parallel_closed_forms():
                                model.alpt_displacement(torch.tensor(dx_only), off).numpy(), atol=1e-14)
 
 
+def test_rsd_radial_equals_plane_parallel_on_the_axis():
+    """Radial line of sight (observer at the centre c = n/2 of the volume, Sect. 2.9): for a plane
+    wave along z the displacement is along z everywhere, so on the line x = y = c through the
+    observer the line of sight is z itself and the radial redshift-space displacement equals the
+    plane-parallel one; off that line it gains x and y components."""
+    f, n, box = 0.8, 16, 100.0
+    dx = box / n
+    X, Y, Z = _mesh(n)
+    d0 = torch.tensor(0.2 * np.cos(2 * math.pi * 3 / box * Z * dx))
+    pp = model.alpt_displacement(d0, small_cfg(n=n, box=box, r_s=0.0, growth_d=1.0, rsd_f=f)).numpy()
+    rad = model.alpt_displacement(d0, small_cfg(n=n, box=box, r_s=0.0, growth_d=1.0, rsd_f=f, rsd_los=1)).numpy()
+    axis = (X == n // 2) & (Y == n // 2)
+    np.testing.assert_allclose(rad[:, axis], pp[:, axis], atol=1e-12)
+    assert np.abs(rad[0][~axis]).max() > 1e-2 and np.abs(rad[1][~axis]).max() > 1e-2
+
+
+def test_rsd_radial_closed_form_two_waves():
+    """Two orthogonal waves along x and z, pure 2LPT (r_s = 0): the real-space displacement Psi is
+    the closed form of the 2LPT pin and the linear one Psi_1 its Zel'dovich part.  Each particle
+    sits at r = q + Psi - c relative to the observer (c = n/2; the Eulerian, not the Lagrangian,
+    position) and moves by f (Psi_1 . r) r / |r|^2 -- the linear velocity, not the full 2LPT
+    displacement, projected on its own line of sight."""
+    f, n, box = 0.8, 16, 100.0
+    cfg = small_cfg(n=n, box=box, r_s=0.0, growth_d=1.0, rsd_f=f, rsd_los=1)
+    dx = box / n
+    X, Y, Z = _mesh(n)
+    k1, k3 = 2 * math.pi * 2 / box, 2 * math.pi * 3 / box
+    A1, A3 = 0.3, 0.2
+    x, z = X * dx, Z * dx
+    d0 = A1 * np.cos(k1 * x) + A3 * np.cos(k3 * z)
+    D2 = -3.0 / 7.0
+    z1x, z1z = -A1 * np.sin(k1 * x) / k1 / dx, -A3 * np.sin(k3 * z) / k3 / dx    # Zel'dovich, cells
+    psi = np.stack([z1x + D2 * A1 * A3 * k1 * np.sin(k1 * x) * np.cos(k3 * z) / (k1 ** 2 + k3 ** 2) / dx,
+                    np.zeros_like(x),
+                    z1z + D2 * A1 * A3 * k3 * np.cos(k1 * x) * np.sin(k3 * z) / (k1 ** 2 + k3 ** 2) / dx])
+    r = np.stack([X, Y, Z]) + psi - n / 2
+    r2 = (r * r).sum(0)
+    centre = r2 < 1e-20   # the particle at the observer (Psi vanishes there): not moved
+    proj = np.where(centre, 0.0, (z1x * r[0] + z1z * r[2]) / np.where(centre, 1.0, r2))
+    expect = psi + f * proj * r
+    got = model.alpt_displacement(torch.tensor(d0), cfg).numpy()
+    np.testing.assert_allclose(got, expect, atol=1e-11)
+
+
+def test_rsd_radial_is_linear_in_f_and_conserves_mass():
+    """The radial shift is linear in f (Psi(2f) - Psi(0) = 2 (Psi(f) - Psi(0))) for a random field
+    with the ALPT blend on, and the CIC mass of the redshift-space positions is N^3."""
+    d0 = model.delta0_from_nu(torch.tensor(synth.white_noise(16, 31)), small_cfg(n=16, box=160.0, growth_d=1.0))
+    p = [model.alpt_displacement(d0, small_cfg(n=16, box=160.0, growth_d=1.0, rsd_f=f, rsd_los=1)).numpy()
+         for f in (0.0, 0.5, 1.0)]
+    np.testing.assert_allclose(p[2] - p[0], 2 * (p[1] - p[0]), atol=1e-12)
+    assert np.abs(p[1] - p[0]).max() > 1e-2
+    rho = model.cic_delta(torch.tensor(p[1])) + 1.0
+    assert abs(float(rho.sum()) - 16 ** 3) < 1e-9
+
+
 def test_rsd_only_moves_the_line_of_sight_component():
     """A random field with the ALPT blend on: RSD leaves Psi_x, Psi_y unchanged and adds to Psi_z a
     term linear in f (Psi_z(2f) - Psi_z(0) = 2 (Psi_z(f) - Psi_z(0))), which is curl-free with
@@ -627,9 +683,9 @@ def test_flat_likelihood_gradient_is_minus_nu():
 # ---------------------------------------------------------------------------
 # gradients: autograd vs central finite differences
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("n_regions", [4, 16])
-def test_gradient_matches_central_fd(n_regions):
-    cfg = small_cfg(n=8, box=60.0, n_regions=n_regions)
+@pytest.mark.parametrize("n_regions,rsd_f,rsd_los", [(4, 0.0, 0), (16, 0.0, 0), (16, 0.8, 1)])
+def test_gradient_matches_central_fd(n_regions, rsd_f, rsd_los):
+    cfg = small_cfg(n=8, box=60.0, n_regions=n_regions, rsd_f=rsd_f, rsd_los=rsd_los)
     bias = synth.default_bias(cfg)
     nu_t = synth.white_noise(8, 21)
     counts = mock.mock_counts(nu_t, cfg, bias, 22)
