@@ -374,7 +374,8 @@ def run_ours(args):
 def run_extras(pkg, synth, cfg, bias, nu32, counts, args):
     """Comparators reported beside the headline: FP64 plain path, HMC dH at several step sizes,
     batched FP32 chains against single FP64 chains at equal dH accuracy, a cuFFT cross-check of
-    the FFT passes, stored vs recomputed ALPT fields, batched and 512^3 throughput."""
+    the FFT passes, stored vs recomputed ALPT fields, batched and 512^3 throughput, and redshift
+    space with both lines of sight."""
     import numpy as np
     import torch
     out = {}
@@ -606,7 +607,7 @@ def run_extras(pkg, synth, cfg, bias, nu32, counts, args):
     del ctx5, g5
     # redshift space (Sect. 2.9, f = 0.8): plane-parallel and radial line of sight, 256^3 and 512^3
     rsd = {}
-    for label, cbase, bx, nux, cnx in (("256", cfg, bias, nu, counts), ("512", c5, b5, nu5, cn5)):
+    for label, cbase, bx, nux, cnx in (("256", cfg, bias, nu32, counts), ("512", c5, b5, nu5, cn5)):
         for los, name in ((0, "plane_parallel"), (1, "radial")):
             cr = copy.copy(cbase)
             cr.rsd_f, cr.rsd_los = 0.8, los

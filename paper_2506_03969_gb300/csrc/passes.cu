@@ -69,13 +69,16 @@ __device__ __forceinline__ cplx_t<T> ymult(const Term& tm, int my, int mz, int n
 // (XM = true, lines contiguous).  Spectra are [kz][ky or y][x] with N*N
 // elements per kz plane and N/2+1 planes.
 // ---------------------------------------------------------------------------
+#ifndef BRIDGE_XNODE_T32
+#define BRIDGE_XNODE_T32 256   // threads of an FP32 x-node CTA (its tile: BRIDGE_XNODE_T32 / N2 lines)
+#endif
 template <typename T, int N, bool XM> struct Tile {
     using V = cplx_t<T>;
     static constexpr int N1 = Split<N>::N1, N2 = Split<N>::N2, J = N1 / N2;
     // FP64 at N = 512: 8 columns, so that the forward pass's tile and its staged copy fit in shared memory
     static constexpr int GY0 = (sizeof(V) == 16 && N >= 512) ? 8
                                : ((int)(128 / sizeof(V)) > 256 / N2 ? (int)(128 / sizeof(V)) : 256 / N2);
-    static constexpr int GX0 = (sizeof(V) == 8 ? 256 : 128) / N2;
+    static constexpr int GX0 = (sizeof(V) == 8 ? BRIDGE_XNODE_T32 : 128) / N2;
     static constexpr int G0 = XM ? GX0 : GY0;
     static constexpr int G = G0 < N ? G0 : N;
     static constexpr int NT = G * N2;
@@ -491,8 +494,12 @@ __device__ __forceinline__ cplx_t<T> xmult(const XTerm<T>& x, int mx, int ix, in
 #ifndef BRIDGE_XNODE_MINB
 #define BRIDGE_XNODE_MINB 2
 #endif
+// FP32: as many CTAs per SM as fit 2 x 256 threads (the register budget of 128 per thread)
+template <typename T, int N> constexpr int xnode_minb() {
+    return sizeof(T) == 4 ? BRIDGE_XNODE_MINB * 256 / Tile<T, N, true>::NT : BRIDGE_XNODE_MINB;
+}
 template <typename T, int N>
-__global__ void __launch_bounds__(Tile<T, N, true>::NT, BRIDGE_XNODE_MINB) k_x_node(const PassProgram P, const KParams kp) {
+__global__ void __launch_bounds__(Tile<T, N, true>::NT, (xnode_minb<T, N>())) k_x_node(const PassProgram P, const KParams kp) {
     using TL = Tile<T, N, true>;
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
