@@ -120,12 +120,15 @@ def integrate_joint(nu0, p0, theta0, ptheta0, counts, cfg, bias, n_steps: int, e
     return nu, p, th, pt, h0, h1
 
 
-def nuts_step(nu0, p0, counts, cfg, bias, eps: float, rng, max_depth: int = 10, grad_fn=None, delta_max: float = 1000.0):
+def nuts_step(nu0, p0, counts, cfg, bias, eps: float, rng, max_depth: int = 10, grad_fn=None, delta_max: float = 1000.0,
+              with_accept: bool = False):
     """One No-U-Turn transition (Hoffman & Gelman 2014, efficient NUTS with a slice variable) from
     nu0 with momentum p0.  Uniform draws from rng, in the order: slice level; then per doubling
     the direction, the subtree's proposal choices (taken only when the subtree has an admissible
     point) and the doubling's own proposal choice (taken only when the subtree did not stop).
-    Returns (sample, depth, leapfrog steps)."""
+    Returns (sample, depth, leapfrog steps), and with with_accept also the acceptance statistic
+    of the last doubling's subtree: the mean over its states of min(1, exp(E - E0)), E the log
+    joint density (their step-size adaptation statistic)."""
     if grad_fn is None:
         def grad_fn(x):
             lp, g, _, _ = model.logpost_and_grad(x, counts, cfg, bias)
@@ -148,12 +151,16 @@ def nuts_step(nu0, p0, counts, cfg, bias, eps: float, rng, max_depth: int = 10, 
         d = plus[0] - minus[0]
         return float((d * minus[1]).sum()) < 0.0 or float((d * plus[1]).sum()) < 0.0
 
+    acc = [0.0, 0]   # acceptance statistic of the subtree being built: sum, count
+
     def build(state, log_u, v, j):
         if j == 0:
             t = leap(state, v)
             e = joint(t)
             if not np.isfinite(e):
                 e = -np.inf
+            acc[0] += 0.0 if e == -np.inf else min(1.0, math.exp(min(0.0, e - e0)))
+            acc[1] += 1
             return t, t, t, int(log_u <= e), bool(log_u < e + delta_max)
         minus, plus, prop, n1, ok = build(state, log_u, v, j - 1)
         if ok:
@@ -169,11 +176,13 @@ def nuts_step(nu0, p0, counts, cfg, bias, eps: float, rng, max_depth: int = 10, 
 
     lp0, g0 = grad_fn(np.asarray(nu0, dtype=np.float64))
     s0 = (np.asarray(nu0, dtype=np.float64), np.asarray(p0, dtype=np.float64), lp0, g0)
-    log_u = joint(s0) + math.log(rng.random())
+    e0 = joint(s0)
+    log_u = e0 + math.log(rng.random())
     minus = plus = sample = s0
     n, depth, ok = 1, 0, True
     while ok and depth < max_depth:
         v = -1 if rng.random() < 0.5 else 1
+        acc[0], acc[1] = 0.0, 0
         if v < 0:
             minus, _, prop, n2, ok2 = build(minus, log_u, v, depth)
         else:
@@ -183,4 +192,39 @@ def nuts_step(nu0, p0, counts, cfg, bias, eps: float, rng, max_depth: int = 10, 
         n += n2
         ok = ok2 and not turning(minus, plus)
         depth += 1
+    if with_accept:
+        return sample[0], depth, steps[0], acc[0] / acc[1]
     return sample[0], depth, steps[0]
+
+
+class DualAveraging:
+    """Step-size adaptation of Hoffman & Gelman (2014, Sect. 3.2, dual averaging after Nesterov
+    2009): after transition m (1-based) with acceptance statistic a_m,
+        Hbar_m = (1 - 1/(m + t0)) Hbar_{m-1} + (delta - a_m) / (m + t0),
+        log eps_m = mu - sqrt(m) / gamma * Hbar_m,  mu = log(10 eps_0),
+        log epsbar_m = m^-kappa log eps_m + (1 - m^-kappa) log epsbar_{m-1},  epsbar_0 = 1,
+    eps_m is used for the next transition and epsbar after the adaptation phase.  Defaults are
+    theirs: delta = 0.8 (the paper does not state its target), gamma = 0.05, t0 = 10,
+    kappa = 0.75."""
+
+    def __init__(self, eps0: float, delta: float = 0.8, gamma: float = 0.05, t0: float = 10.0,
+                 kappa: float = 0.75):
+        self.mu = math.log(10.0 * eps0)
+        self.delta, self.gamma, self.t0, self.kappa = delta, gamma, t0, kappa
+        self.m, self.hbar, self.log_epsbar = 0, 0.0, 0.0
+        self.eps = eps0
+
+    def update(self, accept_stat: float) -> float:
+        self.m += 1
+        m = self.m
+        w = 1.0 / (m + self.t0)
+        self.hbar = (1.0 - w) * self.hbar + w * (self.delta - accept_stat)
+        log_eps = self.mu - math.sqrt(m) / self.gamma * self.hbar
+        eta = m ** (-self.kappa)
+        self.log_epsbar = eta * log_eps + (1.0 - eta) * self.log_epsbar
+        self.eps = math.exp(log_eps)
+        return self.eps
+
+    @property
+    def final_eps(self) -> float:
+        return math.exp(self.log_epsbar)

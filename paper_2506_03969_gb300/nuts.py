@@ -12,6 +12,9 @@ Random draws (slice level, directions, proposal choices) come from the caller's
 ``numpy.random.Generator`` in the order the algorithm consumes them, so a run is
 reproducible from its seed; the momentum is drawn by the caller.  One chain per
 context (batch 1): each chain grows its own tree.
+
+Step-size adaptation (``StepSizeAdaptation``) is their dual-averaging scheme
+(Sect. 3.2 of the same paper), fed with each transition's acceptance statistic.
 """
 from __future__ import annotations
 
@@ -43,6 +46,7 @@ class NutsResult:
     depth: int            # tree depth reached
     n_leapfrog: int       # leapfrog steps taken (gradient evaluations)
     diverged: bool
+    accept_stat: float    # mean of min(1, exp(E - E0)) over the last doubling's states
 
 
 class NUTS:
@@ -55,6 +59,7 @@ class NUTS:
         self.eps, self.max_depth = float(eps), int(max_depth)
         self.n_leapfrog = 0
         self.diverged = False
+        self._acc_sum, self._acc_n, self._e0 = 0.0, 0, 0.0
 
     def _dot(self, a, b) -> float:
         return float(self.ctx.bridge_dot(a, b)[0])
@@ -83,6 +88,8 @@ class NUTS:
             e = self._energy(t)
             if not math.isfinite(e):
                 e = -math.inf
+            self._acc_sum += 0.0 if e == -math.inf else math.exp(min(0.0, e - self._e0))
+            self._acc_n += 1
             n_ok = 1 if log_u <= e else 0
             ok = log_u < e + DELTA_MAX
             if not ok:
@@ -106,11 +113,13 @@ class NUTS:
         self.n_leapfrog = 0
         self.diverged = False
         s0 = _State(nu.clone(), p.clone(), grad.clone(), float(logpost))
-        log_u = self._energy(s0) + math.log(rng.random())
+        self._e0 = self._energy(s0)
+        log_u = self._e0 + math.log(rng.random())
         minus, plus, sample = s0, s0, s0
         n, depth, ok = 1, 0, True
         while ok and depth < self.max_depth:
             direction = -1 if rng.random() < 0.5 else 1
+            self._acc_sum, self._acc_n = 0.0, 0
             if direction < 0:
                 minus, _, prop, n2, ok2 = self._build(minus, log_u, direction, depth, rng)
             else:
@@ -120,4 +129,36 @@ class NUTS:
             n += n2
             ok = ok2 and self._no_uturn(minus, plus)
             depth += 1
-        return NutsResult(sample.nu, sample.lp, sample.g, depth, self.n_leapfrog, self.diverged)
+        return NutsResult(sample.nu, sample.lp, sample.g, depth, self.n_leapfrog, self.diverged,
+                          self._acc_sum / max(self._acc_n, 1))
+
+
+class StepSizeAdaptation:
+    """Dual averaging of the log step size towards a target acceptance statistic (Hoffman &
+    Gelman 2014, Sect. 3.2): with w = 1/(m + t0) after transition m,
+    H <- (1 - w) H + w (target - a_m); log eps = log(10 eps0) - sqrt(m) H / gamma; the running
+    average log eps_bar <- m^-kappa log eps + (1 - m^-kappa) log eps_bar is the step to keep once
+    adaptation ends.  Defaults as theirs (target 0.8, gamma 0.05, t0 10, kappa 0.75)."""
+
+    def __init__(self, eps0: float, target: float = 0.8, gamma: float = 0.05, t0: float = 10.0,
+                 kappa: float = 0.75):
+        self.anchor = math.log(10.0 * float(eps0))
+        self.target, self.gamma, self.t0, self.kappa = target, gamma, t0, kappa
+        self.count, self.h, self.log_avg = 0, 0.0, 0.0
+        self.eps = float(eps0)
+
+    def update(self, accept_stat: float) -> float:
+        """Record one transition's acceptance statistic; returns the step for the next one."""
+        self.count += 1
+        w = 1.0 / (self.count + self.t0)
+        self.h += w * ((self.target - accept_stat) - self.h)
+        log_eps = self.anchor - math.sqrt(self.count) * self.h / self.gamma
+        weight = self.count ** -self.kappa
+        self.log_avg += weight * (log_eps - self.log_avg)
+        self.eps = math.exp(log_eps)
+        return self.eps
+
+    @property
+    def adapted_eps(self) -> float:
+        """The averaged step to use after adaptation."""
+        return math.exp(self.log_avg)

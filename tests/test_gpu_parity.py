@@ -982,13 +982,15 @@ def test_nuts_host_driver_matches_oracle():
         rng_o, rng_g = np.random.default_rng(7 + t), np.random.default_rng(7 + t)
         x_g = torch.tensor(x_o, dtype=torch.float64, device="cuda").contiguous()
         lp, g, _ = ctx.bridge_logpost_grad(x_g, c_d, [bias], want_bias_grad=False)
-        x_new, depth_o, steps_o = hmc.nuts_step(x_o, moms[t], counts, cfg, bias, 0.05, rng_o, max_depth=5)
+        x_new, depth_o, steps_o, acc_o = hmc.nuts_step(x_o, moms[t], counts, cfg, bias, 0.05, rng_o, max_depth=5,
+                                                       with_accept=True)
         p_d = torch.tensor(moms[t], dtype=torch.float64, device="cuda").contiguous()
         res = sampler.step(x_g, p_d, g, float(lp[0]), rng_g)
         e = rel_l2(res.nu.cpu().numpy(), x_new)
         print(f"NUTS transition {t}: depth {res.depth} / {depth_o}, leapfrog steps {res.n_leapfrog} / {steps_o}, "
-              f"sample rel L2 {e:.2e}")
+              f"sample rel L2 {e:.2e}, acceptance statistic {res.accept_stat:.6f} / {acc_o:.6f}")
         assert res.depth == depth_o and res.n_leapfrog == steps_o and e <= 1e-8
+        assert abs(res.accept_stat - acc_o) <= 1e-5
         x_o = x_new
     ctx.close()
     c32, nu32, c_d = run_gpu(cfg, bias, nu, counts, pkg.BRIDGE_FP32)

@@ -856,6 +856,67 @@ def test_nuts_leaves_a_gaussian_invariant():
     assert max(depths) < 8
 
 
+def test_nuts_acceptance_statistic_one_step_closed_form():
+    """With max_depth = 1 the only subtree is one leapfrog step, so the acceptance statistic is
+    min(1, exp(-dH)) of that step; for the standard normal target the step and its energy error
+    follow by hand: x1 = x + v eps (p - v eps x / 2), p1 = p - v eps (x + x1) / 2."""
+    grad = lambda x: (-0.5 * float((x ** 2).sum()), -x)
+    for seed, eps in ((3, 0.4), (4, 1.3), (5, 1.9)):
+        x0 = np.array([0.7, -1.2])
+        p0 = np.array([0.3, 0.9])
+        rng = np.random.default_rng(seed)
+        _, depth, steps, stat = hmc.nuts_step(x0, p0, None, None, None, eps, rng, max_depth=1, grad_fn=grad,
+                                              with_accept=True)
+        r2 = np.random.default_rng(seed)
+        r2.random()
+        v = -1.0 if r2.random() < 0.5 else 1.0
+        x1 = x0 + v * eps * (p0 - 0.5 * v * eps * x0)
+        p1 = p0 - 0.5 * v * eps * (x0 + x1)
+        dH = 0.5 * float((x1 ** 2 + p1 ** 2).sum()) - 0.5 * float((x0 ** 2 + p0 ** 2).sum())
+        assert depth == 1 and steps == 1
+        assert abs(stat - min(1.0, math.exp(-dH))) < 1e-14, (stat, dH)
+
+
+def test_dual_averaging_fixed_point_and_direction():
+    """Dual averaging (Hoffman & Gelman 2014, Sect. 3.2): an acceptance statistic equal to the
+    target leaves the step at its anchor 10 eps0 for good; statistics above the target grow the
+    step, below it shrink it."""
+    da = hmc.DualAveraging(0.05)
+    for _ in range(20):
+        e = da.update(0.8)
+        assert abs(e - 0.5) < 1e-14
+    assert abs(da.final_eps - 0.5) < 1e-14
+    up, down = hmc.DualAveraging(0.05), hmc.DualAveraging(0.05)
+    eu = [up.update(0.99) for _ in range(5)]
+    ed = [down.update(0.3) for _ in range(5)]
+    assert all(a > 0.5 for a in eu) and all(b < 0.5 for b in ed)
+    assert eu[-1] > eu[0] and ed[-1] < ed[0]
+
+
+def test_nuts_step_size_adaptation_reaches_the_target():
+    """NUTS with dual averaging on a 50-dimensional standard normal from a far too small step:
+    after 150 adaptation transitions the averaged step gives a mean acceptance statistic near the
+    target 0.8 over 150 further transitions, and the step lands in the range where leapfrog on a
+    unit Gaussian accepts that often (about 0.5-1.5)."""
+    grad = lambda x: (-0.5 * float((x ** 2).sum()), -x)
+    rng = np.random.default_rng(71)
+    x = rng.standard_normal(50)
+    da = hmc.DualAveraging(0.01)
+    eps = 0.01
+    for _ in range(150):
+        x, _, _, a = hmc.nuts_step(x, rng.standard_normal(50), None, None, None, eps, rng, max_depth=8,
+                                   grad_fn=grad, with_accept=True)
+        eps = da.update(a)
+    eps = da.final_eps
+    stats = []
+    for _ in range(150):
+        x, _, _, a = hmc.nuts_step(x, rng.standard_normal(50), None, None, None, eps, rng, max_depth=8,
+                                   grad_fn=grad, with_accept=True)
+        stats.append(a)
+    print(f"adapted eps {eps:.3f}, mean acceptance {np.mean(stats):.3f}")
+    assert 0.5 < eps < 1.5 and 0.7 < np.mean(stats) < 0.9
+
+
 def test_displacement_shift_hook_moves_particles():
     """The conditioning hook adds a displacement (cells) before the mass assignment: a uniform
     shift by one cell along x rolls the density by one cell (CIC permutation invariance), and a
