@@ -179,8 +179,12 @@ int bridge_logpost_grad(bridge_ctx* ctx, const void* nu, const int32_t* counts, 
 
 /* The same evaluation with HOST buffers: nu_host, counts_host and
  * grad_nu_host are host arrays of the shapes above (pinned memory gives
- * asynchronous copies).  The call copies the inputs to the device, evaluates,
- * copies the gradient back and synchronises. */
+ * asynchronous copies).  The call copies nu to device staging buffers owned by
+ * the context (allocated on the first call), then copies and prepares the
+ * counts on a second stream while the forward fields, which do not need them,
+ * run; copies the gradient back and synchronises.  The host buffers must stay
+ * valid and unchanged until the call returns; on an error no copy into them is
+ * left in flight. */
 int bridge_logpost_grad_host(bridge_ctx* ctx, const void* nu_host, const int32_t* counts_host,
                              const bridge_bias* bias, double* logpost_out, void* grad_nu_host,
                              double* grad_bias_out);

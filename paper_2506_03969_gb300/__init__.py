@@ -279,13 +279,18 @@ class Context:
                                              bias_array(biases), cot, ctypes.c_void_p(_ptr(g)), gb))
         return g, (np.array(gb[:]).reshape(self.batch, nf) if gb is not None else None)
 
-    def bridge_logpost_grad_host(self, nu_host, counts_host, biases, grad_host):
-        """Host (ideally pinned) torch CPU tensors in and out; copies are part of the call."""
+    def bridge_logpost_grad_host(self, nu_host, counts_host, biases, grad_host, want_bias_grad: bool = False):
+        """Host (ideally pinned) torch CPU tensors in and out; copies are part of the call.
+        Returns the log posterior [B], and with want_bias_grad also the free bias gradient."""
         lp = (ctypes.c_double * self.batch)()
+        nf = n_free(biases)
+        gb = (ctypes.c_double * (self.batch * nf))() if want_bias_grad and nf > 0 else None
         self._check(lib().bridge_logpost_grad_host(self.handle, ctypes.c_void_p(nu_host.data_ptr()),
                                                    ctypes.c_void_p(counts_host.data_ptr()), bias_array(biases), lp,
-                                                   ctypes.c_void_p(grad_host.data_ptr()), None))
-        return np.array(lp[:])
+                                                   ctypes.c_void_p(grad_host.data_ptr()), gb))
+        if not want_bias_grad:
+            return np.array(lp[:])
+        return np.array(lp[:]), (np.array(gb[:]).reshape(self.batch, nf) if gb is not None else None)
 
     def bridge_leapfrog(self, nu, p, counts, biases, n_steps: int, eps: float):
         """Leapfrog trajectory in place; returns (H0 [B], H1 [B]).  A chain whose H0 or H1 is not

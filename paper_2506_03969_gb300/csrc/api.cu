@@ -115,6 +115,14 @@ struct bridge_ctx {
     uint32_t gjoint = 0;            // free_mask of a captured joint step (0: fields only)
     int64_t glaunches = 0;
     cudaEvent_t gev[2] = {nullptr, nullptr};
+    // host-buffer evaluation: the counts are copied and prepared on cstream while the two
+    // graphs (forward fields; likelihood + adjoint) run on gstream
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t hev[2] = {nullptr, nullptr};
+    cudaGraphExec_t hexec[2] = {nullptr, nullptr};
+    int64_t hlaunches[2] = {0, 0};
+    int hkey = -1;                  // bias_grad of the captured second graph
+    const int32_t* hcounts = nullptr;   // set by bridge_logpost_grad_host for one call
     // per-launch CUDA-event profiling (bridge_profile_enable)
     bool prof = false;
     struct ProfRec { const char* name; double bytes; cudaEvent_t a, b; };
@@ -453,7 +461,9 @@ template <typename T> int psi_real(bridge_ctx* ctx, int first) {
 // (unless recompute_alpt), rho, the tensors in real space, ln f and beta_i,
 // and the scalars (ntr, sumf, lnC, loglik, G, logpost).  nu: device [B][N^3].
 // ---------------------------------------------------------------------------
-template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelihood) {
+// run_forward_fields: every step up to the tensors in real space (needs no counts);
+// run_forward_lik: the web/bias pass and the likelihood (needs the counts prepared).
+template <typename T> int run_forward_fields(bridge_ctx* ctx, const T* nu) {
     const double invn3 = 1.0 / double(ctx->nvox);
     const bool hier = ctx->nr == 16;
     const int nth = nth_of(ctx);
@@ -493,8 +503,13 @@ template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelih
         }
         CKL("y_inv", (p.n_in + p.n_out) * sby<T>(ctx), launch_y_inv<T>(ctx->n, ctx->B, p, ctx->kp, ctx->stream));
     }
-    // tensors to real space, fused eigenvalue / web / bias pass, normalisation
+    // tensors to real space
     RUN(z_inv<T>(ctx, cspec<T>(ctx, SP_TH, nth), mreal(ctx, RB_TH, nth)));
+    return BRIDGE_OK;
+}
+template <typename T> int run_forward_lik(bridge_ctx* ctx, const T* nu, bool likelihood) {
+    const int nth = nth_of(ctx);
+    // fused eigenvalue / web / bias pass, normalisation
     CKL("web_bias", (nth + 3) * rby<T>(ctx), launch_pass_a<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 12), RB<T>(ctx, RB_DELTA), RB<T>(ctx, RB_LNF),
                         RB<T>(ctx, RB_LNF + 1), reinterpret_cast<const BiasT<T>*>(ctx->biast), ctx->wp, ctx->partial,
                         red_args(ctx), ctx->stream));   // sum f and ln C reduced by the last block
@@ -503,6 +518,10 @@ template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelih
                             ctx->partial, red_args(ctx), ctx->stream));   // log posterior reduced by the last block
     }
     return BRIDGE_OK;
+}
+template <typename T> int run_forward(bridge_ctx* ctx, const T* nu, bool likelihood) {
+    RUN(run_forward_fields<T>(ctx, nu));
+    return run_forward_lik<T>(ctx, nu, likelihood);
 }
 
 // ---------------------------------------------------------------------------
@@ -735,6 +754,74 @@ int ensure_graph_stream(bridge_ctx* ctx) {
 
 // The whole evaluation (counts preparation, forward, adjoint) replayed from a
 // CUDA graph captured on a private stream; re-captured when the buffers change.
+// Capture body() (which launches on ctx->stream) into *exec on the private stream.
+template <typename F> int capture_exec(bridge_ctx* ctx, cudaGraphExec_t* exec, int64_t* nlaunch, F body) {
+    cudaStream_t user = ctx->stream;
+    const int64_t launches = ctx->launches;
+    ctx->stream = ctx->gstream;
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeRelaxed));
+    const int st = body();
+    const cudaError_t ce = cudaStreamEndCapture(ctx->gstream, &graph);
+    *nlaunch = ctx->launches - launches;
+    ctx->stream = user;
+    ctx->launches = launches;
+    if (st != BRIDGE_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (ce != cudaSuccess) return fail(ctx, BRIDGE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    const cudaError_t ie = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) { *exec = nullptr; return fail(ctx, BRIDGE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie)); }
+    return BRIDGE_OK;
+}
+
+// Evaluation on the context's device staging buffers with the inputs in host memory
+// (bridge_logpost_grad_host): nu is copied in on the caller's stream; the counts are
+// copied and prepared on a second stream while the forward fields, which do not need
+// them, run; the web/bias pass waits for both.  The gradient is copied out last.
+template <typename T> int host_eval(bridge_ctx* ctx, const void* nu_host, T* grad_host, bool bias_grad) {
+    RUN(ensure_graph_stream(ctx));
+    if (!ctx->cstream) {
+        CK(cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking));
+        for (auto& e : ctx->hev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    const T* nu = reinterpret_cast<const T*>(ctx->h_nu);
+    T* g = reinterpret_cast<T*>(ctx->h_grad);
+    if (!ctx->hexec[0]) RUN(capture_exec(ctx, &ctx->hexec[0], &ctx->hlaunches[0], [&] { return run_forward_fields<T>(ctx, nu); }));
+    if (!ctx->hexec[1] || ctx->hkey != int(bias_grad)) {
+        if (ctx->hexec[1]) { cudaGraphExecDestroy(ctx->hexec[1]); ctx->hexec[1] = nullptr; }
+        RUN(capture_exec(ctx, &ctx->hexec[1], &ctx->hlaunches[1], [&] {
+            RUN(run_forward_lik<T>(ctx, nu, true));
+            return run_adjoint<T>(ctx, nu, g, bias_grad);
+        }));
+        ctx->hkey = int(bias_grad);
+    }
+    const size_t fb = size_t(ctx->nvox) * ctx->B * sizeof(T), cb = size_t(ctx->nvox) * ctx->B * sizeof(int32_t);
+    // nu first (the forward fields need it): both copies share the host link, so the counts
+    // follow it, on the second stream, and overlap the forward fields instead
+    CK(cudaMemcpyAsync(ctx->h_nu, nu_host, fb, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaEventRecord(ctx->hev[0], ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->cstream, ctx->hev[0], 0));
+    CK(cudaMemcpyAsync(ctx->h_counts, ctx->hcounts, cb, cudaMemcpyHostToDevice, ctx->cstream));
+    {
+        cudaStream_t user = ctx->stream;
+        ctx->stream = ctx->cstream;
+        const int st = prep_counts<T>(ctx, ctx->h_counts);
+        ctx->stream = user;
+        RUN(st);
+    }
+    CK(cudaEventRecord(ctx->hev[1], ctx->cstream));
+    // the two halves of the evaluation, joined before the web/bias pass
+    CK(cudaStreamWaitEvent(ctx->gstream, ctx->hev[0], 0));
+    CK(cudaGraphLaunch(ctx->hexec[0], ctx->gstream));
+    CK(cudaStreamWaitEvent(ctx->gstream, ctx->hev[1], 0));
+    CK(cudaGraphLaunch(ctx->hexec[1], ctx->gstream));
+    CK(cudaEventRecord(ctx->gev[1], ctx->gstream));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->gev[1], 0));
+    CK(cudaMemcpyAsync(grad_host, g, fb, cudaMemcpyDeviceToHost, ctx->stream));
+    ctx->launches += ctx->hlaunches[0] + ctx->hlaunches[1];
+    return BRIDGE_OK;
+}
+
 template <typename T> int eval_graph(bridge_ctx* ctx, const T* nu, const int32_t* counts, T* grad, bool bias_grad) {
     RUN(ensure_graph_stream(ctx));
     const void* key[4] = {nu, counts, grad, bias_grad ? ctx : nullptr};
@@ -796,7 +883,8 @@ template <typename T> int do_grad(bridge_ctx* ctx, const void* nu, const int32_t
     const T* nuT = reinterpret_cast<const T*>(nu);
     T* gT = reinterpret_cast<T*>(grad);
     const bool want_bias = gbias_out != nullptr && bias[0].free_mask != 0u;
-    if (ctx->prof) RUN(eval_body<T>(ctx, nuT, counts, gT, want_bias));   // per-launch events need direct launches
+    if (ctx->hcounts) RUN(host_eval<T>(ctx, nu, gT, want_bias));        // nu, counts and grad in host memory
+    else if (ctx->prof) RUN(eval_body<T>(ctx, nuT, counts, gT, want_bias));   // per-launch events need direct launches
     else RUN(eval_graph<T>(ctx, nuT, counts, gT, want_bias));
     bool scale = false;
     if (cot) {
@@ -1239,6 +1327,9 @@ int prof_class_ms(bridge_ctx* ctx, const char* name, double* ms_out) {
 void drop_graphs(bridge_ctx* ctx) {
     if (ctx->eexec) { cudaGraphExecDestroy(ctx->eexec); ctx->eexec = nullptr; }
     if (ctx->gexec) { cudaGraphExecDestroy(ctx->gexec); ctx->gexec = nullptr; }
+    for (auto& h : ctx->hexec)
+        if (h) { cudaGraphExecDestroy(h); h = nullptr; }
+    ctx->hkey = -1;
     for (auto& k : ctx->ekey) k = nullptr;
     for (auto& k : ctx->gkey) k = nullptr;
 }
@@ -1475,8 +1566,11 @@ void bridge_destroy(bridge_ctx* ctx) {
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->eexec) cudaGraphExecDestroy(ctx->eexec);
+    for (cudaGraphExec_t h : ctx->hexec) if (h) cudaGraphExecDestroy(h);
     if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+    if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
     for (cudaEvent_t e : ctx->gev) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->hev) if (e) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -1511,6 +1605,17 @@ int bridge_logpost_grad_host(bridge_ctx* ctx, const void* nu_host, const int32_t
             cudaGetLastError();
             return fail(ctx, BRIDGE_ENOMEM, "device staging for host buffers");
         }
+    }
+    if (!ctx->prof) {
+        // overlapped: the counts are copied and prepared while the forward fields run (host_eval)
+        ctx->hcounts = counts_host;
+        const int st = DISPATCH(ctx, do_grad, nu_host, counts_host, bias, logpost_out, grad_nu_host, grad_bias_out);
+        ctx->hcounts = nullptr;
+        if (st != BRIDGE_OK) {
+            cudaStreamSynchronize(ctx->stream);   // no copy into the caller's buffers is left in flight
+            return st;
+        }
+        return BRIDGE_OK;
     }
     CK(cudaMemcpyAsync(ctx->h_nu, nu_host, fb, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_counts, counts_host, cb, cudaMemcpyHostToDevice, ctx->stream));

@@ -756,14 +756,27 @@ def test_autograd_function_against_oracle_and_fd():
         _, g1, gb1 = ctx.bridge_logpost_grad(nu_d, c_d, [bias])
         assert rel_l2(g2.cpu().numpy(), -0.5 * g1.cpu().numpy()) <= 1e-6
         assert np.max(np.abs(gb2 + 0.5 * gb1)) <= 1e-6 * np.max(np.abs(gb1))
-        if precision == "fp32":
-            # host-buffer entry point
-            nu_h = torch.tensor(nu, dtype=torch.float32).pin_memory()
-            c_h = torch.tensor(counts, dtype=torch.int32).pin_memory()
+        # host-buffer entry point (counts copied and prepared while the forward fields run):
+        # the same results as the device path, on repeated calls with new inputs, with the bias
+        # gradient, and an out-of-range count still reported
+        hdt = torch.float64 if precision == "fp64" else torch.float32
+        htol = 1e-12 if precision == "fp64" else 1e-6
+        c_h = torch.tensor(counts, dtype=torch.int32).pin_memory()
+        for k, shift in enumerate((0.0, 0.01)):
+            nu_k = nu + shift * pp.f32(synth.white_noise(32, 4100 + k))
+            nu_h = torch.tensor(nu_k, dtype=hdt).pin_memory()
             g_h = torch.empty_like(nu_h).pin_memory()
-            lp_h = ctx.bridge_logpost_grad_host(nu_h, c_h, [bias], g_h)
-            assert abs(lp_h[0] - float(lp.detach()[0])) <= 1e-7 * abs(float(lp.detach()[0]))
-            assert rel_l2(g_h.numpy(), g_full.cpu().numpy()) <= 1e-6
+            lp_h, gb_h = ctx.bridge_logpost_grad_host(nu_h, c_h, [bias], g_h, want_bias_grad=True)
+            lp_d, g_dev, gb_d = ctx.bridge_logpost_grad(nu_h.to("cuda"), c_d, [bias])
+            assert abs(lp_h[0] - lp_d[0]) <= htol * abs(lp_d[0])
+            assert rel_l2(g_h.numpy(), g_dev.cpu().numpy()) <= htol
+            assert np.max(np.abs(gb_h - gb_d)) <= htol * np.max(np.abs(gb_d))
+        bad = c_h.clone()
+        bad[0, 0, 0] = 70000
+        with pytest.raises(pkg.BridgeError) as e:
+            ctx.bridge_logpost_grad_host(nu_h, bad, [bias], g_h)
+        assert e.value.status == pkg.BRIDGE_EINVAL
+        ctx.bridge_logpost_grad_host(nu_h, c_h, [bias], g_h)
         ctx.close()
 
 
