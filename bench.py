@@ -69,11 +69,16 @@ def measured_peaks():
     return {"hbm_gbs": FALLBACK_HBM}, "fallback"
 
 
-def csrc_hash() -> str:
+def csrc_hash(files=None) -> str:
+    """sha1 (first 12 hex digits) over the CUDA sources: every file under csrc, or the listed
+    ones (names and contents, in sorted order)."""
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_2506_03969_gb300", "csrc")
-    for name in sorted(os.listdir(d)):
-        with open(os.path.join(d, name), "rb") as f:
+    for name in sorted(files if files is not None else os.listdir(d)):
+        path = os.path.join(d, name)
+        if not os.path.isfile(path):
+            return "missing"
+        with open(path, "rb") as f:
             h.update(name.encode())
             h.update(f.read())
     return h.hexdigest()[:12]
@@ -84,15 +89,16 @@ def recorded_traffic(kernel: str, alg_bytes_per_launch: float):
 
     profiles/dram_traffic.json holds, per kernel class, the source hash of the capture and the
     ratio of DRAM bytes to algorithmic bytes per launch; the ratio times the algorithmic bytes of
-    the timed launch is the traffic.  Records of other sources give None."""
+    the timed launch is the traffic.  A record may name the source files that define the kernel
+    ("sources": its translation unit and the headers it includes); the hash then covers those
+    files only, else every file under csrc.  Records of other sources give None."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         data = json.load(f)
-    cur = csrc_hash()
     for r in data.get("records", []):
-        if r.get("kernel") == kernel and r.get("csrc_hash") == cur:
+        if r.get("kernel") == kernel and r.get("csrc_hash") == csrc_hash(r.get("sources")):
             return float(r["dram_over_algorithmic"]) * alg_bytes_per_launch
     return None
 

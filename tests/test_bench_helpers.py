@@ -51,6 +51,22 @@ def test_recorded_traffic_only_for_the_recorded_sources(tmp_path, monkeypatch):
     assert bench.recorded_traffic("x_node", 1000.0) is None           # sources changed since
 
 
+def test_recorded_traffic_keyed_to_the_kernels_own_sources(tmp_path, monkeypatch):
+    """A record that names its kernel's source files stays valid while only other files change."""
+    root = _tree(tmp_path, {"k.cu": "kernel", "k.cuh": "header", "other.cu": "host"}, "{}")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    files = ["k.cu", "k.cuh"]
+    (root / "profiles" / "dram_traffic.json").write_text(json.dumps({"records": [
+        {"kernel": "x_node", "sources": files, "csrc_hash": bench.csrc_hash(files), "dram_over_algorithmic": 0.5}]}))
+    assert bench.recorded_traffic("x_node", 10.0) == pytest.approx(5.0)
+    (root / "paper_2506_03969_gb300" / "csrc" / "other.cu").write_text("host, changed")
+    assert bench.recorded_traffic("x_node", 10.0) == pytest.approx(5.0)
+    (root / "paper_2506_03969_gb300" / "csrc" / "k.cuh").write_text("header, changed")
+    assert bench.recorded_traffic("x_node", 10.0) is None
+    os.remove(root / "paper_2506_03969_gb300" / "csrc" / "k.cuh")
+    assert bench.recorded_traffic("x_node", 10.0) is None
+
+
 def test_recorded_traffic_without_a_record(tmp_path, monkeypatch):
     root = _tree(tmp_path, {"k.cu": "kernel"}, "{}")
     os.remove(root / "profiles" / "dram_traffic.json")
