@@ -3,7 +3,7 @@
 Both sides always see the same input: nu is rounded to FP32 before the oracle
 gets it, so the FP32 path's input rounding is never part of a measured error.
 
-Bounds (the benchmark spec): FP32 fields relative L2 <= 1e-5, gradients <= 1e-4, log
+Bounds (the target tolerances): FP32 fields relative L2 <= 1e-5, gradients <= 1e-4, log
 posterior |d|/|lp| <= 1e-6; FP64 path fields and gradients <= 1e-10, log
 posterior <= 1e-12.  They are held at well-conditioned points (see
 ``parity_points``): every cell at least 1e-3 in D delta0 away from the
