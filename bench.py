@@ -623,6 +623,12 @@ def run_extras(pkg, synth, cfg, bias, nu32, counts, args):
             rsd[f"{name}_{label}"] = {"evals_per_s": 1.0 / tx, "ms_per_eval": 1e3 * tx}
             del cx, gx
     out["redshift_space"] = rsd
+    # deterministic mass assignment (64-bit fixed-point CIC sums), 256^3
+    cdet = pkg.Context(pkg.config_from(cfg, batch=1, deterministic=True))
+    gdet = torch.empty_like(nu32)
+    tdet = timed(lambda: cdet.bridge_logpost_grad(nu32, counts, [bias], grad_out=gdet, want_bias_grad=False), 5)
+    out["deterministic_256"] = {"evals_per_s": 1.0 / tdet, "ms_per_eval": 1e3 * tdet}
+    del cdet, gdet
     return out
 
 

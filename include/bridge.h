@@ -101,6 +101,12 @@ typedef struct {
                                 the particle's real-space position in cell units
                                 relative to the observer (a particle at r = 0 is not
                                 moved); 6 more half spectra in the workspace.  0 or 1 */
+    int32_t deterministic;   /* 1: the CIC mass assignment sums in 64-bit fixed point
+                                (FP32: units of 2^-40, FP64: 2^-50), independent of the
+                                order of the atomic adds, so every result is identical
+                                from run to run (8 N^3 bytes more workspace per chain,
+                                one more launch); 0: float atomics, whose order varies
+                                (results differ by rounding).  0 or 1              */
 } bridge_config;
 
 /* Bias table of one chain; entries [0, n_regions) are used (Eq. local_bias,

@@ -42,7 +42,7 @@ class bridge_config(ctypes.Structure):
                 ("r_s", ctypes.c_double), ("lambda_th_phi", ctypes.c_double), ("lambda_th_delta", ctypes.c_double),
                 ("sharpness", ctypes.c_double), ("n_regions", ctypes.c_int32), ("rho_floor", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("recompute_alpt", ctypes.c_int32), ("rsd_f", ctypes.c_double),
-                ("rsd_los", ctypes.c_int32)]
+                ("rsd_los", ctypes.c_int32), ("deterministic", ctypes.c_int32)]
 
 
 _D16 = ctypes.c_double * MAX_REGIONS
@@ -120,24 +120,25 @@ def make_config(n: int, box: float, batch: int = 1, sigma8: float = 0.8, pk_ns: 
                 d2_over_d2: float = -3.0 / 7.0, r_s: float = 4.0, lambda_th_phi: float = 0.0,
                 lambda_th_delta: float = 0.0, sharpness: float = 20.0, n_regions: int = 4,
                 rho_floor: float = 1e-6, precision: int = BRIDGE_FP32, recompute_alpt: bool = False,
-                rsd_f: float = 0.0, rsd_los: int = 0) -> bridge_config:
+                rsd_f: float = 0.0, rsd_los: int = 0, deterministic: bool = False) -> bridge_config:
     """A bridge_config; the P(k) amplitude is fixed by sigma(8 Mpc/h) = sigma8 unless given."""
     if pk_amp is None:
         pk_amp = bridge_pk_amplitude(sigma8, 8.0, pk_ns, pk_kc, pk_pow)
     return bridge_config(n, batch, box, pk_amp, pk_ns, pk_kc, pk_pow, growth_d, d2_over_d2, r_s, lambda_th_phi,
                          lambda_th_delta, sharpness, n_regions, rho_floor, precision, int(bool(recompute_alpt)),
-                         float(rsd_f), int(rsd_los))
+                         float(rsd_f), int(rsd_los), int(bool(deterministic)))
 
 
 def config_from(cfg, precision: int = BRIDGE_FP32, batch: Optional[int] = None,
-                recompute_alpt: bool = False) -> bridge_config:
+                recompute_alpt: bool = False, deterministic: bool = False) -> bridge_config:
     """bridge_config from any object with the workload attributes (n, box, sigma8, ...)."""
     return make_config(cfg.n, cfg.box, batch=cfg.batch if batch is None else batch, sigma8=cfg.sigma8,
                        pk_ns=cfg.pk_ns, pk_kc=cfg.pk_kc, pk_pow=cfg.pk_pow, growth_d=cfg.growth_d,
                        d2_over_d2=cfg.d2_over_d2, r_s=cfg.r_s, lambda_th_phi=cfg.lambda_th_phi,
                        lambda_th_delta=cfg.lambda_th_delta, sharpness=cfg.sharpness, n_regions=cfg.n_regions,
                        rho_floor=cfg.rho_floor, precision=precision, recompute_alpt=recompute_alpt,
-                       rsd_f=getattr(cfg, "rsd_f", 0.0), rsd_los=getattr(cfg, "rsd_los", 0))
+                       rsd_f=getattr(cfg, "rsd_f", 0.0), rsd_los=getattr(cfg, "rsd_los", 0),
+                       deterministic=deterministic)
 
 
 def all_free(n_regions: int) -> int:

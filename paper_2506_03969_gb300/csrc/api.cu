@@ -63,6 +63,7 @@ struct bridge_ctx {
     int sp_alpt = SP_ALPT_STORED, sp_psi = SP_PSI_STORED;   // ALPT spectrum slots (recompute_alpt moves them)
     bool recompute = false;
     bool radial = false;                 // radial line of sight (rsd_f != 0, rsd_los = 1)
+    unsigned long long* fixed_acc = nullptr;   // deterministic CIC: 64-bit fixed-point mass per cell
     int sp_psi1 = 0, sp_gpsi1 = 0;       // its Psi_1 and g_Psi_1 slots
     long long nvox = 0, nspec = 0;
     size_t esz = 4;
@@ -195,6 +196,7 @@ int validate(const bridge_config* c, std::string* why) {
     if (c->recompute_alpt != 0 && c->recompute_alpt != 1) return bad("recompute_alpt must be 0 or 1");
     if (!std::isfinite(c->rsd_f)) return bad("rsd_f must be finite");
     if (c->rsd_los != 0 && c->rsd_los != 1) return bad("rsd_los must be 0 (plane-parallel) or 1 (radial)");
+    if (c->deterministic != 0 && c->deterministic != 1) return bad("deterministic must be 0 or 1");
     return BRIDGE_OK;
 }
 
@@ -231,7 +233,7 @@ int validate_bias(const bridge_ctx* ctx, const bridge_bias* b, std::string* why)
 
 struct Plan {
     size_t spec_bytes, real_bytes, c16_bytes, partial_bytes, sc_bytes, biasd_bytes, biast_bytes, node_bytes, rtab_bytes,
-        cot_bytes, total;
+        cot_bytes, fixed_bytes, total;
     int nspec_buf, nreal_buf;
 };
 
@@ -256,8 +258,9 @@ Plan make_plan(const bridge_config* c) {
     p.node_bytes = align_up(size_t(BRIDGE_NODE_L2_MB + 8) << 20);   // fused-node slabs (the launcher keeps them below the budget)
     p.rtab_bytes = align_up(size_t(kRadialTables) * (3 * (n / 2) * (n / 2) + 1) * esz);
     p.cot_bytes = align_up(sizeof(double) * B) + 2 * align_up(sizeof(double) * 32 * B);
+    p.fixed_bytes = c->deterministic ? align_up(size_t(nvox) * 8 * B) : 0;   // 64-bit CIC accumulator
     p.total = p.spec_bytes * p.nspec_buf + p.real_bytes * (p.nreal_buf + kExtraReal) + p.c16_bytes + p.partial_bytes +
-              p.sc_bytes + p.biasd_bytes + p.biast_bytes + p.node_bytes + p.rtab_bytes + p.cot_bytes + 256;
+              p.sc_bytes + p.biasd_bytes + p.biast_bytes + p.node_bytes + p.rtab_bytes + p.cot_bytes + p.fixed_bytes + 256;
     return p;
 }
 
@@ -471,8 +474,16 @@ template <typename T> int run_forward_fields(bridge_ctx* ctx, const T* nu) {
     // CIC (mass rho accumulated into a zeroed field); the displacement in real
     // space borrows the tensor buffers, which are written only afterwards
     RUN(psi_real<T>(ctx, RB_TH));
-    CKL("fill", rby<T>(ctx), launch_fill<T>(ctx->nvox * ctx->B, RB<T>(ctx, RB_DELTA), T(0), ctx->stream));
-    CKL("cic_scatter", 4 * rby<T>(ctx), launch_cic_scatter<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 3), RB<T>(ctx, RB_DELTA), ctx->stream));
+    if (ctx->fixed_acc) {
+        // order-independent 64-bit fixed-point sums (bit-reproducible mass assignment)
+        CKL("cic_scatter", 5 * rby<T>(ctx), launch_cic_scatter_fixed<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 3), ctx->fixed_acc,
+                                                                       ctx->stream));   // psi in, 64-bit zero + add
+        CKL("fixed_to_mass", 3 * rby<T>(ctx), launch_fixed_to_mass<T>(ctx->n, ctx->B, ctx->fixed_acc, RB<T>(ctx, RB_DELTA),
+                                                                      ctx->stream));
+    } else {
+        CKL("fill", rby<T>(ctx), launch_fill<T>(ctx->nvox * ctx->B, RB<T>(ctx, RB_DELTA), T(0), ctx->stream));
+        CKL("cic_scatter", 4 * rby<T>(ctx), launch_cic_scatter<T>(ctx->n, ctx->B, fields(ctx, RB_TH, 3), RB<T>(ctx, RB_DELTA), ctx->stream));
+    }
     // tidal tensor and density Hessian spectra (Sect. 2.8, App. B)
     RUN(z_fwd<T>(ctx, creal(ctx, RB_DELTA, 1), mspec<T>(ctx, SP_SCR, 1)));
     RUN(y_identity<T>(ctx, SP_SCR, 1, true));
@@ -1510,6 +1521,8 @@ int bridge_create(const bridge_config* cfg, void* stream, bridge_ctx** out) {
     ctx->theta = reinterpret_cast<double*>(w + align_up(sizeof(double) * ctx->B));
     ctx->ptheta = ctx->theta + 32 * size_t(ctx->B);
     w += pl.cot_bytes;
+    ctx->fixed_acc = pl.fixed_bytes ? reinterpret_cast<unsigned long long*>(w) : nullptr;
+    w += pl.fixed_bytes;
     {
         const int rlen = 3 * (cfg->n / 2) * (cfg->n / 2) + 1;
         std::vector<double> tab(size_t(4) * rlen);

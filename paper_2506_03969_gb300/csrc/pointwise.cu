@@ -146,24 +146,80 @@ __device__ __forceinline__ void cic_flush4(double* g, const CicWin<double>& W, i
     }
 }
 
+// Where a particle's weights go.  CicFloat: float (or double) atomics into rho, the
+// window flushed with vector atomics; the sum order varies from run to run.
+// CicFixed: 64-bit fixed-point integers (FP32: the window's exact 2^-40 units; FP64:
+// units of 2^-50, weights rounded once), whose sums do not depend on the order, so the
+// mass assignment is bit-reproducible; k_fixed_to_mass converts afterwards.
+template <typename T> struct CicFloat {
+    T* r;
+    __device__ void add(size_t i, T w) const { atomicAdd(r + i, w); }
+    __device__ void flush4(size_t i, const CicWin<T>& W, int wi) const { cic_flush4(r + i, W, wi); }
+};
+template <typename T> struct CicFixedScale;
+template <> struct CicFixedScale<float> { static constexpr int S = 40; };
+template <> struct CicFixedScale<double> { static constexpr int S = 50; };
+__device__ __forceinline__ unsigned long long fixed_units(float w) {   // the window's split: hi 2^20 + lo
+    const float s = w * 1048576.0f;
+    const float h = floorf(s);
+    return ((unsigned long long)h << 20) + __float2uint_rn((s - h) * 1048576.0f);
+}
+__device__ __forceinline__ unsigned long long fixed_units(double w) { return __double2ull_rn(w * 1125899906842624.0); }   // 2^50
+// FP64 windows of the fixed-point mode hold the integer units themselves
+struct CicWinFx64 {
+    unsigned long long* w;
+    __device__ CicWinFx64(unsigned char* raw, int) : w(reinterpret_cast<unsigned long long*>(raw)) {}
+    __device__ void zero(int i) { w[i] = 0ull; }
+    __device__ void add(int i, double v) { atomicAdd(w + i, fixed_units(v)); }
+    __device__ unsigned long long units(int i) const { return w[i]; }
+};
+template <typename T> struct CicFixed {
+    unsigned long long* r;
+    __device__ void add(size_t i, T w) const { atomicAdd(r + i, fixed_units(w)); }
+    template <typename W> __device__ void flush4(size_t i, const W& win, int wi) const {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            unsigned long long v;
+            if constexpr (sizeof(T) == 4) v = ((unsigned long long)win.hi[wi + q] << 20) + win.lo[wi + q];
+            else v = win.units(wi + q);
+            if (v != 0ull) atomicAdd(r + i + q, v);
+        }
+    }
+};
+template <typename T, bool FX> struct CicOut;
+template <typename T> struct CicOut<T, false> { using type = CicFloat<T>; using win = CicWin<T>; };
+template <> struct CicOut<float, true> { using type = CicFixed<float>; using win = CicWin<float>; };
+template <> struct CicOut<double, true> { using type = CicFixed<double>; using win = CicWinFx64; };
+
+// rho = units 2^-S, per chain; FP32 without FP64 arithmetic (two exact 32-bit halves).
+template <typename T> __global__ void k_fixed_to_mass(long long count, const unsigned long long* acc, T* rho) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long v = acc[i];
+        if constexpr (sizeof(T) == 4)
+            rho[i] = __fmaf_rn(float(unsigned(v >> 32)), 0.00390625f, float(unsigned(v & 0xffffffffull)) * 9.094947017729282e-13f);   // 2^32 2^-40, 2^-40
+        else
+            rho[i] = double(v) * 8.881784197001252e-16;   // 2^-50
+    }
+}
+
 #ifndef BRIDGE_CIC_BZ
 #define BRIDGE_CIC_BZ 16   // particle block depth along z: 16 gives 16 x 16 x 24-cell windows (48 KB, four CTAs
                            // per SM), 0.33 -> 0.22 ms at 256^3 against 32 (80 KB, two CTAs per SM)
 #endif
-template <typename T, int BZ>
-__global__ void __launch_bounds__(kPwThreads) k_cic_scatter(int N, long long nvox, Fields16 psi3, T* rho) {
+template <typename T, int BZ, bool FX, typename OutT>
+__global__ void __launch_bounds__(kPwThreads) k_cic_scatter(int N, long long nvox, Fields16 psi3, OutT* out_base) {
     using CB = CicBlock<T>;
     constexpr int BX = CB::BX, BY = CB::BY, H = CB::H;
     constexpr int WX = BX + 2 * H, WY = BY + 2 * H, WZ = BZ + 2 * H, CELLS = WX * WY * WZ;
     static_assert(WZ % 4 == 0 && H % 4 == 0, "window rows are groups of four cells");
     extern __shared__ __align__(16) unsigned char smraw[];
-    CicWin<T> W(smraw, CELLS);
+    typename CicOut<T, FX>::win W(smraw, CELLS);
     const int t = threadIdx.x;
     const size_t off = (size_t)blockIdx.y * nvox;
     const T* p0 = (const T*)psi3.p[0] + off;
     const T* p1 = (const T*)psi3.p[1] + off;
     const T* p2 = (const T*)psi3.p[2] + off;
-    T* r = rho + off;
+    const typename CicOut<T, FX>::type out{out_base + off};
     const int msk = N - 1;
     const int nbz = N / BZ, nby = N / BY;
     const int b = blockIdx.x;
@@ -190,8 +246,7 @@ __global__ void __launch_bounds__(kPwThreads) k_cic_scatter(int N, long long nvo
                     if (inside)
                         W.add(((wx + a) * WY + (wy + bb)) * WZ + wz + e, w);
                     else
-                        atomicAdd(r + ((size_t)((c.i0[0] + a) & msk) * N + ((c.i0[1] + bb) & msk)) * N +
-                                      ((c.i0[2] + e) & msk), w);
+                        out.add(((size_t)((c.i0[0] + a) & msk) * N + ((c.i0[1] + bb) & msk)) * N + ((c.i0[2] + e) & msk), w);
                 }
             }
         }
@@ -203,7 +258,7 @@ __global__ void __launch_bounds__(kPwThreads) k_cic_scatter(int N, long long nvo
         const int g = i % G, col = i / G;
         const int wy = col % WY, wx = col / WY;
         const int gx = (x0 - H + wx) & msk, gy = (y0 - H + wy) & msk, gz = (z0 - H + 4 * g) & msk;
-        cic_flush4(r + ((size_t)gx * N + gy) * N + gz, W, col * WZ + 4 * g);
+        out.flush4(((size_t)gx * N + gy) * N + gz, W, col * WZ + 4 * g);
     }
 }
 
@@ -578,8 +633,8 @@ template <typename T> cudaError_t launch_fill(long long count, T* p, T v, cudaSt
     k_fill<T><<<(unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b)), 256, 0, s>>>(count, p, v);
     return cudaGetLastError();
 }
-template <typename T>
-cudaError_t launch_cic_scatter(int n, int batch, const Fields16& psi3, T* delta, cudaStream_t s) {
+template <typename T, bool FX, typename OutT>
+static cudaError_t cic_scatter_run(int n, int batch, const Fields16& psi3, OutT* out, cudaStream_t s) {
     using CB = CicBlock<T>;
     if (n < 16) return cudaErrorInvalidValue;
     // BZ = BRIDGE_CIC_BZ (16 or 32 particles along z), 16 on the smallest mesh
@@ -588,10 +643,27 @@ cudaError_t launch_cic_scatter(int n, int batch, const Fields16& psi3, T* delta,
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
         if (e != cudaSuccess) return e;
         const unsigned blocks = unsigned((n / CB::BX) * (n / CB::BY) * (n / bz));
-        kern<<<dim3(blocks, batch), kPwThreads, sm, s>>>(n, nvox_of(n), psi3, delta);
+        kern<<<dim3(blocks, batch), kPwThreads, sm, s>>>(n, nvox_of(n), psi3, out);
         return cudaGetLastError();
     };
-    return n >= BRIDGE_CIC_BZ ? run(k_cic_scatter<T, BRIDGE_CIC_BZ>, BRIDGE_CIC_BZ) : run(k_cic_scatter<T, 16>, 16);
+    return n >= BRIDGE_CIC_BZ ? run(k_cic_scatter<T, BRIDGE_CIC_BZ, FX, OutT>, BRIDGE_CIC_BZ)
+                              : run(k_cic_scatter<T, 16, FX, OutT>, 16);
+}
+template <typename T>
+cudaError_t launch_cic_scatter(int n, int batch, const Fields16& psi3, T* delta, cudaStream_t s) {
+    return cic_scatter_run<T, false>(n, batch, psi3, delta, s);
+}
+template <typename T>
+cudaError_t launch_cic_scatter_fixed(int n, int batch, const Fields16& psi3, unsigned long long* acc, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(acc, 0, size_t(nvox_of(n)) * batch * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    return cic_scatter_run<T, true>(n, batch, psi3, acc, s);
+}
+template <typename T> cudaError_t launch_fixed_to_mass(int n, int batch, const unsigned long long* acc, T* rho, cudaStream_t s) {
+    const long long count = nvox_of(n) * batch;
+    long long b = (count + 1023) / 1024;
+    k_fixed_to_mass<T><<<(unsigned)(b > 4096 ? 4096 : (b < 1 ? 1 : b)), 256, 0, s>>>(count, acc, rho);
+    return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_pass_a(int n, int batch, const Fields16& th, const T* delta, T* lnf, T* beta_i,
@@ -684,6 +756,8 @@ cudaError_t launch_reduce(int what, int nblk, int batch, const double* partial, 
                                                cudaStream_t);                                                       \
     template cudaError_t launch_fill<T>(long long, T*, T, cudaStream_t);                                            \
     template cudaError_t launch_cic_scatter<T>(int, int, const Fields16&, T*, cudaStream_t);                        \
+    template cudaError_t launch_cic_scatter_fixed<T>(int, int, const Fields16&, unsigned long long*, cudaStream_t);    \
+    template cudaError_t launch_fixed_to_mass<T>(int, int, const unsigned long long*, T*, cudaStream_t);               \
     template cudaError_t launch_pass_a<T>(int, int, const Fields16&, const T*, T*, T*, const BiasT<T>*,             \
                                           const WebParams&, double*, const RedArgs&, cudaStream_t);                 \
     template cudaError_t launch_pass_b<T>(int, int, const T*, const T*, const uint16_t*, const T*,                  \

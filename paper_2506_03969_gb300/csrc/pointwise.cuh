@@ -73,6 +73,12 @@ cudaError_t launch_web_adjoint(int n, int batch, const Fields16& th, const T* de
                                const Fields16& out, double* partial, bool bias_grad, cudaStream_t s,
                                int blocks = 0);   // blocks per chain without bias_grad (0: built-in)
 template <typename T> cudaError_t launch_shift(long long count, const T* in, T* out, T c, cudaStream_t s);
+// CIC mass assignment in 64-bit fixed point (order-independent sums): zeroes acc (n^3 per chain)
+// and scatters into it; launch_fixed_to_mass then writes the mass rho = 1 + delta.
+template <typename T>
+cudaError_t launch_cic_scatter_fixed(int n, int batch, const Fields16& psi3, unsigned long long* acc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fixed_to_mass(int n, int batch, const unsigned long long* acc, T* rho, cudaStream_t s);
 // Radial redshift-space displacement in place (Sect. 2.9): psi += f (psi1 . r) r / |r|^2,
 // r = q + psi - (n/2)(1,1,1) in cell units; psi, psi1: 3 real fields each, [B][n^3].
 template <typename T>

@@ -48,7 +48,8 @@ def test_validate_config(pkg):
     assert pkg.lib().bridge_workspace_bytes(ctypes.byref(good)) > 0
     for field, value in (("n", 48), ("n", 8), ("n", 1024), ("batch", 0), ("box", -1.0), ("n_regions", 5),
                          ("sharpness", 0.0), ("rho_floor", 0.0), ("precision", 7), ("r_s", float("nan")),
-                         ("recompute_alpt", 2), ("rsd_los", 2), ("rsd_los", -1), ("rsd_f", float("inf"))):
+                         ("recompute_alpt", 2), ("rsd_los", 2), ("rsd_los", -1), ("rsd_f", float("inf")),
+                         ("deterministic", 2)):
         bad = pkg.make_config(32, 300.0, pk_amp=1.0)
         setattr(bad, field, value)
         assert pkg.lib().bridge_validate_config(ctypes.byref(bad)) == pkg.BRIDGE_EINVAL, field
@@ -80,6 +81,10 @@ def test_workspace_scales_with_mesh_and_batch(pkg):
     rad = pkg.lib().bridge_workspace_bytes(ctypes.byref(pkg.make_config(512, 2000.0, pk_amp=1.0, n_regions=16,
                                                                           rsd_f=0.8, rsd_los=1)))
     assert pp == d and abs((rad - d) - 6 * spec) < 4096
+    # the deterministic mass assignment adds one 64-bit field
+    det = pkg.lib().bridge_workspace_bytes(ctypes.byref(pkg.make_config(512, 2000.0, pk_amp=1.0, n_regions=16,
+                                                                          deterministic=True)))
+    assert abs((det - d) - 8 * 512 ** 3) < 4096
 
 
 def test_pk_amplitude_matches_oracle_quadrature(pkg):

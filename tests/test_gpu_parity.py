@@ -16,8 +16,9 @@ At the unmodified off-truth points a few cells dominate the gradient and S
 reaches 1e-3 (128^3) to 4e-2 (256^3): no FP32 evaluation can hold 1e-4 there.
 Those points check the fields and the log posterior; a field tolerance scaled
 by its own conditioning is capped at 1e-3, and the gradient error is printed
-next to S, asserted only where 10 S <= 1e-3.  Nothing is bit-exact: CIC atomics
-reorder sums.
+next to S, asserted only where 10 S <= 1e-3.  Nothing matches the oracle bit for bit;
+with float CIC atomics two GPU evaluations also differ by rounding, with the
+deterministic mass assignment they are bit-identical.
 """
 import math
 
@@ -512,6 +513,39 @@ def test_radial_redshift_space_256():
     nu, counts, _, cleared = pp.condition(nu_t, counts, cfg, bias, clear_empty=True)
     print(f"256 radial RSD truth: {cleared} near-empty cells cleared")
     ctx = _full_check("256_rsd_radial", cfg, bias, nu, counts, "fp32", conditioning="fields", psi=True)[0]
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_deterministic_mass_assignment(precision):
+    """deterministic = 1: the CIC sums are 64-bit fixed point, so two evaluations of one input
+    give bit-identical log posteriors and gradients (float atomics differ by rounding from run
+    to run), and the results still match the oracle at the fixed bounds; the batched path gives
+    each chain the same bits as its single-chain call."""
+    n, box, nr, seed = CASES["64_hier"]
+    cfg, bias, nu, counts, _ = make_case(n, box, nr, seed, point="eval")
+    f, lp_o, g_o, gb_o, _ = oracle_ref(f"64_hier_det_{precision}", cfg, bias, nu, counts, conditioning=False)
+    ctx, nu_d, c_d = run_gpu(cfg, bias, nu, counts, prec_code(precision), deterministic=True)
+    ftol, gtol, ltol = bounds(precision)
+    check_fields(ctx, nu_d, c_d, bias, f, ftol)
+    runs = [ctx.bridge_logpost_grad(nu_d, c_d, [bias]) for _ in range(3)]
+    for lp, g, gb in runs[1:]:
+        assert lp[0] == runs[0][0][0]
+        assert torch.equal(g, runs[0][1]) and np.array_equal(gb, runs[0][2])
+    lp, g, gb = runs[0]
+    e_g = rel_l2(g.double().cpu().numpy().reshape(g_o.shape), g_o)
+    print(f"deterministic {precision}: logpost rel {abs(lp[0] - lp_o) / abs(lp_o):.2e}, grad rel L2 {e_g:.2e}, "
+          f"3 evaluations bit-identical")
+    assert abs(lp[0] - lp_o) <= ltol * abs(lp_o) and e_g <= gtol
+    # batched: each chain bit-identical to its single-chain evaluation
+    cb = pkg.Context(pkg.config_from(cfg, precision=prec_code(precision), batch=2, deterministic=True))
+    nu2 = torch.stack([nu_d, nu_d.flip(0)]).contiguous()
+    c2 = torch.stack([c_d, c_d]).contiguous()
+    lpb, gbt, _ = cb.bridge_logpost_grad(nu2, c2, [bias, bias])
+    lp1, g1, _ = ctx.bridge_logpost_grad(nu2[1].contiguous(), c_d, [bias])
+    assert lpb[0] == lp[0] and torch.equal(gbt[0], g)
+    assert lpb[1] == lp1[0] and torch.equal(gbt[1], g1)
+    cb.close()
     ctx.close()
 
 
