@@ -83,3 +83,11 @@ def test_committed_record_parses():
     for r in recs:
         assert re.fullmatch(r"[0-9a-f]{12}", r["csrc_hash"]) and r["kernel"]
         assert 0.5 < float(r["dram_over_algorithmic"]) < 1.5
+
+
+def test_workload_config_names_the_small_case():
+    """The --small-case profiling run labels its line as the 128^3 case, never as the headline."""
+    head = bench.workload_config(1)
+    small = bench.workload_config(1, 128)
+    assert head["n"] == 256 and "256^3" in head["workload"]
+    assert small["n"] == 128 and "not the headline" in small["workload"]
